@@ -1,0 +1,520 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, closed forms of the lattice and of the Shan-Chen force,
+exact invariants of the scheme, and transport coefficients printed in the paper
+(eta = 0.383 and D = 1/6 at tau = 1, Section 2). A dropped term, a wrong sign,
+a wrong weight or a transposed operand in the oracle fails one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1909_01092_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+# Printed D3Q19 velocity set in the documented direction order.
+C = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+              [1, 1, 0], [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1], [-1, 0, -1], [1, 0, -1],
+              [-1, 0, 1], [0, 1, 1], [0, -1, -1], [0, 1, -1], [0, -1, 1]], dtype=float)
+
+
+def _feq(rho, u):
+    """Textbook second-order equilibrium, written from the lattice tables."""
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    cu = C @ u
+    return w * rho * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * (u @ u))
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 and the normal deviates
+# ---------------------------------------------------------------------------
+def test_philox_known_answer_vectors(oracle_mod):
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if ln.strip() and ln[0] != "#"]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle_mod.philox(v[0:4], v[4:6])
+        assert list(out) == v[6:10]
+
+
+def test_uniform_map_is_open_and_exact_in_binary32(oracle_mod):
+    lo, hi = oracle_mod.uniform(0), oracle_mod.uniform(0xFFFFFFFF)
+    assert lo == 0.5 * 2.0 ** -23 and hi == 1.0 - 0.5 * 2.0 ** -23
+    for x in (0, 1, 511, 512, 12345678, 0x80000000, 0xFFFFFFFF):
+        u = oracle_mod.uniform(x)
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u
+
+
+def test_normals_are_standard_gaussian(oracle_mod):
+    from scipy import stats
+    z = np.concatenate([oracle_mod.normals(99, 3, 7, n) for n in range(4000)])
+    assert abs(z.mean()) < 4 / math.sqrt(z.size)
+    assert abs(z.var() - 1) < 4 * math.sqrt(2 / z.size)
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    zz = z.reshape(4000, 36)
+    corr = np.corrcoef(zz.T) - np.eye(36)
+    assert np.abs(corr).max() < 5 / math.sqrt(4000)
+
+
+def test_normals_depend_on_every_key_field(oracle_mod):
+    base = oracle_mod.normals(5, 0, 0, 0)
+    for args in ((6, 0, 0, 0), (5, 1, 0, 0), (5, 0, 1, 0), (5, 0, 0, 1), (5 + (1 << 32), 0, 0, 0)):
+        assert not np.allclose(oracle_mod.normals(*args), base)
+
+
+# ---------------------------------------------------------------------------
+# Lattice and mode basis (D3Q19, Section 2)
+# ---------------------------------------------------------------------------
+def test_lattice_isotropy(oracle_mod):
+    L = oracle_mod.lattice()
+    c, w, opp = L["c"], L["w"], L["opp"]
+    assert np.array_equal(c, C)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.abs(w @ c).max() < 1e-16
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), np.eye(3) / 3, atol=1e-15)
+    d = np.eye(3)
+    iso4 = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d) + np.einsum("ad,bc->abcd", d, d)) / 9
+    assert np.allclose(np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c), iso4, atol=1e-15)
+    assert np.array_equal(c[opp], -c)
+
+
+def test_mode_basis_orthogonal_with_closed_form_norms(oracle_mod):
+    L = oracle_mod.lattice()
+    e, w, b = L["e"], L["w"], L["b"]
+    gram = (e * w) @ e.T
+    assert np.allclose(gram, np.diag(b), atol=1e-15)
+    expect = [1, 1 / 3, 1 / 3, 1 / 3, 2 / 3, 4 / 3, 4 / 9, 1 / 9, 1 / 9, 1 / 9,
+              2 / 3, 2 / 3, 2 / 3, 2 / 9, 2 / 9, 2 / 9, 2, 4 / 3, 4 / 9]
+    assert np.allclose(b, expect, atol=1e-15)
+    # rows 0..3 are density and momentum
+    assert np.array_equal(e[0], np.ones(19))
+    assert np.array_equal(e[1:4], C.T)
+
+
+# ---------------------------------------------------------------------------
+# Collision: equilibrium, forcing, rest state (Eq. lbe, MRT, Section 2)
+# ---------------------------------------------------------------------------
+def test_single_node_collision_is_second_order_equilibrium(oracle_mod):
+    """On a 1x1x1 periodic lattice streaming is the identity, so one step with
+    tau = 1 returns f_eq(rho_l, u) of the textbook polynomial, u = sum_l j_l / rho_tot."""
+    p = W.params(lx=1, ly=1, lz=1, wall=(0, 0, 0), G=1.5)
+    o = oracle_mod.Oracle(p)
+    rng = np.random.default_rng(3)
+    f = rng.uniform(0.01, 0.1, size=(2, 19, 1, 1, 1))
+    o.set_f(f)
+    o.step(1)
+    out = o.get_f()[:, :, 0, 0, 0]
+    rho = f[:, :, 0, 0, 0].sum(1)
+    j = (f[:, :, 0, 0, 0] @ C).sum(0)
+    u = j / rho.sum()
+    for l in range(2):
+        assert np.allclose(out[l], _feq(rho[l], u), rtol=1e-13, atol=1e-16)
+
+
+def test_single_node_forcing_matches_guo_source(oracle_mod):
+    """With a body force F_l the tau = 1 result is f_eq(rho_l, u) + 1/2 S_i, where S_i
+    is the second-order (Guo-type) source w_i [3 (c - u).F + 9 (c.u)(c.F)] and
+    u = (j + F/2) / rho_tot (the hydrodynamical velocity v^(H) of Section 2)."""
+    g = np.array([1e-3, -2e-3, 3e-3])
+    p = W.params(lx=1, ly=1, lz=1, wall=(0, 0, 0), fluid_force=tuple(g))
+    o = oracle_mod.Oracle(p)
+    rng = np.random.default_rng(4)
+    f = rng.uniform(0.01, 0.1, size=(2, 19, 1, 1, 1))
+    o.set_f(f)
+    o.step(1)
+    out = o.get_f()[:, :, 0, 0, 0]
+    f0 = f[:, :, 0, 0, 0]
+    rho = f0.sum(1)
+    Fl = np.outer(rho / rho.sum(), g)
+    u = ((f0 @ C).sum(0) + 0.5 * Fl.sum(0)) / rho.sum()
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    for l in range(2):
+        S = w * (3 * (C - u) @ Fl[l] + 9 * (C @ u) * (C @ Fl[l]))
+        assert np.allclose(out[l], _feq(rho[l], u) + 0.5 * S, rtol=1e-13, atol=1e-16)
+
+
+def test_uniform_rest_state_is_fixed_point_with_walls(oracle_mod):
+    p = W.params(lx=6, ly=5, lz=4, wall=(1, 1, 0), G=1.2, init_pert=0.0)
+    o = oracle_mod.Oracle(p)
+    f0 = o.get_f()
+    o.step(10)
+    assert np.allclose(o.get_f(), f0, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("i", range(1, 19))
+def test_free_streaming_and_halfway_walls(oracle_mod, i):
+    """With every relaxation time infinite (no collision), G = 0 and no noise,
+    a pulse moves one node per step along c_i; at a wall it comes back on the
+    opposite direction one step later (halfway bounce-back)."""
+    inf = float("inf")
+    p = W.params(lx=4, ly=4, lz=4, wall=(1, 1, 0), tau_s=inf, tau_d=inf, tau_g=inf, G=0.0, init_pert=0.0)
+    o = oracle_mod.Oracle(p)
+    base = o.get_f()
+    f = base.copy()
+    x0 = np.array([1, 2, 1])
+    f[0, i, x0[2], x0[1], x0[0]] += 0.25
+    o.set_f(f)
+    opp = [0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17]
+    pos, d = x0.copy(), i
+    for _ in range(6):
+        o.step(1)
+        nxt = pos + C[d].astype(int)
+        if nxt[0] < 0 or nxt[0] > 3 or nxt[1] < 0 or nxt[1] > 3:
+            d = opp[d]
+        else:
+            pos = nxt
+            pos[2] %= 4
+        g = o.get_f() - base
+        want = np.zeros_like(g)
+        want[0, d, pos[2], pos[1], pos[0]] = 0.25
+        assert np.allclose(g, want, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Shan-Chen force, Eq. (sc-force), with omega_i = D3Q19 weights
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_sc_force_on_a_sine_wave(oracle_mod, axis):
+    """rho_B = rho_B0 (1 + a sin(k x_axis)), rho_A uniform. Summing Eq. (sc-force)
+    by hand with the D3Q19 weights (1/6 of the weight on each side of the axis):
+    F_A = -G rho_A rho_B0 a sin(k) cos(k x) / 3 along the axis, F_B = 0."""
+    L, G, a = 12, 1.3, 0.1
+    dims = [1, 1, 1]
+    dims[axis] = L
+    p = W.params(lx=dims[0], ly=dims[1], lz=dims[2], wall=(0, 0, 0), G=G, init_pert=0.0)
+    o = oracle_mod.Oracle(p)
+    f = o.get_f()
+    k = 2 * np.pi / L
+    s = np.arange(L)
+    prof = (1 + a * np.sin(k * s)).reshape([L if ax == axis else 1 for ax in (2, 1, 0)])
+    f[1] = f[1] * prof[None]
+    o.set_f(f)
+    fl = o.fields()
+    rhoA = p["rho_a0"]
+    want = -G * rhoA * p["rho_b0"] * a * np.sin(k) * np.cos(k * s) / 3
+    got = fl["force"][0, axis].reshape(L)
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-17)
+    for ax in range(3):
+        if ax != axis:
+            assert np.abs(fl["force"][0, ax]).max() < 1e-17
+    assert np.abs(fl["force"][1]).max() < 1e-17
+
+
+@pytest.mark.parametrize("drho", [0.0, 0.02, 0.5, -0.3])
+def test_virtual_layer_and_sc_reaction(oracle_mod, drho):
+    """A sphere at rest in a uniform mixture (Section 2: virtual fluid layer).
+    Surface particle nodes carry psi = (rho_A + drho, rho_B - drho), clipped at 0;
+    nodes with no fluid neighbour carry 0. The force on a fluid node next to the
+    sphere is -G rho_l sum over its particle-node directions of w_i (psi_l'(s) - rho_l') c_i,
+    and the reaction on the particle is minus the sum of those forces."""
+    G = 1.2
+    p = W.params(lx=12, ly=12, lz=12, wall=(0, 0, 0), G=G, init_pert=0.0, radius=3.3, delta_rho=drho,
+                 pos0=(5.3, 5.6, 5.9))
+    o = oracle_mod.Oracle(p)
+    fl = o.fields()
+    ra, rb = p["rho_a0"], p["rho_b0"]
+    X = np.array(p["pos0"])
+    zz, yy, xx = np.meshgrid(np.arange(12), np.arange(12), np.arange(12), indexing="ij")
+    pts = np.stack([xx, yy, zz], -1).astype(float)
+    d = pts - X
+    d -= 12 * np.floor(d / 12 + 0.5)
+    solid = (d ** 2).sum(-1) < 3.3 ** 2
+    assert np.array_equal(fl["solid"], solid)
+    va, vb = max(ra + drho, 0.0), max(rb - drho, 0.0)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    tot = np.zeros(3)
+    for z in range(12):
+        for y in range(12):
+            for x in range(12):
+                nb = [((x + int(c[0])) % 12, (y + int(c[1])) % 12, (z + int(c[2])) % 12) for c in C[1:]]
+                if solid[z, y, x]:
+                    has_fluid = any(not solid[q[2], q[1], q[0]] for q in nb)
+                    want = (va, vb) if has_fluid else (0.0, 0.0)
+                    assert np.allclose(fl["psi"][:, z, y, x], want, atol=1e-15)
+                    continue
+                fa = np.zeros(3)
+                fb = np.zeros(3)
+                for idx, q in enumerate(nb, start=1):
+                    if solid[q[2], q[1], q[0]]:
+                        fa += -G * ra * w[idx] * (vb - rb) * C[idx]
+                        fb += -G * rb * w[idx] * (va - ra) * C[idx]
+                assert np.allclose(fl["force"][0, :, z, y, x], fa, atol=1e-15)
+                assert np.allclose(fl["force"][1, :, z, y, x], fb, atol=1e-15)
+                tot += fa + fb
+    assert np.allclose(fl["sc_reaction_force"], -tot, atol=1e-13)
+
+
+def test_neutral_wall_ghosts_exert_no_force_on_uniform_fluid(oracle_mod):
+    p = W.params(lx=5, ly=6, lz=3, wall=(1, 1, 1), G=1.5, init_pert=0.0)
+    o = oracle_mod.Oracle(p)
+    assert np.abs(o.fields()["force"]).max() < 1e-16
+
+
+def test_wall_ghost_is_mean_of_fluid_neighbours(oracle_mod):
+    """rho_B varies along y; walls on x. A node at x = 0 sees, across the wall,
+    ghosts whose psi is the mean over their fluid neighbours (Delta rho = 0)."""
+    G = 1.0
+    p = W.params(lx=3, ly=6, lz=1, wall=(1, 0, 0), G=G, init_pert=0.0)
+    o = oracle_mod.Oracle(p)
+    f = o.get_f()
+    prof = np.array([1.0, 1.3, 0.7, 1.1, 0.9, 1.2])
+    f[1] *= prof[None, None, :, None]
+    o.set_f(f)
+    fl = o.fields()
+    rb = p["rho_b0"] * prof
+    ra = p["rho_a0"]
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    # ghost at (-1, y): fluid neighbours (0, y), (0, y+-1) (z is a single periodic layer,
+    # so (0, y, z+-1) is (0, y) again twice)
+    def ghost(y):
+        vals = [rb[y], rb[(y + 1) % 6], rb[(y - 1) % 6], rb[y], rb[y]]
+        return np.mean(vals)
+    x, y = 0, 2
+    acc = np.zeros(3)
+    for i in range(1, 19):
+        cx, cy, cz = C[i].astype(int)
+        nx, ny = x + cx, (y + cy) % 6
+        psi = ghost(ny) if nx < 0 else rb[ny]
+        acc += w[i] * psi * C[i]
+    assert np.allclose(fl["force"][0, :, 0, y, x], -G * ra * acc, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Exact invariants
+# ---------------------------------------------------------------------------
+def test_mass_and_momentum_conservation_with_noise_and_sc(oracle_mod):
+    p = W.params(lx=6, ly=5, lz=7, wall=(0, 0, 0), G=1.5, kT=1e-4, tau_s=0.9, tau_d=1.3, tau_g=0.8)
+    o = oracle_mod.Oracle(p)
+    o.set_f(W.random_populations(p, 11))
+    a = o.observables()
+    o.step(15)
+    b = o.observables()
+    assert np.allclose(b["mass"], a["mass"], rtol=1e-13)
+    assert np.allclose(b["momentum"], a["momentum"], rtol=0, atol=1e-12)
+
+
+def test_constant_force_momentum_growth(oracle_mod):
+    """Total momentum grows by exactly N F per step under a constant body force."""
+    g = np.array([1e-5, -2e-5, 3e-5])
+    p = W.params(lx=4, ly=5, lz=3, wall=(0, 0, 0), G=1.2, kT=1e-5, fluid_force=tuple(g))
+    o = oracle_mod.Oracle(p)
+    o.set_f(W.random_populations(p, 12))
+    a = o.observables()["momentum"]
+    o.step(7)
+    b = o.observables()["momentum"]
+    assert np.allclose(b - a, 7 * 60 * g, rtol=1e-10, atol=1e-14)
+
+
+def test_particle_closes_mass_and_momentum(oracle_mod):
+    """A sphere moving through a periodic box (walls off, no driving force),
+    with Shan-Chen forces, wetting and noise: fluid mass plus the pending mass
+    correction is conserved per component, and fluid momentum plus particle
+    momentum plus the pending cover/uncover impulse is conserved exactly,
+    through bounce-back, virtual-layer reactions and cover/uncover events."""
+    p = W.params(lx=12, ly=12, lz=12, wall=(0, 0, 0), G=1.2, kT=1e-5, radius=2.7, delta_rho=0.3)
+    o = oracle_mod.Oracle(p)
+    o.set_particle(p["pos0"], V=(0.05, -0.03, 0.08), Omega=(0.01, 0.0, -0.02))
+
+    def inv():
+        ob, pa = o.observables(), o.particle()
+        return ob["mass"] + ob["pending_mass"], ob["momentum"] + ob["particle_momentum"] + pa["Ppend"]
+
+    m0, p0 = inv()
+    n0 = o.particle()["nfluid"]
+    changed = False
+    for _ in range(12):
+        o.step(1)
+        changed |= o.particle()["nfluid"] != n0
+        m1, p1 = inv()
+        assert np.allclose(m1, m0, rtol=1e-13)
+        assert np.allclose(p1, p0, rtol=0, atol=1e-12)
+    assert changed  # cover/uncover happened
+
+
+def test_particle_at_rest_feels_no_force_and_starts_with_fp_over_mp(oracle_mod):
+    """A centred sphere at rest in a uniform mixture: the exchanged force is zero
+    by symmetry, so after one step V = F_p / m_p along z exactly, with
+    F_p = (4/3) pi R^3 (rho_p - rho_tot) g and m_p = (4/3) pi R^3 rho_p (Eq. fp)."""
+    R, ratio, g = 3.0, 1.5, 1e-5
+    p = W.params(lx=16, ly=16, lz=16, wall=(1, 1, 0), G=1.2, init_pert=0.0, radius=R, rho_p_ratio=ratio, g=g,
+                 pos0=(7.5, 7.5, 7.5))
+    o = oracle_mod.Oracle(p)
+    o.step(1)
+    pa = o.particle()
+    rt = p["rho_a0"] + p["rho_b0"]
+    vol = 4 / 3 * math.pi * R ** 3
+    assert math.isclose(pa["Fp"], vol * (ratio * rt - rt) * g, rel_tol=1e-14)
+    assert math.isclose(pa["mp"], vol * ratio * rt, rel_tol=1e-14)
+    assert np.abs(pa["F"]).max() < 1e-14
+    assert np.allclose(pa["V"], [0, 0, pa["Fp"] / pa["mp"]], rtol=1e-12, atol=1e-16)
+    assert np.allclose(pa["X"], np.array(p["pos0"]) + pa["V"], rtol=1e-15)
+
+
+def test_moving_sphere_is_dragged_backwards(oracle_mod):
+    p = W.params(lx=14, ly=14, lz=14, wall=(0, 0, 0), G=0.0, init_pert=0.0, radius=3.0)
+    o = oracle_mod.Oracle(p)
+    V = np.array([0.0, 0.0, 0.01])
+    o.set_particle(p["pos0"], V=V)
+    o.step(1)
+    F = o.particle()["F"]
+    assert F[2] < 0 and abs(F[0]) < 1e-3 * abs(F[2]) and abs(F[1]) < 1e-3 * abs(F[2])
+
+
+# ---------------------------------------------------------------------------
+# Transport coefficients printed in the paper (Section 2: eta = 0.383, D = 1/6)
+# ---------------------------------------------------------------------------
+def _shear_decay_rate(oracle_mod, tau_s, L=48, steps=120):
+    p = W.params(lx=L, ly=1, lz=1, wall=(0, 0, 0), G=0.0, tau_s=tau_s, init_pert=0.0, rho_a0=2.21, rho_b0=0.09)
+    o = oracle_mod.Oracle(p)
+    x = np.arange(L)
+    k = 2 * np.pi / L
+    A = 1e-4
+    f = np.zeros((2, 19, 1, 1, L))
+    for l, r in enumerate((2.21, 0.09)):
+        for n in range(L):
+            f[l, :, 0, 0, n] = _feq(r, np.array([0.0, A * np.sin(k * x[n]), 0.0]))
+    o.set_f(f)
+
+    def amp():
+        g = o.get_f()
+        uy = np.einsum("li...,i->...", g, C[:, 1]).reshape(L) / 2.3
+        return 2 * (uy * np.sin(k * x)).mean()
+
+    a0 = amp()
+    o.step(steps)
+    a1 = amp()
+    return -math.log(a1 / a0) / steps / k ** 2
+
+
+@pytest.mark.parametrize("tau_s", [1.0, 0.8])
+def test_shear_wave_gives_printed_viscosity(oracle_mod, tau_s):
+    """A decaying shear wave measures the kinematic viscosity nu = (tau - 1/2)/3.
+    At tau = 1 and rho_A + rho_B = 2.3 this is eta = rho nu = 0.383 (Section 2)."""
+    nu = _shear_decay_rate(oracle_mod, tau_s)
+    assert abs(nu - (tau_s - 0.5) / 3) < 0.005 * nu
+    if tau_s == 1.0:
+        assert abs(2.3 * nu - 0.383) < 0.001
+
+
+def test_interdiffusion_gives_printed_diffusivity(oracle_mod):
+    """A composition wave at constant total density (G = 0) decays with the
+    diffusivity D = (tau_d - 1/2)/3 = 1/6 at tau_d = 1 (Section 2)."""
+    L = 48
+    p = W.params(lx=L, ly=1, lz=1, wall=(0, 0, 0), G=0.0, init_pert=0.0, rho_a0=1.0, rho_b0=1.0)
+    o = oracle_mod.Oracle(p)
+    k = 2 * np.pi / L
+    x = np.arange(L)
+    c = 0.01 * np.sin(k * x)
+    f = np.zeros((2, 19, 1, 1, L))
+    for n in range(L):
+        f[0, :, 0, 0, n] = _feq(1.0 + c[n], np.zeros(3))
+        f[1, :, 0, 0, n] = _feq(1.0 - c[n], np.zeros(3))
+    o.set_f(f)
+
+    def amp():
+        rA = o.get_f()[0].sum(0).reshape(L)
+        return 2 * ((rA - 1.0) * np.sin(k * x)).mean()
+
+    a0 = amp()
+    o.step(150)
+    D = -math.log(amp() / a0) / 150 / k ** 2
+    assert abs(D - 1 / 6) < 0.005 / 6
+
+
+def test_poiseuille_profile_curvature(oracle_mod):
+    """Plane Poiseuille flow between halfway walls: the steady velocity has
+    constant second difference -g / (rho nu) with nu = (tau - 1/2)/3, and is
+    symmetric about the channel centre."""
+    L, g, tau = 12, 1e-6, 0.9
+    p = W.params(lx=L, ly=1, lz=1, wall=(1, 0, 0), G=0.0, tau_s=tau, init_pert=0.0,
+                 rho_a0=1.0, rho_b0=0.0, fluid_force=(0.0, 0.0, g))
+    o = oracle_mod.Oracle(p)
+    o.step(4000)
+    f = o.get_f()
+    rho = f.sum((0, 1)).reshape(L)
+    uz = (np.einsum("li...,i->...", f, C[:, 2]).reshape(L) + 0.5 * g) / rho
+    nu = (tau - 0.5) / 3
+    d2 = uz[2:] - 2 * uz[1:-1] + uz[:-2]
+    assert np.allclose(d2, -g / nu, rtol=2e-4)
+    assert np.allclose(uz, uz[::-1], rtol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Fluctuation-dissipation (Section 2): noise only on non-conserved modes with
+# variance 3 kT rho_l b_k; equipartition <j^2>/rho = kT per direction.
+# ---------------------------------------------------------------------------
+def test_single_node_mode_variances(oracle_mod):
+    kT = 1e-4
+    p = W.params(lx=1, ly=1, lz=1, wall=(0, 0, 0), G=0.0, kT=kT, init_pert=0.0, rho_a0=1.0, rho_b0=0.5)
+    o = oracle_mod.Oracle(p)
+    L = oracle_mod.lattice()
+    e, b = L["e"], L["b"]
+    n = 6000
+    modes = np.empty((n, 2, 19))
+    for s in range(n):
+        o.step(1)
+        f = o.get_f()[:, :, 0, 0, 0]
+        modes[s] = f @ e.T
+    rho = np.array([1.0, 0.5])
+    # conserved: densities exactly, total momentum exactly
+    assert np.allclose(modes[:, :, 0], rho, rtol=1e-12)
+    assert np.abs(modes[:, 0, 1:4] + modes[:, 1, 1:4]).max() < 1e-14
+    for l in range(2):
+        var = (modes[:, l, 4:] ** 2).mean(0)
+        want = 3 * kT * rho[l] * b[4:]
+        assert np.all(np.abs(var / want - 1) < 5 * math.sqrt(2 / n))
+    jvar = (modes[:, 0, 1:4] ** 2).mean(0)
+    want = kT * rho[0] * rho[1] / rho.sum()
+    assert np.all(np.abs(jvar / want - 1) < 5 * math.sqrt(2 / n))
+    flat = modes[:, :, 4:].reshape(n, -1)
+    corr = np.corrcoef(flat.T) - np.eye(flat.shape[1])
+    assert np.abs(corr).max() < 6 / math.sqrt(n)
+
+
+@pytest.mark.slow
+def test_fluid_equipartition(oracle_mod):
+    kT = 1e-4
+    p = W.params(lx=6, ly=6, lz=6, wall=(0, 0, 0), G=0.0, kT=kT, init_pert=0.0, rho_a0=1.0, rho_b0=0.3)
+    o = oracle_mod.Oracle(p)
+    o.step(50)
+    acc, cnt = np.zeros(3), 0
+    for _ in range(150):
+        o.step(1)
+        f = o.get_f()
+        rho = f.sum((0, 1))
+        j = np.einsum("li...,ia->a...", f, C)
+        acc += (j ** 2 / rho).mean((1, 2, 3))
+        cnt += 1
+    assert np.allclose(acc / cnt, kT, rtol=0.05)
+
+
+def test_sphere_comoving_with_uniform_flow_is_invisible(oracle_mod):
+    """Galilean invariance of the moving-wall link rule (Ladd 1994, cited in
+    Section 2): in a uniform flow U with the sphere moving at U (no wetting
+    shift), the bounced populations equal the equilibrium ones the solid would
+    have sent, so the exchanged force and torque vanish and the flow is left
+    unchanged. A wrong factor or sign in the moving-wall term fails this."""
+    drho = 0.0
+    U = np.array([0.013, -0.021, 0.017])
+    p = W.params(lx=12, ly=11, lz=13, wall=(0, 0, 0), G=1.2, init_pert=0.0, radius=3.1,
+                 delta_rho=drho, pos0=(5.37, 4.81, 6.22))
+    o = oracle_mod.Oracle(p)
+    f = o.get_f()
+    for l, r in enumerate((p["rho_a0"], p["rho_b0"])):
+        f[l] = _feq(r, U)[:, None, None, None] * np.ones((1, 13, 11, 12))
+    o.set_f(f)
+    o.set_particle(p["pos0"], V=U)
+    solid0 = o.fields()["solid"].copy()
+    o.step(1)
+    pa = o.particle()
+    assert np.abs(pa["F"]).max() < 1e-14
+    assert np.abs(pa["T"]).max() < 1e-13
+    g = o.get_f()
+    keep = ~(solid0 | o.fields()["solid"])
+    for l in range(2):
+        assert np.allclose(g[l][:, keep], f[l][:, keep], rtol=0, atol=1e-15)
