@@ -1,0 +1,276 @@
+#!/usr/bin/env python3
+"""Throughput of the FLBM two-component Shan-Chen + particle time step on GB300.
+
+Workload: the 128x128x512 square channel (walls on x and y, periodic z) with
+thermal noise kT = 1e-5, a sphere of radius 12 driven by g = 1e-5 along z,
+G = 1.2, rho_A = 1.0, rho_B = 0.05, tau = 1 on every mode, FP32 populations
+(2.55 GB in two copies, far larger than L2, so no flush is needed between
+steps). One step = density pass, virtual layer, density shell, fused
+collide-stream with bounce-back and momentum exchange, particle update.
+
+Prints one JSON line. `--impl reference` times the FP64 CPU oracle on a
+bounded slab of the same channel instead (rank 0 only).
+Multi-GPU (torchrun): every rank advances its own replica (distinct Philox
+replica index); no data-path collective, value = all ranks' node updates /
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "2-comp D3Q19 FLBM MLUPS & % HBM roofline; ensemble/adjoint vs plain step"
+WORKLOAD = "channel_128x128x512_kT1e-5_R12"
+# Algorithmic bytes per node update: 2 components x 19 float32 populations read
+# and written once (the method's minimum), and for the fused collide kernel
+# alone also the 2 float32 densities of its own node.
+STEP_BYTES_PER_NODE = 2 * 19 * 4 * 2
+COLLIDE_BYTES_PER_NODE = STEP_BYTES_PER_NODE + 2 * 4
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lz", type=int, default=512, help="channel length (shorter only for profiler captures)")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [ln.split(",") for ln in open(self.f.name).read().strip().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_median": statistics.median(power)}
+
+
+def cpu_baseline(max_seconds: float = 12.0, max_steps: int = 40) -> dict:
+    """The FP64 oracle, as it stands, on a slab of the benchmarked channel:
+    128x128x32 nodes (same cross-section, physics and sphere; 1/16 of the length)."""
+    import oracle
+    from paper_1909_01092_gb300 import workloads as W
+
+    p = W.channel_large(lz=32)
+    o = oracle.Oracle(p)
+    n = p["lx"] * p["ly"] * p["lz"]
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        o.step(1)
+        steps += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} steps of the FP64 oracle on a 128x128x32 slab of the channel (kT=1e-5, R=12 sphere), "
+                      f"{dt:.1f} s, OpenMP over nodes"}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_init()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1909_01092_gb300 import workloads as W
+
+    p = W.channel_large(lz=32)
+    o = oracle.Oracle(p)
+    n = p["lx"] * p["ly"] * p["lz"]
+    t0 = time.perf_counter()
+    o.step(1)
+    est = time.perf_counter() - t0
+    budget = 150.0
+    warm = min(args.warmup, max(0, int(budget * 0.1 / est)))
+    o.step(max(0, warm - 1))
+    k = max(3, min(args.steps, int(budget / est)))
+    t0 = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t0
+    value = n * k / dt / 1e6
+    sample = (f"{k} timed steps (of {args.steps} requested) after {max(warm, 1)} warm-up, FP64 oracle on a "
+              f"128x128x32 slab of the channel (kT=1e-5, R=12 sphere)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / k * 1e3 * (8388608 / n),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_lz": 32},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1909_01092_gb300 import binding, workloads as W
+
+    p = W.channel_large(replica=rank, lz=args.lz)
+    nodes = p["lx"] * p["ly"] * p["lz"]
+    sim = binding.Sim(p)
+    stream = sim.stream
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    kms = sim.step_timed(args.steps)
+    ev1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    launches = sim.launches()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = nodes * args.steps * world / (ms_max * 1e-3) / 1e6
+
+    # End to end through the C-ABI with host buffers: the initial populations
+    # go host->device from pinned memory, every step's particle record and the
+    # final populations come back device->host.
+    f_host = torch.empty(sim.shape, dtype=torch.float32, pin_memory=True).numpy()
+    f_out = torch.empty(sim.shape, dtype=torch.float32, pin_memory=True).numpy()
+    f_host[...] = sim.read_f()
+    barrier()
+    t0 = time.perf_counter()
+    sim.run_host(f_host, args.steps, f_out=f_out, traj=True)
+    t1 = time.perf_counter()
+    tt = torch.tensor([t1 - t0], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_s = float(tt.item())
+    fbytes = f_host.nbytes
+    rec = binding.record_bytes()  # bytes of one particle record
+    e2e = {"value": nodes * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": fbytes / args.steps, "d2h_bytes_per_step": (fbytes + rec * args.steps) / args.steps,
+           "api": "flbm_run_host"}
+
+    peak, src = peaks()
+    coll_ms = kms["k_collide"] / args.steps
+    achieved = COLLIDE_BYTES_PER_NODE * nodes / (coll_ms * 1e-3) / 1e9
+    step_gbs = STEP_BYTES_PER_NODE * nodes / (ms / args.steps * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_collide", "peak_source": f"{src} hbm_gbs (copy)",
+                "bytes_per_node": COLLIDE_BYTES_PER_NODE,
+                "step": {"achieved": step_gbs, "frac": step_gbs / peak, "bytes_per_node": STEP_BYTES_PER_NODE},
+                "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD if args.lz == 512 else f"channel_128x128x{args.lz}_kT1e-5_R12", "lx": p["lx"], "ly": p["ly"], "lz": p["lz"], "kT": p["kT"],
+                           "radius": p["radius"], "g": p["g"], "G": p["G"], "walls": "x,y", "replicas_per_gpu": 1,
+                           "l2": "inputs larger than L2 (2.55 GB of populations), no flush"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

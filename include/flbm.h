@@ -1,0 +1,198 @@
+/*
+ * flbm.h - C ABI of the GB300 (sm_103a) library for one time step of the
+ * fluctuating lattice Boltzmann method (FLBM) for a two-component Shan-Chen
+ * mixture coupled to a wetted finite-size spherical particle.
+ *
+ * Method: X. Xue, L. Biferale, M. Sbragaglia, F. Toschi, "A lattice Boltzmann
+ * study of particle settling in a fluctuating multicomponent fluid under
+ * confinement", arXiv:1909.01092.
+ *   - Section 2, Eq. (density): component densities and mixture momentum.
+ *   - Section 2, Eq. (lbe): collision (MRT), source term, thermal noise, streaming.
+ *   - Section 2, Eq. (sc-force): Shan-Chen inter-component force.
+ *   - Section 2, particle paragraph: particle nodes, moving bounce-back with
+ *     momentum exchange, leap-frog Newton-Euler update, cover/uncover, mass
+ *     correction, virtual fluid layer for wettability.
+ *   - Section 3, Eq. (fp): driving force on the particle; square channel walls.
+ *
+ * Conventions for every function:
+ *   - Return 0 (FLBM_OK) on success, a negative FLBM_E_* code on failure;
+ *     flbm_error_string() names the code and flbm_last_error() gives the
+ *     message of the handle's last failure.
+ *   - Handles are not thread-safe: one host thread at a time per handle.
+ *   - All device work is issued on the handle's stream (the one passed to
+ *     flbm_create; NULL means the legacy default stream). Functions that
+ *     return data to host memory synchronise that stream before returning.
+ *   - Host pointers are plain host memory (pageable or pinned); pinned memory
+ *     makes flbm_run_host's copies faster. Device pointers are CUDA global
+ *     memory on the current device.
+ *
+ * Population layout (host and device): float32 f[l][i][z][y][x], l = 0 (A),
+ * 1 (B); D3Q19 direction i in the order
+ *   0:(0,0,0)  1:(+1,0,0)  2:(-1,0,0)  3:(0,+1,0)  4:(0,-1,0)  5:(0,0,+1)  6:(0,0,-1)
+ *   7:(+1,+1,0) 8:(-1,-1,0) 9:(+1,-1,0) 10:(-1,+1,0)
+ *   11:(+1,0,+1) 12:(-1,0,-1) 13:(+1,0,-1) 14:(-1,0,+1)
+ *   15:(0,+1,+1) 16:(0,-1,-1) 17:(0,+1,-1) 18:(0,-1,+1)
+ * The stored state is the post-streaming (pre-collision) population of the
+ * current time. Values at particle nodes are not part of the state.
+ */
+#ifndef FLBM_H
+#define FLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FLBM_OK = 0,
+    FLBM_E_INVAL = -1,       /* invalid argument or parameter set */
+    FLBM_E_NOMEM = -2,       /* device or host allocation failed */
+    FLBM_E_CUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+    FLBM_E_NONFINITE = -4,   /* a NaN/Inf was found in the state */
+    FLBM_E_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    FLBM_E_UNSUPPORTED = -6  /* valid request this build does not implement */
+};
+
+/* Parameters of one simulation; host memory, copied by flbm_create. */
+typedef struct flbm_params {
+    int32_t lx, ly, lz;             /* lattice nodes per axis, each >= 1 */
+    int32_t wall_x, wall_y, wall_z; /* 1: halfway bounce-back walls at -1/2 and L-1/2; 0: periodic */
+    double tau_s;                   /* relaxation time of the stress modes (viscosity nu = (tau_s-1/2)/3) */
+    double tau_d;                   /* relaxation time of the component momenta (diffusivity D = (tau_d-1/2)/3) */
+    double tau_g;                   /* relaxation time of the ghost modes */
+    double G;                       /* Shan-Chen coupling of Eq. (sc-force), psi = rho */
+    double rho_a0, rho_b0;          /* initial densities of components A and B */
+    double init_pert;               /* relative amplitude of the uniform random initial density perturbation */
+    double kT;                      /* thermal energy; 0 switches the noise off */
+    double radius;                  /* sphere radius in lattice units; <= 0: no particle */
+    double rho_p_ratio;             /* particle density / (rho_a0 + rho_b0) */
+    double g;                       /* body-force density along z of Eq. (fp): F_p = 4/3 pi R^3 (rho_p - rho_tot) g */
+    double delta_rho;               /* wetting shift of the virtual layer: +delta_rho on A, -delta_rho on B */
+    double fluid_force[3];          /* constant body-force density on the fluid, split over A/B by rho_l/rho_tot */
+    int32_t fluid_counterforce;     /* 1: also apply -F_p/N_fluid along z on the fluid (zero net external force) */
+    uint32_t replica;               /* replica index, folded into the Philox key */
+    uint64_t seed;                  /* Philox key */
+    double pos0[3];                 /* initial particle centre (lattice coordinates, node centres at integers) */
+} flbm_params;
+
+/* Particle record (host memory, filled by the library). */
+typedef struct flbm_particle {
+    double X[3];          /* centre after the last step */
+    double V[3];          /* velocity V_{n+1/2} of the last leap-frog update */
+    double Vavg[3];       /* (V_{n-1/2} + V_{n+1/2}) / 2: the velocity reported for step n */
+    double Omega[3];      /* angular velocity Omega_{n+1/2} */
+    double F[3];          /* hydrodynamic force of the last step (exchange + Shan-Chen reaction + cover/uncover) */
+    double T[3];          /* hydrodynamic torque of the last step */
+    double P_pending[3];  /* cover/uncover impulse carried into the next step */
+    double L_pending[3];  /* cover/uncover angular impulse carried into the next step */
+    double delta[2];      /* per-node mass correction of A and B applied in the next collision */
+    double mp;            /* particle mass 4/3 pi R^3 rho_p */
+    double Fp;            /* driving force of Eq. (fp) */
+    int64_t nfluid;       /* number of fluid nodes */
+    int64_t step;         /* completed steps */
+} flbm_particle;
+
+/* Observables of the current state (host memory, filled by the library). */
+typedef struct flbm_obs {
+    double mass[2];              /* sum over fluid nodes of rho_A, rho_B */
+    double momentum[3];          /* sum over fluid nodes of sum_l sum_i f_li c_i */
+    double kinetic;              /* sum over fluid nodes of |j|^2 / (2 rho_tot) */
+    double particle_momentum[3]; /* m_p V */
+    double pending_mass[2];      /* delta_l * N_fluid, still to be added by the next collision */
+    int64_t nfluid;
+    int64_t step;
+    int64_t nonfinite;           /* number of non-finite populations on fluid nodes */
+} flbm_obs;
+
+typedef struct flbm_sim flbm_t;
+
+/* Device bytes of the population storage (two float32 copies of
+ * 2 x 19 x lx*ly*lz values) for these parameters; 0 if they are invalid. */
+size_t flbm_state_bytes(const flbm_params* p);
+
+/* Create a simulation on the current CUDA device.
+ *   p        : parameters (validated; FLBM_E_INVAL if out of range).
+ *   f_dev    : NULL, or device memory of at least flbm_state_bytes(p) bytes,
+ *              256-byte aligned, that the library borrows for the populations
+ *              (the caller keeps it alive until flbm_destroy). NULL: the
+ *              library allocates it.
+ *   f_dev_bytes : size of f_dev in bytes (ignored when f_dev is NULL).
+ *   stream   : cudaStream_t to issue all work on (NULL: default stream).
+ *   out      : receives the handle.
+ * Initial state (Section 2 set-up): f_li = w_i rho_l0 (1 + a (2u-1)) with one
+ * Philox uniform u per (node, component); the particle at pos0, at rest.
+ * Errors: FLBM_E_INVAL, FLBM_E_NOMEM, FLBM_E_CUDA. */
+int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* stream, flbm_t** out);
+
+/* Advance nsteps >= 0 time steps (Eq. (lbe) with all of Section 2's particle
+ * coupling). Asynchronous on the handle's stream. Errors: FLBM_E_INVAL,
+ * FLBM_E_CUDA (launch failure). */
+int flbm_step(flbm_t* h, int64_t nsteps);
+
+/* Copy the particle record to host memory `out`; synchronises the stream. */
+int flbm_particle_state(flbm_t* h, flbm_particle* out);
+
+/* Reduce the observables of the current state (FP64) into `out`;
+ * synchronises the stream. Returns FLBM_E_NONFINITE if any fluid population
+ * is not finite (out is still filled). */
+int flbm_observables(flbm_t* h, flbm_obs* out);
+
+/* Copy the current populations to host_f (2*19*N float32, layout above) and,
+ * if host_rho is not NULL, the densities used by the Shan-Chen force of the
+ * next step (2*N float32: rho on fluid nodes, virtual-layer values on surface
+ * particle nodes, 0 elsewhere). Either pointer may be NULL. Synchronises. */
+int flbm_read_fields(flbm_t* h, float* host_f, float* host_rho);
+
+/* Overwrite the current populations from host_f (2*19*N float32). */
+int flbm_write_fields(flbm_t* h, const float* host_f);
+
+/* Set the particle centre, velocity (V_{n-1/2}) and angular velocity, and
+ * re-mark the particle nodes. Pending impulses and mass corrections are
+ * cleared. FLBM_E_UNSUPPORTED if the simulation has no particle. */
+int flbm_set_particle(flbm_t* h, const double X[3], const double V[3], const double Omega[3]);
+
+/* End-to-end call from host memory: copy host_f_in (2*19*N float32) to the
+ * device, advance nsteps, write the particle record of every step to
+ * traj[0..nsteps-1] (may be NULL), copy the final populations to host_f_out
+ * (may be NULL). Synchronises before returning. */
+int flbm_run_host(flbm_t* h, const float* host_f_in, int64_t nsteps, float* host_f_out, flbm_particle* traj);
+
+/* Kernel classes of one step, in launch order (k_virtual runs only with a particle). */
+enum {
+    FLBM_K_DENSITY = 0,  /* densities of fluid nodes (Eq. (density)) */
+    FLBM_K_VIRTUAL = 1,  /* virtual wetting layer on particle surface nodes */
+    FLBM_K_SHELL = 2,    /* periodic copies and neutral wall ghosts of the density field */
+    FLBM_K_COLLIDE = 3,  /* force, MRT collision, noise, streaming, bounce-back, exchange */
+    FLBM_K_PARTICLE = 4, /* leap-frog update, cover/uncover, mass correction */
+    FLBM_NKERNELS = 5
+};
+
+/* Same as flbm_step, and measures the device time of each kernel class with
+ * CUDA events recorded between the kernels on the handle's stream (no extra
+ * synchronisation between steps). On return ms[FLBM_NKERNELS] (host memory,
+ * caller-owned) holds the summed milliseconds of each class over the nsteps
+ * steps. Synchronises the stream. Errors: FLBM_E_INVAL, FLBM_E_CUDA. */
+int flbm_step_timed(flbm_t* h, int64_t nsteps, double* ms);
+
+/* Static name of kernel class k ("" if out of range). */
+const char* flbm_kernel_name(int k);
+
+/* Number of kernel launches the last flbm_step / flbm_step_timed / flbm_run_host issued. */
+int64_t flbm_last_launch_count(const flbm_t* h);
+
+/* Release the handle and the device memory the library allocated. */
+void flbm_destroy(flbm_t* h);
+
+/* Static name of an FLBM_E_* code. */
+const char* flbm_error_string(int code);
+
+/* Message of the handle's last failure ("" if none); valid until the next call. */
+const char* flbm_last_error(const flbm_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLBM_H */

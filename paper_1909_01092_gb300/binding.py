@@ -1,0 +1,248 @@
+"""Thin ctypes binding of the C-ABI in include/flbm.h (argument marshalling only).
+
+Every step of the method runs in the sm_103a kernels of libflbm. There is no
+CPU path: if the shared library is missing or cannot be loaded, `load()`
+raises. PyTorch provides the device memory of the populations (borrowed by
+the library) and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+_LOCK = threading.Lock()
+
+# Every function declared in include/flbm.h.
+EXPORTS = (
+    "flbm_state_bytes", "flbm_create", "flbm_step", "flbm_particle_state", "flbm_observables",
+    "flbm_read_fields", "flbm_write_fields", "flbm_set_particle", "flbm_run_host",
+    "flbm_last_launch_count", "flbm_destroy", "flbm_error_string", "flbm_last_error",
+    "flbm_step_timed", "flbm_kernel_name",
+)
+NKERNELS = 5
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("lx", ctypes.c_int32), ("ly", ctypes.c_int32), ("lz", ctypes.c_int32),
+        ("wall_x", ctypes.c_int32), ("wall_y", ctypes.c_int32), ("wall_z", ctypes.c_int32),
+        ("tau_s", ctypes.c_double), ("tau_d", ctypes.c_double), ("tau_g", ctypes.c_double),
+        ("G", ctypes.c_double), ("rho_a0", ctypes.c_double), ("rho_b0", ctypes.c_double),
+        ("init_pert", ctypes.c_double), ("kT", ctypes.c_double), ("radius", ctypes.c_double),
+        ("rho_p_ratio", ctypes.c_double), ("g", ctypes.c_double), ("delta_rho", ctypes.c_double),
+        ("fluid_force", ctypes.c_double * 3), ("fluid_counterforce", ctypes.c_int32),
+        ("replica", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("pos0", ctypes.c_double * 3),
+    ]
+
+
+class Particle(ctypes.Structure):
+    _fields_ = [
+        ("X", ctypes.c_double * 3), ("V", ctypes.c_double * 3), ("Vavg", ctypes.c_double * 3),
+        ("Omega", ctypes.c_double * 3), ("F", ctypes.c_double * 3), ("T", ctypes.c_double * 3),
+        ("P_pending", ctypes.c_double * 3), ("L_pending", ctypes.c_double * 3),
+        ("delta", ctypes.c_double * 2), ("mp", ctypes.c_double), ("Fp", ctypes.c_double),
+        ("nfluid", ctypes.c_int64), ("step", ctypes.c_int64),
+    ]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [
+        ("mass", ctypes.c_double * 2), ("momentum", ctypes.c_double * 3), ("kinetic", ctypes.c_double),
+        ("particle_momentum", ctypes.c_double * 3), ("pending_mass", ctypes.c_double * 2),
+        ("nfluid", ctypes.c_int64), ("step", ctypes.c_int64), ("nonfinite", ctypes.c_int64),
+    ]
+
+
+class FLBMError(RuntimeError):
+    pass
+
+
+def load(build_if_missing: bool = True):
+    """Load libflbm (building it with nvcc if needed). Raises if unavailable."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        path = _build.lib_path()
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise FLBMError(f"libflbm not built at {path}; run paper_1909_01092_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.flbm_state_bytes.restype = ctypes.c_size_t
+        lib.flbm_state_bytes.argtypes = [ctypes.POINTER(Params)]
+        lib.flbm_create.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+        lib.flbm_step.argtypes = [vp, ctypes.c_int64]
+        lib.flbm_particle_state.argtypes = [vp, ctypes.POINTER(Particle)]
+        lib.flbm_observables.argtypes = [vp, ctypes.POINTER(Obs)]
+        lib.flbm_read_fields.argtypes = [vp, fp, fp]
+        lib.flbm_write_fields.argtypes = [vp, fp]
+        lib.flbm_set_particle.argtypes = [vp, dp, dp, dp]
+        lib.flbm_run_host.argtypes = [vp, fp, ctypes.c_int64, fp, ctypes.POINTER(Particle)]
+        lib.flbm_step_timed.argtypes = [vp, ctypes.c_int64, dp]
+        lib.flbm_kernel_name.restype = ctypes.c_char_p
+        lib.flbm_kernel_name.argtypes = [ctypes.c_int]
+        lib.flbm_last_launch_count.restype = ctypes.c_int64
+        lib.flbm_last_launch_count.argtypes = [vp]
+        lib.flbm_destroy.argtypes = [vp]
+        lib.flbm_error_string.restype = ctypes.c_char_p
+        lib.flbm_error_string.argtypes = [ctypes.c_int]
+        lib.flbm_last_error.restype = ctypes.c_char_p
+        lib.flbm_last_error.argtypes = [vp]
+        _LIB = lib
+        return lib
+
+
+def to_params(p: dict) -> Params:
+    s = Params()
+    s.lx, s.ly, s.lz = int(p["lx"]), int(p["ly"]), int(p["lz"])
+    s.wall_x, s.wall_y, s.wall_z = (int(v) for v in p["wall"])
+    s.tau_s, s.tau_d, s.tau_g = float(p["tau_s"]), float(p["tau_d"]), float(p["tau_g"])
+    s.G = float(p["G"])
+    s.rho_a0, s.rho_b0 = float(p["rho_a0"]), float(p["rho_b0"])
+    s.init_pert, s.kT = float(p["init_pert"]), float(p["kT"])
+    s.radius, s.rho_p_ratio = float(p["radius"]), float(p["rho_p_ratio"])
+    s.g, s.delta_rho = float(p["g"]), float(p["delta_rho"])
+    for a in range(3):
+        s.fluid_force[a] = float(p["fluid_force"][a])
+        s.pos0[a] = float(p["pos0"][a])
+    s.fluid_counterforce = int(p["fluid_counterforce"])
+    s.replica = int(p["replica"]) & 0xFFFFFFFF
+    s.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
+    return s
+
+
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def record_bytes() -> int:
+    return ctypes.sizeof(Particle)
+
+
+def particle_dict(r: Particle) -> dict:
+    d = {k: np.array(getattr(r, k)[:]) for k in ("X", "V", "Vavg", "Omega", "F", "T", "P_pending", "L_pending",
+                                                  "delta")}
+    d.update(mp=r.mp, Fp=r.Fp, nfluid=r.nfluid, step=r.step)
+    return d
+
+
+class Sim:
+    """One simulation on the current CUDA device.
+
+    The population storage (two float32 copies) is a torch CUDA tensor lent to
+    the library; work is issued on torch's current stream unless `stream` (a
+    torch.cuda.Stream) is given.
+    """
+
+    def __init__(self, p: dict, stream=None, borrow_torch: bool = True):
+        import torch
+
+        self.lib = load()
+        self.p = dict(p)
+        self._s = to_params(p)
+        self.shape = (2, 19, p["lz"], p["ly"], p["lx"])
+        self.N = p["lx"] * p["ly"] * p["lz"]
+        nbytes = self.lib.flbm_state_bytes(ctypes.byref(self._s))
+        if nbytes == 0:
+            raise FLBMError("invalid parameters")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._buf = None
+        ptr = None
+        if borrow_torch:
+            self._buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            ptr = ctypes.c_void_p(self._buf.data_ptr())
+        h = ctypes.c_void_p()
+        rc = self.lib.flbm_create(ctypes.byref(self._s), ptr, ctypes.c_size_t(nbytes),
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != 0:
+            raise FLBMError(f"flbm_create: {self.lib.flbm_error_string(rc).decode()}")
+        self.h = h
+
+    def _check(self, rc: int, what: str) -> None:
+        if rc != 0:
+            msg = self.lib.flbm_last_error(self.h).decode()
+            raise FLBMError(f"{what}: {self.lib.flbm_error_string(rc).decode()} {msg}")
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.flbm_destroy(self.h)
+            self.h = None
+            self._buf = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1) -> None:
+        self._check(self.lib.flbm_step(self.h, int(n)), "flbm_step")
+
+    def step_timed(self, n: int) -> dict:
+        """Advance n steps; return the summed device milliseconds per kernel class."""
+        ms = np.zeros(NKERNELS)
+        self._check(self.lib.flbm_step_timed(self.h, int(n), _dptr(ms)), "flbm_step_timed")
+        return {self.lib.flbm_kernel_name(k).decode(): float(ms[k]) for k in range(NKERNELS)}
+
+    def launches(self) -> int:
+        return int(self.lib.flbm_last_launch_count(self.h))
+
+    def particle(self) -> dict:
+        r = Particle()
+        self._check(self.lib.flbm_particle_state(self.h, ctypes.byref(r)), "flbm_particle_state")
+        return particle_dict(r)
+
+    def observables(self, allow_nonfinite: bool = False) -> dict:
+        r = Obs()
+        rc = self.lib.flbm_observables(self.h, ctypes.byref(r))
+        if not (allow_nonfinite and rc == -4):
+            self._check(rc, "flbm_observables")
+        return dict(mass=np.array(r.mass[:]), momentum=np.array(r.momentum[:]), kinetic=r.kinetic,
+                    particle_momentum=np.array(r.particle_momentum[:]), pending_mass=np.array(r.pending_mass[:]),
+                    nfluid=r.nfluid, step=r.step, nonfinite=r.nonfinite)
+
+    def read_f(self) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.float32)
+        self._check(self.lib.flbm_read_fields(self.h, _fptr(out), None), "flbm_read_fields")
+        return out
+
+    def read_rho(self) -> np.ndarray:
+        out = np.empty((2,) + self.shape[2:], dtype=np.float32)
+        self._check(self.lib.flbm_read_fields(self.h, None, _fptr(out)), "flbm_read_fields")
+        return out
+
+    def write_f(self, f: np.ndarray) -> None:
+        a = np.ascontiguousarray(f, dtype=np.float32).reshape(self.shape)
+        self._check(self.lib.flbm_write_fields(self.h, _fptr(a)), "flbm_write_fields")
+
+    def set_particle(self, X, V=(0.0, 0.0, 0.0), Omega=(0.0, 0.0, 0.0)) -> None:
+        x = np.asarray(X, dtype=np.float64)
+        v = np.asarray(V, dtype=np.float64)
+        w = np.asarray(Omega, dtype=np.float64)
+        self._check(self.lib.flbm_set_particle(self.h, _dptr(x), _dptr(v), _dptr(w)), "flbm_set_particle")
+
+    def run_host(self, f_in: np.ndarray, nsteps: int, f_out: np.ndarray | None = None, traj: bool = False):
+        """End-to-end call: host populations in, nsteps, host populations (and the
+        per-step particle records) out. `f_in`/`f_out` may be pinned torch tensors'
+        numpy views."""
+        a = np.ascontiguousarray(f_in, dtype=np.float32)
+        tr = (Particle * max(int(nsteps), 1))() if traj else None
+        self._check(self.lib.flbm_run_host(self.h, _fptr(a), int(nsteps),
+                                           _fptr(f_out) if f_out is not None else None,
+                                           tr if traj else None), "flbm_run_host")
+        if traj:
+            return [particle_dict(tr[k]) for k in range(int(nsteps))]
+        return None

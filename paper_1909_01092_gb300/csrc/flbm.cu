@@ -1,0 +1,525 @@
+// C-ABI of the FLBM step library (declared in include/flbm.h): handle
+// management, validation, launch sequence of one time step, and the host
+// copies. All compute runs in the kernels of flbm_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "flbm.h"
+#include "flbm_kernels.cuh"
+
+using namespace flbm;
+
+struct flbm_sim {
+    flbm_params p;
+    KParams kp;
+    cudaStream_t stream = nullptr;
+    float* fbuf[2] = {nullptr, nullptr};
+    void* f_owned = nullptr;
+    int cur = 0;  // fbuf[cur] holds the current state
+    float* psi = nullptr;
+    DevState* st = nullptr;
+    uint8_t* masks = nullptr;
+    double* partials = nullptr;
+    double* obs_tiles = nullptr;
+    double* obs_out = nullptr;
+    float* scratch_rho = nullptr;
+    DevState* traj_dev = nullptr;
+    size_t traj_cap = 0;
+    DevState* traj_host = nullptr;
+    size_t traj_host_cap = 0;
+    std::vector<cudaEvent_t> events;  // pool for flbm_step_timed
+    dim3 grid, block;
+    long long ntiles = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(flbm_sim* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    return code;
+}
+
+int cuda_fail(flbm_sim* h, cudaError_t e, const char* what)
+{
+    return fail(h, FLBM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                             \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+int ceil_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// Parameter checks; returns an empty string if valid.
+std::string validate(const flbm_params* p)
+{
+    if (!p) return "params is NULL";
+    if (p->lx < 1 || p->ly < 1 || p->lz < 1) return "lattice sizes must be >= 1";
+    if (p->lz > 65535 || p->ly > 65535 * 256) return "lattice too large for the launch grid";
+    const double n = (double)p->lx * p->ly * p->lz;
+    if (n > 4294967295.0) return "more than 2^32 nodes (node index feeds a 32-bit Philox counter)";
+    const int w[3] = {p->wall_x, p->wall_y, p->wall_z};
+    for (int a = 0; a < 3; ++a)
+        if (w[a] != 0 && w[a] != 1) return "wall flags must be 0 or 1";
+    if (!(p->tau_s > 0.5) || !(p->tau_d > 0.5) || !(p->tau_g > 0.5)) return "relaxation times must exceed 1/2";
+    if (!std::isfinite(p->G) || !std::isfinite(p->kT) || p->kT < 0.0) return "G must be finite and kT >= 0";
+    if (!(p->rho_a0 >= 0.0) || !(p->rho_b0 >= 0.0) || !(p->rho_a0 + p->rho_b0 > 0.0)) return "initial densities";
+    if (!(p->init_pert >= 0.0 && p->init_pert < 1.0)) return "init_pert must be in [0, 1)";
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(p->fluid_force[a])) return "fluid_force must be finite";
+    if (p->fluid_counterforce != 0 && p->fluid_counterforce != 1) return "fluid_counterforce must be 0 or 1";
+    if (p->radius > 0.0) {
+        if (!finite_pos(p->rho_p_ratio) || !std::isfinite(p->g) || !std::isfinite(p->delta_rho))
+            return "particle parameters must be finite, rho_p_ratio > 0";
+        const int L[3] = {p->lx, p->ly, p->lz};
+        const int B = (int)std::ceil(2.0 * p->radius) + 2;
+        for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(p->pos0[a])) return "pos0 must be finite";
+            if (w[a]) {
+                if (p->pos0[a] - p->radius < -0.5 || p->pos0[a] + p->radius > L[a] - 0.5)
+                    return "the sphere must lie inside the walls";
+            } else if (B + 2 > L[a]) {
+                return "periodic axis too short for the sphere (need L >= ceil(2R) + 4)";
+            }
+        }
+    }
+    return "";
+}
+
+void fill_kparams(flbm_sim* h)
+{
+    const flbm_params& p = h->p;
+    KParams& k = h->kp;
+    std::memset(&k, 0, sizeof(k));
+    k.lx = p.lx; k.ly = p.ly; k.lz = p.lz;
+    k.wall[0] = p.wall_x; k.wall[1] = p.wall_y; k.wall[2] = p.wall_z;
+    k.px = p.lx + 2; k.py = p.ly + 2; k.pz = p.lz + 2;
+    k.N = (long long)p.lx * p.ly * p.lz;
+    k.padn = (long long)k.px * k.py * k.pz;
+    k.tx = std::min(32, ceil_pow2(p.lx));
+    k.ty = kThreads / k.tx;
+    k.gx = (p.lx + k.tx - 1) / k.tx;
+    k.gy = (p.ly + k.ty - 1) / k.ty;
+    k.G = (float)p.G;
+    const double gs = 1.0 - 1.0 / p.tau_s, gd = 1.0 - 1.0 / p.tau_d, gg = 1.0 - 1.0 / p.tau_g;
+    k.gs = (float)gs; k.gd = (float)gd; k.gg = (float)gg;
+    for (int a = 0; a < 3; ++a) k.ext[a] = (float)p.fluid_force[a];
+    k.drho = (float)p.delta_rho;
+    k.kT = (float)p.kT;
+    const double b[19] = {1, 1. / 3, 1. / 3, 1. / 3, 2. / 3, 4. / 3, 4. / 9, 1. / 9, 1. / 9, 1. / 9,
+                          2. / 3, 2. / 3, 2. / 3, 2. / 9, 2. / 9, 2. / 9, 2, 4. / 3, 4. / 9};
+    for (int q = 0; q < 19; ++q) {
+        const double gm = (q <= 9) ? gs : gg;
+        k.nz_mode[q] = (q >= 4) ? (float)std::sqrt((1.0 - gm * gm) / b[q]) : 0.0f;
+    }
+    k.nz_j = (float)std::sqrt(1.0 - gd * gd);
+    k.key0 = (uint32_t)(p.seed & 0xffffffffu);
+    k.key1 = (uint32_t)(p.seed >> 32) ^ p.replica;
+    k.has_particle = p.radius > 0.0 ? 1 : 0;
+    k.B = k.has_particle ? (int)std::ceil(2.0 * p.radius) + 2 : 1;
+    k.R = p.radius;
+    k.rho0[0] = p.rho_a0; k.rho0[1] = p.rho_b0;
+    k.counterforce = p.fluid_counterforce;
+    h->block = dim3(k.tx, k.ty, 1);
+    h->grid = dim3(k.gx, k.gy, p.lz);
+    h->ntiles = (long long)k.gx * k.gy * p.lz;
+}
+
+int launch_check(flbm_sim* h, const char* what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    h->launches += 1;
+    return FLBM_OK;
+}
+
+void record(flbm_sim* h, cudaEvent_t* ev, int k)
+{
+    if (ev) cudaEventRecord(ev[k], h->stream);
+}
+
+// Densities, virtual layer and psi shell for the current state. With ev,
+// events ev[0..3] bracket the three kernels.
+int launch_psi(flbm_sim* h, const float* f, cudaEvent_t* ev = nullptr)
+{
+    const KParams& k = h->kp;
+    record(h, ev, 0);
+    k_density<<<h->grid, h->block, 0, h->stream>>>(f, h->psi, h->st, h->masks, k);
+    if (int rc = launch_check(h, "k_density")) return rc;
+    record(h, ev, 1);
+    if (k.has_particle) {
+        const int nb = (k.B * k.B * k.B + kThreads - 1) / kThreads;
+        k_virtual<<<nb, kThreads, 0, h->stream>>>(h->psi, h->st, h->masks, k);
+        if (int rc = launch_check(h, "k_virtual")) return rc;
+    }
+    record(h, ev, 2);
+    const long long nshell = 2LL * k.px * k.py + 2LL * k.px * k.lz + 2LL * k.ly * k.lz;
+    const long long nb = (nshell + kThreads - 1) / kThreads;
+    k_shell<<<(unsigned)nb, kThreads, 0, h->stream>>>(h->psi, h->st, h->masks, k);
+    if (int rc = launch_check(h, "k_shell")) return rc;
+    record(h, ev, 3);
+    return FLBM_OK;
+}
+
+// One time step. With ev, events ev[0..5] bracket its five kernels.
+int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
+{
+    const KParams& k = h->kp;
+    const float* fin = h->fbuf[h->cur];
+    float* fout = h->fbuf[1 - h->cur];
+    if (int rc = launch_psi(h, fin, ev)) return rc;
+    const bool noise = k.kT > 0.0f;
+    const bool part = k.has_particle != 0;
+    if (noise && part)
+        k_collide<true, true><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks, h->partials, k);
+    else if (noise)
+        k_collide<true, false><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks, h->partials, k);
+    else if (part)
+        k_collide<false, true><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks, h->partials, k);
+    else
+        k_collide<false, false><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks, h->partials, k);
+    if (int rc = launch_check(h, "k_collide")) return rc;
+    record(h, ev, 4);
+    k_particle<<<1, 1024, 0, h->stream>>>(fout, h->st, h->masks, h->partials, k);
+    if (int rc = launch_check(h, "k_particle")) return rc;
+    record(h, ev, 5);
+    h->cur = 1 - h->cur;
+    return FLBM_OK;
+}
+
+int copy_particle(const DevState& s, flbm_particle* out)
+{
+    for (int a = 0; a < 3; ++a) {
+        out->X[a] = s.X[a]; out->V[a] = s.V[a]; out->Vavg[a] = s.Vavg[a]; out->Omega[a] = s.Om[a];
+        out->F[a] = s.F[a]; out->T[a] = s.T[a]; out->P_pending[a] = s.Ppend[a]; out->L_pending[a] = s.Lpend[a];
+    }
+    out->delta[0] = s.delta[0];
+    out->delta[1] = s.delta[1];
+    out->mp = s.mp;
+    out->Fp = s.Fp;
+    out->nfluid = s.nfluid;
+    out->step = s.step;
+    return FLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t flbm_state_bytes(const flbm_params* p)
+{
+    if (!validate(p).empty()) return 0;
+    return (size_t)2 * 2 * 19 * (size_t)p->lx * p->ly * p->lz * sizeof(float);
+}
+
+int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* stream, flbm_t** out)
+{
+    if (!out) return FLBM_E_INVAL;
+    *out = nullptr;
+    std::string v = validate(p);
+    if (!v.empty()) {
+        std::fprintf(stderr, "flbm_create: %s\n", v.c_str());
+        return FLBM_E_INVAL;
+    }
+    flbm_sim* h = new (std::nothrow) flbm_sim();
+    if (!h) return FLBM_E_NOMEM;
+    h->p = *p;
+    h->stream = (cudaStream_t)stream;
+    fill_kparams(h);
+    const KParams& k = h->kp;
+    const size_t need = flbm_state_bytes(p);
+    int rc = FLBM_OK;
+    auto bail = [&](int code) {
+        flbm_destroy(h);
+        return code;
+    };
+    if (f_dev) {
+        if (f_dev_bytes < need || ((uintptr_t)f_dev % 256) != 0) {
+            std::fprintf(stderr, "flbm_create: borrowed buffer too small or not 256-byte aligned\n");
+            return bail(FLBM_E_INVAL);
+        }
+        h->fbuf[0] = (float*)f_dev;
+    } else {
+        if (cudaMalloc(&h->f_owned, need) != cudaSuccess) return bail(FLBM_E_NOMEM);
+        h->fbuf[0] = (float*)h->f_owned;
+    }
+    h->fbuf[1] = h->fbuf[0] + (size_t)2 * 19 * k.N;
+    const size_t B3 = (size_t)k.B * k.B * k.B;
+    if (cudaMalloc(&h->psi, sizeof(float) * 2 * k.padn) != cudaSuccess ||
+        cudaMalloc(&h->st, sizeof(DevState)) != cudaSuccess ||
+        cudaMalloc(&h->masks, 2 * B3) != cudaSuccess ||
+        cudaMalloc(&h->partials, sizeof(double) * 8 * h->ntiles) != cudaSuccess ||
+        cudaMalloc(&h->obs_tiles, sizeof(double) * 8 * h->ntiles) != cudaSuccess ||
+        cudaMalloc(&h->obs_out, sizeof(double) * 8) != cudaSuccess)
+        return bail(FLBM_E_NOMEM);
+
+    // Particle state (FP64): Eq. (fp) and the nominal sphere mass and inertia.
+    DevState s;
+    std::memset(&s, 0, sizeof(s));
+    if (k.has_particle) {
+        const double vol = 4.0 / 3.0 * M_PI * p->radius * p->radius * p->radius;
+        const double rho_tot = p->rho_a0 + p->rho_b0;
+        const double rho_p = p->rho_p_ratio * rho_tot;
+        s.mp = vol * rho_p;
+        s.Ip = 0.4 * s.mp * p->radius * p->radius;
+        s.Fp = vol * (rho_p - rho_tot) * p->g;
+        for (int a = 0; a < 3; ++a) s.X[a] = p->pos0[a];
+    }
+    s.nfluid = k.N;
+    if ((rc = cudaMemcpyAsync(h->st, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+        return bail(FLBM_E_CUDA);
+    if (cudaMemsetAsync(h->masks, 0, 2 * B3, h->stream) != cudaSuccess) return bail(FLBM_E_CUDA);
+    if (cudaMemsetAsync(h->psi, 0, sizeof(float) * 2 * k.padn, h->stream) != cudaSuccess) return bail(FLBM_E_CUDA);
+    if (cudaMemsetAsync(h->partials, 0, sizeof(double) * 8 * h->ntiles, h->stream) != cudaSuccess)
+        return bail(FLBM_E_CUDA);
+    k_init<<<h->grid, h->block, 0, h->stream>>>(h->fbuf[0], k, (float)p->rho_a0, (float)p->rho_b0,
+                                                 (float)p->init_pert);
+    if (launch_check(h, "k_init")) return bail(FLBM_E_CUDA);
+    // Both copies start equal, so particle nodes (never written by the step) hold defined values.
+    if (cudaMemcpyAsync(h->fbuf[1], h->fbuf[0], need / 2, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+        return bail(FLBM_E_CUDA);
+    if (k.has_particle) {
+        k_mark<<<1, 1024, 0, h->stream>>>(h->st, h->masks, k);
+        if (launch_check(h, "k_mark")) return bail(FLBM_E_CUDA);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(FLBM_E_CUDA);
+    *out = h;
+    return FLBM_OK;
+}
+
+int flbm_step(flbm_t* h, int64_t nsteps)
+{
+    if (!h || nsteps < 0) return fail(h, FLBM_E_INVAL, "invalid handle or step count");
+    h->launches = 0;
+    for (int64_t s = 0; s < nsteps; ++s)
+        if (int rc = launch_step(h)) return rc;
+    return FLBM_OK;
+}
+
+int flbm_particle_state(flbm_t* h, flbm_particle* out)
+{
+    if (!h || !out) return fail(h, FLBM_E_INVAL, "NULL argument");
+    DevState s;
+    CK(h, cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return copy_particle(s, out);
+}
+
+int flbm_observables(flbm_t* h, flbm_obs* out)
+{
+    if (!h || !out) return fail(h, FLBM_E_INVAL, "NULL argument");
+    const KParams& k = h->kp;
+    k_obs_tiles<<<h->grid, h->block, 0, h->stream>>>(h->fbuf[h->cur], h->st, h->masks, h->obs_tiles, k);
+    if (int rc = launch_check(h, "k_obs_tiles")) return rc;
+    k_obs_final<<<1, 1024, 0, h->stream>>>(h->obs_tiles, h->ntiles, h->obs_out);
+    if (int rc = launch_check(h, "k_obs_final")) return rc;
+    double v[8];
+    DevState s;
+    CK(h, cudaMemcpyAsync(v, h->obs_out, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    out->mass[0] = v[0];
+    out->mass[1] = v[1];
+    for (int a = 0; a < 3; ++a) {
+        out->momentum[a] = v[2 + a];
+        out->particle_momentum[a] = s.mp * s.V[a];
+    }
+    out->kinetic = v[5];
+    out->pending_mass[0] = s.delta[0] * (double)s.nfluid;
+    out->pending_mass[1] = s.delta[1] * (double)s.nfluid;
+    out->nfluid = s.nfluid;
+    out->step = s.step;
+    out->nonfinite = (int64_t)v[6];
+    return out->nonfinite ? fail(h, FLBM_E_NONFINITE, "non-finite populations") : FLBM_OK;
+}
+
+int flbm_read_fields(flbm_t* h, float* host_f, float* host_rho)
+{
+    if (!h) return FLBM_E_INVAL;
+    const KParams& k = h->kp;
+    if (host_f)
+        CK(h, cudaMemcpyAsync(host_f, h->fbuf[h->cur], sizeof(float) * 2 * 19 * k.N, cudaMemcpyDeviceToHost,
+                              h->stream));
+    if (host_rho) {
+        if (!h->scratch_rho) CK(h, cudaMalloc(&h->scratch_rho, sizeof(float) * 2 * k.N));
+        if (int rc = launch_psi(h, h->fbuf[h->cur])) return rc;
+        k_unpad<<<h->grid, h->block, 0, h->stream>>>(h->psi, h->scratch_rho, k);
+        if (int rc = launch_check(h, "k_unpad")) return rc;
+        CK(h, cudaMemcpyAsync(host_rho, h->scratch_rho, sizeof(float) * 2 * k.N, cudaMemcpyDeviceToHost,
+                              h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return FLBM_OK;
+}
+
+int flbm_write_fields(flbm_t* h, const float* host_f)
+{
+    if (!h || !host_f) return fail(h, FLBM_E_INVAL, "NULL argument");
+    CK(h, cudaMemcpyAsync(h->fbuf[h->cur], host_f, sizeof(float) * 2 * 19 * h->kp.N, cudaMemcpyHostToDevice,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return FLBM_OK;
+}
+
+int flbm_set_particle(flbm_t* h, const double X[3], const double V[3], const double Omega[3])
+{
+    if (!h || !X || !V || !Omega) return fail(h, FLBM_E_INVAL, "NULL argument");
+    if (!h->kp.has_particle) return fail(h, FLBM_E_UNSUPPORTED, "simulation has no particle");
+    for (int a = 0; a < 3; ++a) {
+        const int L[3] = {h->p.lx, h->p.ly, h->p.lz};
+        const int w[3] = {h->p.wall_x, h->p.wall_y, h->p.wall_z};
+        if (!std::isfinite(X[a]) || !std::isfinite(V[a]) || !std::isfinite(Omega[a]))
+            return fail(h, FLBM_E_INVAL, "non-finite particle state");
+        if (w[a] && (X[a] - h->p.radius < -0.5 || X[a] + h->p.radius > L[a] - 0.5))
+            return fail(h, FLBM_E_INVAL, "the sphere must lie inside the walls");
+    }
+    DevState s;
+    CK(h, cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int a = 0; a < 3; ++a) {
+        s.X[a] = X[a];
+        if (!h->p.wall_x && a == 0) s.X[a] -= h->p.lx * std::floor(s.X[a] / h->p.lx);
+        if (!h->p.wall_y && a == 1) s.X[a] -= h->p.ly * std::floor(s.X[a] / h->p.ly);
+        if (!h->p.wall_z && a == 2) s.X[a] -= h->p.lz * std::floor(s.X[a] / h->p.lz);
+        s.V[a] = V[a];
+        s.Om[a] = Omega[a];
+        s.Ppend[a] = s.Lpend[a] = 0.0;
+    }
+    s.delta[0] = s.delta[1] = 0.0;
+    CK(h, cudaMemcpyAsync(h->st, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+    k_mark<<<1, 1024, 0, h->stream>>>(h->st, h->masks, h->kp);
+    if (int rc = launch_check(h, "k_mark")) return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return FLBM_OK;
+}
+
+int flbm_run_host(flbm_t* h, const float* host_f_in, int64_t nsteps, float* host_f_out, flbm_particle* traj)
+{
+    if (!h || !host_f_in || nsteps < 0) return fail(h, FLBM_E_INVAL, "invalid argument");
+    const KParams& k = h->kp;
+    const size_t fbytes = sizeof(float) * 2 * 19 * k.N;
+    if (traj && (size_t)nsteps > h->traj_cap) {
+        if (h->traj_dev) cudaFree(h->traj_dev);
+        h->traj_dev = nullptr;
+        h->traj_cap = 0;
+        CK(h, cudaMalloc(&h->traj_dev, sizeof(DevState) * (size_t)nsteps));
+        h->traj_cap = (size_t)nsteps;
+    }
+    CK(h, cudaMemcpyAsync(h->fbuf[h->cur], host_f_in, fbytes, cudaMemcpyHostToDevice, h->stream));
+    int64_t launches = 0;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        h->launches = 0;
+        if (int rc = launch_step(h)) return rc;
+        launches += h->launches;
+        if (traj)
+            CK(h, cudaMemcpyAsync(h->traj_dev + s, h->st, sizeof(DevState), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    h->launches = launches;
+    if (host_f_out)
+        CK(h, cudaMemcpyAsync(host_f_out, h->fbuf[h->cur], fbytes, cudaMemcpyDeviceToHost, h->stream));
+    if (traj && nsteps > 0) {
+        if ((size_t)nsteps > h->traj_host_cap) {
+            delete[] h->traj_host;
+            h->traj_host = new (std::nothrow) DevState[(size_t)nsteps];
+            if (!h->traj_host) {
+                h->traj_host_cap = 0;
+                return fail(h, FLBM_E_NOMEM, "trajectory staging");
+            }
+            h->traj_host_cap = (size_t)nsteps;
+        }
+        CK(h, cudaMemcpyAsync(h->traj_host, h->traj_dev, sizeof(DevState) * (size_t)nsteps, cudaMemcpyDeviceToHost,
+                              h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (traj)
+        for (int64_t s = 0; s < nsteps; ++s) copy_particle(h->traj_host[s], traj + s);
+    return FLBM_OK;
+}
+
+int flbm_step_timed(flbm_t* h, int64_t nsteps, double* ms)
+{
+    if (!h || nsteps < 0 || !ms) return fail(h, FLBM_E_INVAL, "invalid argument");
+    const size_t need = (size_t)6 * (size_t)nsteps;
+    while (h->events.size() < need) {
+        cudaEvent_t e;
+        CK(h, cudaEventCreate(&e));
+        h->events.push_back(e);
+    }
+    h->launches = 0;
+    for (int64_t s = 0; s < nsteps; ++s)
+        if (int rc = launch_step(h, h->events.data() + 6 * s)) return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < FLBM_NKERNELS; ++k) ms[k] = 0.0;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        cudaEvent_t* ev = h->events.data() + 6 * s;
+        for (int k = 0; k < FLBM_NKERNELS; ++k) {
+            float t = 0.0f;
+            CK(h, cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+            ms[k] += t;
+        }
+    }
+    return FLBM_OK;
+}
+
+const char* flbm_kernel_name(int k)
+{
+    static const char* names[FLBM_NKERNELS] = {"k_density", "k_virtual", "k_shell", "k_collide", "k_particle"};
+    return (k >= 0 && k < FLBM_NKERNELS) ? names[k] : "";
+}
+
+int64_t flbm_last_launch_count(const flbm_t* h) { return h ? h->launches : 0; }
+
+void flbm_destroy(flbm_t* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(h->f_owned);
+    cudaFree(h->psi);
+    cudaFree(h->st);
+    cudaFree(h->masks);
+    cudaFree(h->partials);
+    cudaFree(h->obs_tiles);
+    cudaFree(h->obs_out);
+    cudaFree(h->scratch_rho);
+    cudaFree(h->traj_dev);
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    delete[] h->traj_host;
+    delete h;
+}
+
+const char* flbm_error_string(int code)
+{
+    switch (code) {
+    case FLBM_OK: return "FLBM_OK";
+    case FLBM_E_INVAL: return "FLBM_E_INVAL: invalid argument";
+    case FLBM_E_NOMEM: return "FLBM_E_NOMEM: allocation failed";
+    case FLBM_E_CUDA: return "FLBM_E_CUDA: CUDA error";
+    case FLBM_E_NONFINITE: return "FLBM_E_NONFINITE: non-finite state";
+    case FLBM_E_TIMEOUT: return "FLBM_E_TIMEOUT: device wait timed out";
+    case FLBM_E_UNSUPPORTED: return "FLBM_E_UNSUPPORTED: not supported";
+    }
+    return "unknown FLBM error code";
+}
+
+const char* flbm_last_error(const flbm_t* h) { return h ? h->err.c_str() : ""; }
+
+}  // extern "C"

@@ -1,0 +1,285 @@
+// Device code of the FLBM step: lattice, Philox, and the kernels.
+//
+// Method: arXiv:1909.01092, Section 2 (Eqs. (density), (lbe), (sc-force), the
+// particle coupling paragraph) and Section 3 (Eq. (fp), channel walls).
+//
+// Data layout in HBM (N = lx*ly*lz, x fastest):
+//   f[2 copies][2 components][19 directions][N]     float32, post-stream state
+//   psi[2 components][lz+2][ly+2][lx+2]              float32, densities with a
+//        one-node shell: copies across periodic faces, neutral wall ghosts
+//        across walled faces; virtual-layer values on particle surface nodes
+//   mask[2][B^3]                                     uint8, particle nodes in a
+//        cube of side B around the sphere (current and next position)
+//   partials[tiles][8]                               float64, per-tile force,
+//        torque and mass ledger of tiles next to the particle
+//   DevState                                         float64 particle state
+#pragma once
+
+#include <cstdint>
+
+namespace flbm {
+
+// ---------------------------------------------------------------------------
+// D3Q19 (Section 2). Direction order: rest, +-x, +-y, +-z, xy, xz, yz pairs.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cxv(int i)
+{
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+           : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cyv(int i)
+{
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+           : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int czv(int i)
+{
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+           : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int oppv(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr float wv(int i) { return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f); }
+
+// Norms b_k of the mode basis (sum_i w_i e_k(c_i)^2).
+__host__ __device__ constexpr float bnorm(int k)
+{
+    return k == 0 ? 1.0f
+           : k <= 3 ? 1.0f / 3.0f
+           : k == 4 ? 2.0f / 3.0f
+           : k == 5 ? 4.0f / 3.0f
+           : k == 6 ? 4.0f / 9.0f
+           : k <= 9 ? 1.0f / 9.0f
+           : k <= 12 ? 2.0f / 3.0f
+           : k <= 15 ? 2.0f / 9.0f
+           : k == 16 ? 2.0f
+           : k == 17 ? 4.0f / 3.0f : 4.0f / 9.0f;
+}
+
+// Forward mode transform m_k = sum_i e_k(c_i) f_i of the D3Q19 MRT basis
+// (density, momentum, 6 stress, 9 ghost modes), evaluated with opposite-pair
+// sums (even modes) and differences (odd modes).
+__device__ __forceinline__ void to_modes(const float f[19], float m[19])
+{
+    const float s1 = f[1] + f[2], d1 = f[1] - f[2];
+    const float s2 = f[3] + f[4], d2 = f[3] - f[4];
+    const float s3 = f[5] + f[6], d3 = f[5] - f[6];
+    const float s7 = f[7] + f[8], d7 = f[7] - f[8];
+    const float s9 = f[9] + f[10], d9 = f[9] - f[10];
+    const float s11 = f[11] + f[12], d11 = f[11] - f[12];
+    const float s13 = f[13] + f[14], d13 = f[13] - f[14];
+    const float s15 = f[15] + f[16], d15 = f[15] - f[16];
+    const float s17 = f[17] + f[18], d17 = f[17] - f[18];
+    const float sax = s1 + s2 + s3;
+    const float sxy = s7 + s9, sxz = s11 + s13, syz = s15 + s17;
+    const float sdg = sxy + sxz + syz;
+    m[0] = f[0] + sax + sdg;
+    m[1] = d1 + d7 + d9 + d11 + d13;
+    m[2] = d2 + d7 - d9 + d15 + d17;
+    m[3] = d3 + d11 - d13 + d15 - d17;
+    m[4] = sdg - f[0];
+    m[5] = 2.0f * s1 - s2 - s3 + sxy + sxz - 2.0f * syz;
+    m[6] = s2 - s3 + sxy - sxz;
+    m[7] = s7 - s9;
+    m[8] = s15 - s17;
+    m[9] = s11 - s13;
+    m[10] = -2.0f * d1 + d7 + d9 + d11 + d13;
+    m[11] = -2.0f * d2 + d7 - d9 + d15 + d17;
+    m[12] = -2.0f * d3 + d11 - d13 + d15 - d17;
+    m[13] = d7 + d9 - d11 - d13;
+    m[14] = -d7 + d9 + d15 + d17;
+    m[15] = d11 - d13 - d15 + d17;
+    m[16] = f[0] - 2.0f * sax + sdg;
+    m[17] = -2.0f * s1 + s2 + s3 + sxy + sxz - 2.0f * syz;
+    m[18] = -s2 + s3 + sxy - sxz;
+}
+
+// Back transform f_i = w_i sum_k e_k(c_i) n_k with n_k = m_k / b_k already
+// normalised, split into the even and odd parts of each opposite pair.
+__device__ __forceinline__ void from_modes(const float n[19], float f[19])
+{
+    const float k18 = 1.0f / 18.0f, k36 = 1.0f / 36.0f;
+    f[0] = (n[0] - n[4] + n[16]) * (1.0f / 3.0f);
+    const float ex = (n[0] + 2.0f * n[5] - 2.0f * n[16] - 2.0f * n[17]) * k18;
+    const float ox = (n[1] - 2.0f * n[10]) * k18;
+    const float ey = (n[0] - n[5] + n[6] - 2.0f * n[16] + n[17] - n[18]) * k18;
+    const float oy = (n[2] - 2.0f * n[11]) * k18;
+    const float ez = (n[0] - n[5] - n[6] - 2.0f * n[16] + n[17] + n[18]) * k18;
+    const float oz = (n[3] - 2.0f * n[12]) * k18;
+    const float cmn = n[0] + n[4] + n[16];
+    const float exy = cmn + n[5] + n[6] + n[17] + n[18];
+    const float exz = cmn + n[5] - n[6] + n[17] - n[18];
+    const float eyz = cmn - 2.0f * n[5] - 2.0f * n[17];
+    const float e7 = (exy + n[7]) * k36, e9 = (exy - n[7]) * k36;
+    const float o7 = (n[1] + n[2] + n[10] + n[11] + n[13] - n[14]) * k36;
+    const float o9 = (n[1] - n[2] + n[10] - n[11] + n[13] + n[14]) * k36;
+    const float e11 = (exz + n[9]) * k36, e13 = (exz - n[9]) * k36;
+    const float o11 = (n[1] + n[3] + n[10] + n[12] - n[13] + n[15]) * k36;
+    const float o13 = (n[1] - n[3] + n[10] - n[12] - n[13] - n[15]) * k36;
+    const float e15 = (eyz + n[8]) * k36, e17 = (eyz - n[8]) * k36;
+    const float o15 = (n[2] + n[3] + n[11] + n[12] + n[14] - n[15]) * k36;
+    const float o17 = (n[2] - n[3] + n[11] - n[12] + n[14] + n[15]) * k36;
+    f[1] = ex + ox; f[2] = ex - ox;
+    f[3] = ey + oy; f[4] = ey - oy;
+    f[5] = ez + oz; f[6] = ez - oz;
+    f[7] = e7 + o7; f[8] = e7 - o7;
+    f[9] = e9 + o9; f[10] = e9 - o9;
+    f[11] = e11 + o11; f[12] = e11 - o11;
+    f[13] = e13 + o13; f[14] = e13 - o13;
+    f[15] = e15 + o15; f[16] = e15 - o15;
+    f[17] = e17 + o17; f[18] = e17 - o17;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from its published
+// definition, and the open-interval uniform used by both the initial
+// perturbation and the thermal noise: ((x >> 9) + 1/2) * 2^-23, exact in
+// binary32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,
+                                              uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
+        const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+        const uint32_t y0 = hi1 ^ x1 ^ k0;
+        const uint32_t y2 = hi0 ^ x3 ^ k1;
+        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+__device__ __forceinline__ float uniform_open(uint32_t x)
+{
+    return __fmaf_rn((float)(x >> 9), 1.0f / 8388608.0f, 0.5f / 8388608.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Launch-invariant parameters (kernel argument, by value).
+// ---------------------------------------------------------------------------
+struct KParams {
+    int lx, ly, lz;
+    int wall[3];
+    int px, py, pz;        // padded psi dimensions lx+2, ly+2, lz+2
+    long long N;           // lx*ly*lz
+    long long padn;        // px*py*pz
+    int tx, ty;            // tile (block) shape in x, y; one z-plane per block
+    int gx, gy;            // tiles per axis in x, y
+    float G;
+    float gs, gd, gg;      // gamma = 1 - 1/tau of stress, component momentum, ghost modes
+    float ext[3];          // constant fluid body force density
+    float drho;            // wetting shift
+    float kT;
+    float nz_mode[19];     // sqrt((1 - gamma_k^2) / b_k) for k >= 4 (noise in normalised modes per sqrt(3 kT rho))
+    float nz_j;            // sqrt(1 - gamma_d^2)
+    uint32_t key0, key1;   // Philox key
+    int has_particle;
+    int B;                 // side of the particle box
+    double R;              // sphere radius
+    double rho0[2];        // initial densities (fallback for an uncovered node with no fluid neighbour)
+    int counterforce;
+};
+
+// Particle and bookkeeping state, kept in device memory (FP64).
+struct DevState {
+    double X[3], V[3], Vavg[3], Om[3], F[3], T[3], Ppend[3], Lpend[3];
+    double delta[2];       // per-node mass correction for the next collision
+    double fc;             // counterforce density along z on the fluid
+    double mp, Ip, Fp;
+    long long nfluid;
+    long long step;
+    int cur;               // index of the current mask
+    int box0[3];           // origin of the particle box (periodic axes in [0, L))
+    int err;
+    int pad_;
+};
+
+// Signed offset of box coordinate of lattice coordinate c on one axis.
+__device__ __forceinline__ int box_rel(int c, int o, int L, int wall)
+{
+    int t = c - o;
+    if (!wall && t < 0) t += L;
+    return t;
+}
+
+__device__ __forceinline__ bool in_box(int x, int y, int z, const int o[3], const KParams& P, int& bi)
+{
+    const int dx = box_rel(x, o[0], P.lx, P.wall[0]);
+    const int dy = box_rel(y, o[1], P.ly, P.wall[1]);
+    const int dz = box_rel(z, o[2], P.lz, P.wall[2]);
+    const int B = P.B;
+    if ((unsigned)dx >= (unsigned)B || (unsigned)dy >= (unsigned)B || (unsigned)dz >= (unsigned)B) return false;
+    bi = dx + B * (dy + B * dz);
+    return true;
+}
+
+__device__ __forceinline__ bool is_solid(int x, int y, int z, const int o[3], const uint8_t* mask, const KParams& P)
+{
+    int bi;
+    return in_box(x, y, z, o, P, bi) && mask[bi];
+}
+
+// Does [a0, a0+la) meet [b0, b0+lb) on an axis of length L (periodic: modulo L)?
+__device__ __forceinline__ bool ranges_meet(int a0, int la, int b0, int lb, int L, int wall)
+{
+    if (wall) return a0 < b0 + lb && b0 < a0 + la;
+    if (lb >= L) return true;
+    int d0 = (a0 - b0) % L;
+    if (d0 < 0) d0 += L;
+    return d0 < lb || d0 + la > L;
+}
+
+// Tile (bx, by, bz) meets the particle box grown by one node on every side:
+// only such tiles have fluid nodes whose stencil touches a particle node.
+__device__ __forceinline__ bool tile_near(int bx, int by, int bz, const int o[3], const KParams& P)
+{
+    const int x0 = bx * P.tx, y0 = by * P.ty;
+    const int lxr = min(P.tx, P.lx - x0), lyr = min(P.ty, P.ly - y0);
+    const int B2 = P.B + 2;
+    return ranges_meet(x0, lxr, o[0] - 1, B2, P.lx, P.wall[0]) &&
+           ranges_meet(y0, lyr, o[1] - 1, B2, P.ly, P.wall[1]) &&
+           ranges_meet(bz, 1, o[2] - 1, B2, P.lz, P.wall[2]);
+}
+
+__device__ __forceinline__ long long pad_index(int x, int y, int z, const KParams& P)
+{
+    return (long long)(x + 1) + (long long)P.px * ((y + 1) + (long long)P.py * (z + 1));
+}
+
+// Vector from the particle centre to point r, minimum image on periodic axes.
+__device__ __forceinline__ double rel_axis(double r, double X, int L, int wall)
+{
+    double d = r - X;
+    if (!wall) {
+        if (d > 0.5 * L) d -= L;
+        else if (d < -0.5 * L) d += L;
+    }
+    return d;
+}
+
+// Block-wide sum of 8 doubles into out[0..7] (thread 0 holds the result in
+// s_out). Fixed reduction tree: deterministic.
+template <int NT>
+__device__ __forceinline__ void block_sum8(double v[8], double* s_red, double* s_out)
+{
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarp = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        double a = v[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+        if (lane == 0) s_red[warp * 8 + k] = a;
+    }
+    __syncthreads();
+    if (tid < 8) {
+        double a = 0.0;
+        for (int w = 0; w < nwarp; ++w) a += s_red[w * 8 + tid];
+        s_out[tid] = a;
+    }
+    __syncthreads();
+}
+
+}  // namespace flbm
