@@ -182,6 +182,34 @@ const char* flbm_kernel_name(int k);
 /* Number of kernel launches the last flbm_step / flbm_step_timed / flbm_run_host issued. */
 int64_t flbm_last_launch_count(const flbm_t* h);
 
+/* Observables of a population field, allocating nothing.
+ *
+ * For callers that cannot allocate device memory: code whose device memory is
+ * owned by a pool or arena, host plugins that must not call cudaMalloc or
+ * cudaFree (cudaFree synchronises the device), or code that must not grow the
+ * process's device footprint after start-up. The paper has no counterpart:
+ * this is an alternative entry to the observables reduction of
+ * flbm_observables.
+ *   p       : parameters of the field (sizes and walls are used); the
+ *             simulation must have no particle (radius <= 0), else
+ *             FLBM_E_UNSUPPORTED.
+ *   f_dev   : device memory, 2*19*N float32 populations in the layout above.
+ *   out_dev : device memory for 8 doubles, written in stream order:
+ *             mass A, mass B, momentum x, y, z, kinetic energy, number of
+ *             non-finite populations, 0.
+ *   stream  : cudaStream_t (NULL: default stream). Asynchronous.
+ * Scratch: a file-scope device array of FLBM_NOALLOC_MAX_TILES x 8 doubles
+ * (2 MiB), held by every GPU that loads the library until the process exits.
+ * A lattice that needs more tiles (more than 128x128x512 nodes or equivalent)
+ * is rejected with FLBM_E_INVAL and a message on stderr. The first call on a
+ * device looks up the array's device address with that device current; make
+ * that first call before any stream capture. All calls share the array:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. Every scratch slot a call reads is
+ * written earlier in the same call, so no clearing is needed. */
+#define FLBM_NOALLOC_MAX_TILES 32768
+int flbm_observables_noalloc(const flbm_params* p, const float* f_dev, double* out_dev, void* stream);
+
 /* Release the handle and the device memory the library allocated. */
 void flbm_destroy(flbm_t* h);
 

@@ -23,7 +23,7 @@ EXPORTS = (
     "flbm_state_bytes", "flbm_create", "flbm_step", "flbm_particle_state", "flbm_observables",
     "flbm_read_fields", "flbm_write_fields", "flbm_set_particle", "flbm_run_host",
     "flbm_last_launch_count", "flbm_destroy", "flbm_error_string", "flbm_last_error",
-    "flbm_step_timed", "flbm_kernel_name",
+    "flbm_step_timed", "flbm_kernel_name", "flbm_observables_noalloc",
 )
 NKERNELS = 5
 
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
         lib.flbm_set_particle.argtypes = [vp, dp, dp, dp]
         lib.flbm_run_host.argtypes = [vp, fp, ctypes.c_int64, fp, ctypes.POINTER(Particle)]
         lib.flbm_step_timed.argtypes = [vp, ctypes.c_int64, dp]
+        lib.flbm_observables_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp]
         lib.flbm_kernel_name.restype = ctypes.c_char_p
         lib.flbm_kernel_name.argtypes = [ctypes.c_int]
         lib.flbm_last_launch_count.restype = ctypes.c_int64

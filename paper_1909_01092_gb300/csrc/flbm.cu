@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -523,3 +524,75 @@ const char* flbm_error_string(int code)
 const char* flbm_last_error(const flbm_t* h) { return h ? h->err.c_str() : ""; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Observables without any allocation.
+//
+// For callers that cannot allocate device memory themselves: code running
+// inside a memory pool or arena that owns every byte of the device, plugins
+// of host applications that forbid cudaMalloc/cudaFree on their streams, or
+// callers that must not synchronise the device (cudaFree does). They pass the
+// population field and a place for the result; the per-tile partial sums go
+// to the file-scope array below, which every GPU that loads this library
+// holds until the process exits.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_tiles[FLBM_NOALLOC_MAX_TILES * 8];
+
+namespace {
+
+// Device address of g_noalloc_tiles, looked up once per device on the first
+// call made with that device current (host code may not use the symbol
+// itself: in host code its name is only a stand-in, not a device address).
+struct NoallocSlot {
+    double* ptr = nullptr;
+    bool ready = false;
+};
+NoallocSlot g_noalloc_slots[64];
+std::mutex g_noalloc_mutex;
+
+}  // namespace
+
+extern "C" int flbm_observables_noalloc(const flbm_params* p, const float* f_dev, double* out_dev, void* stream)
+{
+    if (!p || !f_dev || !out_dev) return FLBM_E_INVAL;
+    if (p->lx < 1 || p->ly < 1 || p->lz < 1 || p->lz > 65535 ||
+        (double)p->lx * p->ly * p->lz > 4294967295.0) {
+        std::fprintf(stderr, "flbm_observables_noalloc: invalid lattice size\n");
+        return FLBM_E_INVAL;
+    }
+    if (p->radius > 0.0) {
+        std::fprintf(stderr, "flbm_observables_noalloc: only for simulations without a particle\n");
+        return FLBM_E_UNSUPPORTED;
+    }
+    flbm_sim tmp;  // launch geometry only; nothing is allocated
+    tmp.p = *p;
+    fill_kparams(&tmp);
+    if (tmp.ntiles > FLBM_NOALLOC_MAX_TILES) {
+        std::fprintf(stderr, "flbm_observables_noalloc: lattice needs %lld tiles, more than the %d of the static "
+                             "scratch (at most 128x128x512 nodes or equivalent)\n",
+                     tmp.ntiles, FLBM_NOALLOC_MAX_TILES);
+        return FLBM_E_INVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FLBM_E_CUDA;
+    double* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        NoallocSlot& s = g_noalloc_slots[dev];
+        if (!s.ready) {
+            void* ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_tiles) != cudaSuccess) return FLBM_E_CUDA;
+            s.ptr = (double*)ptr;
+            s.ready = true;
+        }
+        scratch = s.ptr;
+    }
+    // Every tile slot the final sum reads is written by k_obs_tiles in this
+    // same call, so nothing has to be cleared first.
+    cudaStream_t st = (cudaStream_t)stream;
+    k_obs_tiles<<<tmp.grid, tmp.block, 0, st>>>(f_dev, nullptr, nullptr, scratch, tmp.kp);
+    if (cudaGetLastError() != cudaSuccess) return FLBM_E_CUDA;
+    k_obs_final<<<1, 1024, 0, st>>>(scratch, tmp.ntiles, out_dev);
+    if (cudaGetLastError() != cudaSuccess) return FLBM_E_CUDA;
+    return FLBM_OK;
+}
