@@ -26,7 +26,11 @@ struct flbm_sim {
     float* psi = nullptr;
     DevState* st = nullptr;
     uint8_t* masks = nullptr;
-    double* partials = nullptr;
+    double* partials = nullptr;    // per candidate near tile: force, torque, ledger
+    int* box_counts = nullptr;      // per block of the particle box: particle nodes
+    double* box_parts = nullptr;    // per block of the particle box: cover/uncover sums
+    int box_blocks = 0;
+    long long ncand = 0;
     double* obs_tiles = nullptr;
     double* obs_out = nullptr;
     float* scratch_rho = nullptr;
@@ -134,6 +138,10 @@ void fill_kparams(flbm_sim* h)
     k.nz_j = (float)std::sqrt(1.0 - gd * gd);
     k.key0 = (uint32_t)(p.seed & 0xffffffffu);
     k.key1 = (uint32_t)(p.seed >> 32) ^ p.replica;
+    for (int r = 0; r < 10; ++r) {
+        k.rk0[r] = k.key0 + (uint32_t)r * 0x9E3779B9u;
+        k.rk1[r] = k.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     k.has_particle = p.radius > 0.0 ? 1 : 0;
     k.B = k.has_particle ? (int)std::ceil(2.0 * p.radius) + 2 : 1;
     k.R = p.radius;
@@ -142,6 +150,12 @@ void fill_kparams(flbm_sim* h)
     h->block = dim3(k.tx, k.ty, 1);
     h->grid = dim3(k.gx, k.gy, p.lz);
     h->ntiles = (long long)k.gx * k.gy * p.lz;
+    // Candidate tiles that can meet the particle box grown by one node.
+    k.ncx = std::min(k.gx, (k.B + 2 + k.tx - 1) / k.tx + 2);
+    k.ncy = std::min(k.gy, (k.B + 2 + k.ty - 1) / k.ty + 2);
+    k.ncz = std::min(p.lz, k.B + 2);
+    h->ncand = (long long)k.ncx * k.ncy * k.ncz;
+    h->box_blocks = (k.B * k.B * k.B + 255) / 256;
 }
 
 int launch_check(flbm_sim* h, const char* what)
@@ -180,7 +194,7 @@ int launch_psi(flbm_sim* h, const float* f, cudaEvent_t* ev = nullptr)
     return FLBM_OK;
 }
 
-// One time step. With ev, events ev[0..5] bracket its five kernels.
+// One time step. With ev, events ev[0..5] bracket its five kernel classes.
 int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
 {
     const KParams& k = h->kp;
@@ -189,18 +203,30 @@ int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
     if (int rc = launch_psi(h, fin, ev)) return rc;
     const bool noise = k.kT > 0.0f;
     const bool part = k.has_particle != 0;
-    if (noise && part)
-        k_collide<true, true><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks, h->partials, k);
-    else if (noise)
-        k_collide<true, false><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks, h->partials, k);
-    else if (part)
-        k_collide<false, true><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks, h->partials, k);
+    if (noise)
+        k_collide_bulk<true><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, k);
     else
-        k_collide<false, false><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks, h->partials, k);
-    if (int rc = launch_check(h, "k_collide")) return rc;
+        k_collide_bulk<false><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, k);
+    if (int rc = launch_check(h, "k_collide_bulk")) return rc;
+    if (part) {
+        const dim3 g(k.ncx, k.ncy, k.ncz);
+        if (noise)
+            k_collide_near<true><<<g, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks, h->partials, k);
+        else
+            k_collide_near<false><<<g, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks, h->partials, k);
+        if (int rc = launch_check(h, "k_collide_near")) return rc;
+    }
     record(h, ev, 4);
-    k_particle<<<1, 1024, 0, h->stream>>>(fout, h->st, h->masks, h->partials, k);
-    if (int rc = launch_check(h, "k_particle")) return rc;
+    if (part) {
+        k_update<<<1, 256, 0, h->stream>>>(h->st, h->partials, k);
+        if (int rc = launch_check(h, "k_update")) return rc;
+        k_mark_next<<<h->box_blocks, 256, 0, h->stream>>>(h->st, h->masks, h->box_counts, k);
+        if (int rc = launch_check(h, "k_mark_next")) return rc;
+        k_cover<<<h->box_blocks, 256, 0, h->stream>>>(fout, h->st, h->masks, h->box_parts, k);
+        if (int rc = launch_check(h, "k_cover")) return rc;
+    }
+    k_finish<<<1, 256, 0, h->stream>>>(h->st, h->box_counts, h->box_parts, h->box_blocks, k);
+    if (int rc = launch_check(h, "k_finish")) return rc;
     record(h, ev, 5);
     h->cur = 1 - h->cur;
     return FLBM_OK;
@@ -267,7 +293,9 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
     if (cudaMalloc(&h->psi, sizeof(float) * 2 * k.padn) != cudaSuccess ||
         cudaMalloc(&h->st, sizeof(DevState)) != cudaSuccess ||
         cudaMalloc(&h->masks, 2 * B3) != cudaSuccess ||
-        cudaMalloc(&h->partials, sizeof(double) * 8 * h->ntiles) != cudaSuccess ||
+        cudaMalloc(&h->partials, sizeof(double) * 8 * h->ncand) != cudaSuccess ||
+        cudaMalloc(&h->box_counts, sizeof(int) * h->box_blocks) != cudaSuccess ||
+        cudaMalloc(&h->box_parts, sizeof(double) * 8 * h->box_blocks) != cudaSuccess ||
         cudaMalloc(&h->obs_tiles, sizeof(double) * 8 * h->ntiles) != cudaSuccess ||
         cudaMalloc(&h->obs_out, sizeof(double) * 8) != cudaSuccess)
         return bail(FLBM_E_NOMEM);
@@ -289,7 +317,9 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
         return bail(FLBM_E_CUDA);
     if (cudaMemsetAsync(h->masks, 0, 2 * B3, h->stream) != cudaSuccess) return bail(FLBM_E_CUDA);
     if (cudaMemsetAsync(h->psi, 0, sizeof(float) * 2 * k.padn, h->stream) != cudaSuccess) return bail(FLBM_E_CUDA);
-    if (cudaMemsetAsync(h->partials, 0, sizeof(double) * 8 * h->ntiles, h->stream) != cudaSuccess)
+    if (cudaMemsetAsync(h->partials, 0, sizeof(double) * 8 * h->ncand, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->box_counts, 0, sizeof(int) * h->box_blocks, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->box_parts, 0, sizeof(double) * 8 * h->box_blocks, h->stream) != cudaSuccess)
         return bail(FLBM_E_CUDA);
     k_init<<<h->grid, h->block, 0, h->stream>>>(h->fbuf[0], k, (float)p->rho_a0, (float)p->rho_b0,
                                                  (float)p->init_pert);
@@ -498,6 +528,8 @@ void flbm_destroy(flbm_t* h)
     cudaFree(h->st);
     cudaFree(h->masks);
     cudaFree(h->partials);
+    cudaFree(h->box_counts);
+    cudaFree(h->box_parts);
     cudaFree(h->obs_tiles);
     cudaFree(h->obs_out);
     cudaFree(h->scratch_rho);

@@ -174,6 +174,8 @@ struct KParams {
     float nz_mode[19];     // sqrt((1 - gamma_k^2) / b_k) for k >= 4 (noise in normalised modes per sqrt(3 kT rho))
     float nz_j;            // sqrt(1 - gamma_d^2)
     uint32_t key0, key1;   // Philox key
+    uint32_t rk0[10], rk1[10];  // Philox round keys key + r * (0x9E3779B9, 0xBB67AE85)
+    int ncx, ncy, ncz;     // candidate tiles per axis around the particle box
     int has_particle;
     int B;                 // side of the particle box
     double R;              // sphere radius
@@ -189,11 +191,17 @@ struct DevState {
     double mp, Ip, Fp;
     long long nfluid;
     long long step;
+    double ledger_bb[2];   // mass removed by the moving-wall term this step
+    float delta_f[2];      // delta as float, read by the collide kernels
+    float fc_f;            // fc as float
+    uint32_t step_u32;     // step as the 32-bit Philox counter word
     int cur;               // index of the current mask
     int box0[3];           // origin of the particle box (periodic axes in [0, L))
+    int box_next[3];       // origin at the position after this step's update
     int err;
-    int pad_;
 };
+
+constexpr int kThreadsStep = 256;
 
 // Signed offset of box coordinate of lattice coordinate c on one axis.
 __device__ __forceinline__ int box_rel(int c, int o, int L, int wall)

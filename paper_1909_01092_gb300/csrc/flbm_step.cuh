@@ -1,0 +1,611 @@
+// The collide-stream kernels and the particle update of one FLBM step
+// (arXiv:1909.01092, Section 2: Eq. (lbe), Eq. (sc-force), particle coupling;
+// Section 3: Eq. (fp), channel walls).
+//
+// Tiles (TX x TY nodes of one z-plane, one CTA each) split into two sets:
+//   bulk tiles  : no node of the tile or its one-node halo is a particle node;
+//                 k_collide_bulk runs them with no particle code at all.
+//   near tiles  : the tile meets the particle box grown by one node;
+//                 k_collide_near runs them over a fixed grid of candidates
+//                 around the box and reduces force, torque and mass ledger.
+// Both kernels apply the same tile_near() test, so every tile runs exactly once.
+// The particle update then runs as four small kernels (update, mark, cover,
+// finish) spread over the particle box instead of one serial block.
+#pragma once
+
+#include "flbm_device.cuh"
+
+namespace flbm {
+
+// Philox4x32-10 with the round keys precomputed on the host (key + r * Weyl).
+__device__ __forceinline__ void philox_rk(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, const KParams& P)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * x0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * x2;
+        const uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ P.rk0[r];
+        const uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ P.rk1[r];
+        x0 = y0;
+        x1 = (uint32_t)p1;
+        x2 = y2;
+        x3 = (uint32_t)p0;
+    }
+}
+
+// Box-Muller pair from two Philox words with the hardware approximations of
+// log2, rsqrt, sin and cos: z0 = r cos(2 pi u2), z1 = r sin(2 pi u2) with
+// r = sqrt(-2 ln u1); the angle is taken as 2 pi (u2 - 1/2) in (-pi, pi),
+// where the approximations are accurate, and the signs flipped back.
+__device__ __forceinline__ void box_muller(uint32_t w1, uint32_t w2, float& z0, float& z1)
+{
+    const float u1 = uniform_open(w1);
+    const float u2 = uniform_open(w2);
+    const float e = -1.38629436112f * __log2f(u1);  // -2 ln u1 > 0
+    const float r = e * rsqrtf(e);
+    float s, c;
+    __sincosf(6.28318530718f * (u2 - 0.5f), &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
+}
+
+// Collision and push-streaming of one fluid node (Eq. (lbe)). With PARTICLE,
+// solid_nb marks the directions whose neighbour is a particle node; their
+// links take the moving rule and feed acc = (F[3], T[3], ledger[2]).
+template <bool NOISE, bool PARTICLE>
+__device__ __forceinline__ void collide_node(int x, int y, int z, long long n, const float* __restrict__ fin,
+                                             float* __restrict__ fout, const float* __restrict__ psi,
+                                             const DevState* __restrict__ st, const KParams& P, uint32_t solid_nb,
+                                             double* acc)
+{
+    const long long N = P.N;
+    float ma[19], mb[19];
+    {
+        float fa[19], fb[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            fa[i] = __ldg(fin + (long long)i * N + n);
+            fb[i] = __ldg(fin + (long long)(19 + i) * N + n);
+        }
+        to_modes(fa, ma);
+        to_modes(fb, mb);
+    }
+    const float rhoA = ma[0], rhoB = mb[0];
+    const float rt = rhoA + rhoB;
+
+    // Shan-Chen force, Eq. (sc-force), omega_i = w_i, psi = rho.
+    float ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
+    {
+        const float* pA = psi + pad_index(x, y, z, P);
+        const float* pB = pA + P.padn;
+        const long long sy = P.px, sz = (long long)P.px * P.py;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const long long off = cxv(i) + sy * cyv(i) + sz * czv(i);
+            const float pa = __ldg(pA + off);
+            const float pb = __ldg(pB + off);
+            const float w = wv(i);
+            if (cxv(i)) { ga[0] += (cxv(i) * w) * pb; gb[0] += (cxv(i) * w) * pa; }
+            if (cyv(i)) { ga[1] += (cyv(i) * w) * pb; gb[1] += (cyv(i) * w) * pa; }
+            if (czv(i)) { ga[2] += (czv(i) * w) * pb; gb[2] += (czv(i) * w) * pa; }
+            if (PARTICLE && (solid_nb >> i & 1u)) {
+                // Reaction on the particle of this pair force (virtual layer).
+                const double mag = (double)P.G * w * ((double)rhoA * pb + (double)rhoB * pa);
+                const double fr[3] = {mag * cxv(i), mag * cyv(i), mag * czv(i)};
+                const double r[3] = {rel_axis(x + 0.5 * cxv(i), st->X[0], P.lx, P.wall[0]),
+                                     rel_axis(y + 0.5 * cyv(i), st->X[1], P.ly, P.wall[1]),
+                                     rel_axis(z + 0.5 * czv(i), st->X[2], P.lz, P.wall[2])};
+                acc[0] += fr[0]; acc[1] += fr[1]; acc[2] += fr[2];
+                acc[3] += r[1] * fr[2] - r[2] * fr[1];
+                acc[4] += r[2] * fr[0] - r[0] * fr[2];
+                acc[5] += r[0] * fr[1] - r[1] * fr[0];
+            }
+        }
+    }
+    const float irt = 1.0f / rt;
+    float ext[3] = {P.ext[0], P.ext[1], P.ext[2]};
+    if (P.counterforce) ext[2] += st->fc_f;
+    float FA[3], FB[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        FA[a] = -P.G * rhoA * ga[a] + rhoA * irt * ext[a];
+        FB[a] = -P.G * rhoB * gb[a] + rhoB * irt * ext[a];
+    }
+    // Hydrodynamical velocity v^(H) = (sum_l j_l + (F_A + F_B)/2) / rho_tot.
+    float u[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = (ma[1 + a] + mb[1 + a] + 0.5f * (FA[a] + FB[a])) * irt;
+    const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+
+    // MRT relaxation of each component in moment space, then n_k = m_k / b_k.
+    auto relax = [&](float* m, float rl, const float* Fl, float delta) {
+        const float uF = u[0] * Fl[0] + u[1] * Fl[1] + u[2] * Fl[2];
+        const float h = 0.5f * (1.0f + P.gs);
+        m[0] = rl + delta;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            m[1 + a] = rl * u[a] + P.gd * (m[1 + a] + 0.5f * Fl[a] - rl * u[a]) + 0.5f * Fl[a];
+        const float meq[6] = {rl * uu, rl * (3.0f * u[0] * u[0] - uu), rl * (u[1] * u[1] - u[2] * u[2]),
+                              rl * u[0] * u[1], rl * u[1] * u[2], rl * u[0] * u[2]};
+        const float S[6] = {2.0f * uF, 2.0f * (3.0f * u[0] * Fl[0] - uF), 2.0f * (u[1] * Fl[1] - u[2] * Fl[2]),
+                            u[0] * Fl[1] + u[1] * Fl[0], u[1] * Fl[2] + u[2] * Fl[1], u[0] * Fl[2] + u[2] * Fl[0]};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) m[4 + k] = meq[k] + P.gs * (m[4 + k] - meq[k]) + h * S[k];
+#pragma unroll
+        for (int k = 10; k < 19; ++k) m[k] *= P.gg;
+#pragma unroll
+        for (int k = 0; k < 19; ++k) m[k] *= 1.0f / bnorm(k);
+    };
+    relax(ma, rhoA, FA, st->delta_f[0]);
+    relax(mb, rhoB, FB, st->delta_f[1]);
+
+    if (NOISE) {
+        // 33 normals from 9 Philox blocks with counter (step, node, block, 0):
+        // A modes 4..18, B modes 4..18, interdiffusion J_x, J_y, J_z.
+        const float sA = sqrtf(3.0f * P.kT * fmaxf(rhoA, 0.0f));
+        const float sB = sqrtf(3.0f * P.kT * fmaxf(rhoB, 0.0f));
+        const float sJ = 3.0f * P.nz_j * sqrtf(P.kT * fmaxf(rhoA, 0.0f) * fmaxf(rhoB, 0.0f) * fmaxf(irt, 0.0f));
+        const uint32_t stp = st->step_u32;
+#pragma unroll
+        for (int blk = 0; blk < 9; ++blk) {
+            uint32_t r0 = stp, r1 = (uint32_t)n, r2 = (uint32_t)blk, r3 = 0u;
+            philox_rk(r0, r1, r2, r3, P);
+            float zn[4];
+            box_muller(r0, r1, zn[0], zn[1]);
+            box_muller(r2, r3, zn[2], zn[3]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int idx = 4 * blk + q;
+                if (idx < 15) ma[4 + idx] += sA * P.nz_mode[4 + idx] * zn[q];
+                else if (idx < 30) mb[4 + idx - 15] += sB * P.nz_mode[4 + idx - 15] * zn[q];
+                else if (idx < 33) {
+                    ma[1 + idx - 30] += sJ * zn[q];
+                    mb[1 + idx - 30] -= sJ * zn[q];
+                }
+            }
+        }
+    }
+
+    // Neighbour offsets; a wall on a side is flagged instead.
+    const int L[3] = {P.lx, P.ly, P.lz};
+    const int crd[3] = {x, y, z};
+    const long long stride[3] = {1, (long long)P.lx, (long long)P.lx * P.ly};
+    long long offp[3], offm[3];
+    int wallp = 0, wallm = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        offp[a] = stride[a];
+        offm[a] = -stride[a];
+        if (crd[a] + 1 >= L[a]) {
+            if (P.wall[a]) wallp |= 1 << a;
+            else offp[a] = stride[a] * (1 - L[a]);
+        }
+        if (crd[a] - 1 < 0) {
+            if (P.wall[a]) wallm |= 1 << a;
+            else offm[a] = stride[a] * (L[a] - 1);
+        }
+    }
+
+    // Back-transform and push each component (Eq. (lbe) streaming; halfway
+    // bounce-back at walls; moving link rule at the particle).
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        float fo[19];
+        from_modes(l == 0 ? ma : mb, fo);
+        const float rl = l == 0 ? rhoA : rhoB;
+        float* out = fout + (long long)(19 * l) * N;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const int cx = cxv(i), cy = cyv(i), cz = czv(i);
+            const bool wall = (cx > 0 && (wallp & 1)) || (cx < 0 && (wallm & 1)) || (cy > 0 && (wallp & 2)) ||
+                              (cy < 0 && (wallm & 2)) || (cz > 0 && (wallp & 4)) || (cz < 0 && (wallm & 4));
+            if (wall) {
+                out[(long long)oppv(i) * N + n] = fo[i];
+                continue;
+            }
+            if (PARTICLE && (solid_nb >> i & 1u)) {
+                // f_{-i}(x, t+1) = f*_i(x) - 6 w_i rho_l (u_b . c_i), u_b at the link midpoint.
+                const double r[3] = {rel_axis(x + 0.5 * cx, st->X[0], P.lx, P.wall[0]),
+                                     rel_axis(y + 0.5 * cy, st->X[1], P.ly, P.wall[1]),
+                                     rel_axis(z + 0.5 * cz, st->X[2], P.lz, P.wall[2])};
+                const double ub[3] = {st->V[0] + st->Om[1] * r[2] - st->Om[2] * r[1],
+                                      st->V[1] + st->Om[2] * r[0] - st->Om[0] * r[2],
+                                      st->V[2] + st->Om[0] * r[1] - st->Om[1] * r[0]};
+                const float ubc = (float)(ub[0] * cx + ub[1] * cy + ub[2] * cz);
+                const float corr = 6.0f * wv(i) * rl * ubc;
+                const float back = fo[i] - corr;
+                out[(long long)oppv(i) * N + n] = back;
+                const double dp = (double)fo[i] + (double)back;
+                const double fr[3] = {dp * cx, dp * cy, dp * cz};
+                acc[0] += fr[0]; acc[1] += fr[1]; acc[2] += fr[2];
+                acc[3] += r[1] * fr[2] - r[2] * fr[1];
+                acc[4] += r[2] * fr[0] - r[0] * fr[2];
+                acc[5] += r[0] * fr[1] - r[1] * fr[0];
+                acc[6 + l] += corr;
+                continue;
+            }
+            long long d = n;
+            if (cx > 0) d += offp[0]; else if (cx < 0) d += offm[0];
+            if (cy > 0) d += offp[1]; else if (cy < 0) d += offm[1];
+            if (cz > 0) d += offp[2]; else if (cz < 0) d += offm[2];
+            out[(long long)i * N + d] = fo[i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bulk tiles: every tile not next to the particle.
+// ---------------------------------------------------------------------------
+template <bool NOISE>
+__global__ void __launch_bounds__(kThreadsStep, 2)
+    k_collide_bulk(const float* __restrict__ fin, float* __restrict__ fout, const float* __restrict__ psi,
+                   const DevState* __restrict__ st, KParams P)
+{
+    if (P.has_particle) {
+        const int o[3] = {st->box0[0], st->box0[1], st->box0[2]};
+        if (tile_near(blockIdx.x, blockIdx.y, blockIdx.z, o, P)) return;
+    }
+    const int x = blockIdx.x * P.tx + threadIdx.x;
+    const int y = blockIdx.y * P.ty + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= P.lx || y >= P.ly) return;
+    const long long n = x + (long long)P.lx * (y + (long long)P.ly * z);
+    collide_node<NOISE, false>(x, y, z, n, fin, fout, psi, st, P, 0u, nullptr);
+}
+
+// Candidate c on one axis -> tile index, or -1. e0 = first coordinate of the
+// grown box on that axis; tiles of size T, gt of them, axis length L.
+__device__ __forceinline__ int candidate_tile(int c, int o, int T, int gt, int L, int wall)
+{
+    int e0 = o - 1;
+    if (wall) {
+        if (e0 < 0) e0 = 0;
+        const int t = e0 / T + c;
+        return t < gt ? t : -1;
+    }
+    if (e0 < 0) e0 += L;
+    return (e0 / T + c) % gt;
+}
+
+// ---------------------------------------------------------------------------
+// Near tiles: a fixed grid of candidate tiles around the particle box; each
+// near tile reduces force, torque and mass ledger into partials[candidate].
+// ---------------------------------------------------------------------------
+template <bool NOISE>
+__global__ void __launch_bounds__(kThreadsStep)
+    k_collide_near(const float* __restrict__ fin, float* __restrict__ fout, const float* __restrict__ psi,
+                   const DevState* __restrict__ st, const uint8_t* __restrict__ masks,
+                   double* __restrict__ partials, KParams P)
+{
+    __shared__ double s_red[(kThreadsStep / 32) * 8];
+    __shared__ double s_out[8];
+    const int o[3] = {st->box0[0], st->box0[1], st->box0[2]};
+    const int bx = candidate_tile(blockIdx.x, o[0], P.tx, P.gx, P.lx, P.wall[0]);
+    const int by = candidate_tile(blockIdx.y, o[1], P.ty, P.gy, P.ly, P.wall[1]);
+    const int bz = candidate_tile(blockIdx.z, o[2], 1, P.lz, P.lz, P.wall[2]);
+    const long long cand = blockIdx.x + (long long)P.ncx * (blockIdx.y + (long long)P.ncy * blockIdx.z);
+    const bool near = bx >= 0 && by >= 0 && bz >= 0 && tile_near(bx, by, bz, o, P);
+    if (!near) {
+        if (threadIdx.x < 8 && threadIdx.y == 0) partials[cand * 8 + threadIdx.x] = 0.0;
+        return;
+    }
+    const uint8_t* mask = masks + (size_t)st->cur * P.B * P.B * P.B;
+    const int x = bx * P.tx + threadIdx.x;
+    const int y = by * P.ty + threadIdx.y;
+    const int z = bz;
+    const bool inside = x < P.lx && y < P.ly;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (inside && !is_solid(x, y, z, o, mask, P)) {
+        const int L[3] = {P.lx, P.ly, P.lz};
+        uint32_t solid_nb = 0;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            int q[3] = {x + cxv(i), y + cyv(i), z + czv(i)};
+            bool ok = true;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (q[a] < 0 || q[a] >= L[a]) {
+                    if (P.wall[a]) ok = false;
+                    else q[a] += (q[a] < 0) ? L[a] : -L[a];
+                }
+            }
+            if (ok && is_solid(q[0], q[1], q[2], o, mask, P)) solid_nb |= 1u << i;
+        }
+        const long long n = x + (long long)P.lx * (y + (long long)P.ly * z);
+        collide_node<NOISE, true>(x, y, z, n, fin, fout, psi, st, P, solid_nb, acc);
+    }
+    block_sum8<kThreadsStep>(acc, s_red, s_out);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) partials[cand * 8 + k] = s_out[k];
+    }
+}
+
+__device__ __forceinline__ void box_origin(const double X[3], const KParams& P, int o[3])
+{
+    const int L[3] = {P.lx, P.ly, P.lz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int v = (int)floor(X[a] - P.R);
+        if (!P.wall[a]) {
+            v %= L[a];
+            if (v < 0) v += L[a];
+        }
+        o[a] = v;
+    }
+}
+
+// Particle node test for box entry t of a box at origin o around centre X (FP64).
+__device__ __forceinline__ bool box_node_inside(int t, const int o[3], const double X[3], const KParams& P)
+{
+    const int B = P.B;
+    const int d[3] = {t % B, (t / B) % B, t / (B * B)};
+    const int L[3] = {P.lx, P.ly, P.lz};
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int c = o[a] + d[a];
+        if (P.wall[a]) {
+            if (c < 0 || c >= L[a]) return false;
+        } else if (c >= L[a]) {
+            c -= L[a];
+        }
+        const double r = rel_axis((double)c, X[a], L[a], P.wall[a]);
+        s += r * r;
+    }
+    return s < P.R * P.R;
+}
+
+// ---------------------------------------------------------------------------
+// (1) Sum the near-tile partials in candidate order, leap-frog update (FP64),
+// new box origin. One block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_update(DevState* __restrict__ st, const double* __restrict__ partials,
+                                                KParams P)
+{
+    __shared__ double s_red[(256 / 32) * 8];
+    __shared__ double s_out[8];
+    const long long ncand = (long long)P.ncx * P.ncy * P.ncz;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long c = threadIdx.x; c < ncand; c += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += partials[c * 8 + k];
+    block_sum8<256>(acc, s_red, s_out);
+    if (threadIdx.x != 0) return;
+    const int L[3] = {P.lx, P.ly, P.lz};
+    for (int a = 0; a < 3; ++a) {
+        st->F[a] = s_out[a] + st->Ppend[a];
+        st->T[a] = s_out[3 + a] + st->Lpend[a];
+    }
+    for (int a = 0; a < 3; ++a) {
+        const double ext = (a == 2) ? st->Fp : 0.0;
+        const double vn = st->V[a] + (st->F[a] + ext) / st->mp;
+        st->Vavg[a] = 0.5 * (st->V[a] + vn);
+        st->V[a] = vn;
+        st->Om[a] += st->T[a] / st->Ip;
+        double xn = st->X[a] + vn;
+        if (!P.wall[a]) xn -= L[a] * floor(xn / L[a]);
+        st->X[a] = xn;
+    }
+    st->ledger_bb[0] = s_out[6];
+    st->ledger_bb[1] = s_out[7];
+    int o[3];
+    box_origin(st->X, P, o);
+    st->box_next[0] = o[0]; st->box_next[1] = o[1]; st->box_next[2] = o[2];
+}
+
+// (2) Particle nodes at the new position -> mask[1 - cur]; per-block counts.
+__global__ void __launch_bounds__(256) k_mark_next(const DevState* __restrict__ st, uint8_t* __restrict__ masks,
+                                                   int* __restrict__ counts, KParams P)
+{
+    __shared__ int s_cnt[256 / 32];
+    const int B3 = P.B * P.B * P.B;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int o[3] = {st->box_next[0], st->box_next[1], st->box_next[2]};
+    const double X[3] = {st->X[0], st->X[1], st->X[2]};
+    int in = 0;
+    if (t < B3) {
+        in = box_node_inside(t, o, X, P) ? 1 : 0;
+        masks[(size_t)(1 - st->cur) * B3 + t] = (uint8_t)in;
+    }
+    int c = __reduce_add_sync(0xffffffffu, in);
+    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a = 0;
+        for (int w = 0; w < 256 / 32; ++w) a += s_cnt[w];
+        counts[blockIdx.x] = a;
+    }
+}
+
+// (3) Cover (new box) and uncover (old box) on the post-stream populations f;
+// per-block FP64 partials of impulse, angular impulse and mass ledger.
+__global__ void __launch_bounds__(256) k_cover(float* __restrict__ f, const DevState* __restrict__ st,
+                                               const uint8_t* __restrict__ masks, double* __restrict__ parts,
+                                               KParams P)
+{
+    __shared__ double s_red[(256 / 32) * 8];
+    __shared__ double s_out[8];
+    const int B = P.B;
+    const int B3 = B * B * B;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cur = st->cur;
+    const int o_old[3] = {st->box0[0], st->box0[1], st->box0[2]};
+    const int o_new[3] = {st->box_next[0], st->box_next[1], st->box_next[2]};
+    const uint8_t* m_old = masks + (size_t)cur * B3;
+    const uint8_t* m_new = masks + (size_t)(1 - cur) * B3;
+    const int L[3] = {P.lx, P.ly, P.lz};
+    const long long N = P.N;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (t < B3) {
+        const int d[3] = {t % B, (t / B) % B, t / (B * B)};
+        if (m_new[t]) {  // covered: particle node now, fluid before
+            int c[3];
+            for (int a = 0; a < 3; ++a) {
+                c[a] = o_new[a] + d[a];
+                if (!P.wall[a] && c[a] >= L[a]) c[a] -= L[a];
+            }
+            if (!is_solid(c[0], c[1], c[2], o_old, m_old, P)) {
+                const long long n = c[0] + (long long)P.lx * (c[1] + (long long)P.ly * c[2]);
+                double j[3] = {0, 0, 0}, rl[2] = {0, 0};
+                for (int l = 0; l < 2; ++l)
+                    for (int i = 0; i < 19; ++i) {
+                        const double fv = f[(long long)(19 * l + i) * N + n];
+                        rl[l] += fv;
+                        j[0] += fv * cxv(i); j[1] += fv * cyv(i); j[2] += fv * czv(i);
+                    }
+                double r[3];
+                for (int a = 0; a < 3; ++a) r[a] = rel_axis((double)c[a], st->X[a], L[a], P.wall[a]);
+                acc[0] += j[0]; acc[1] += j[1]; acc[2] += j[2];
+                acc[3] += r[1] * j[2] - r[2] * j[1];
+                acc[4] += r[2] * j[0] - r[0] * j[2];
+                acc[5] += r[0] * j[1] - r[1] * j[0];
+                acc[6] += rl[0];
+                acc[7] += rl[1];
+            }
+        }
+        if (m_old[t]) {  // uncovered: particle node before, fluid now
+            int c[3];
+            for (int a = 0; a < 3; ++a) {
+                c[a] = o_old[a] + d[a];
+                if (!P.wall[a] && c[a] >= L[a]) c[a] -= L[a];
+            }
+            if (!is_solid(c[0], c[1], c[2], o_new, m_new, P)) {
+                double mean[2] = {0.0, 0.0};
+                int cnt = 0;
+                for (int jd = 1; jd < 19; ++jd) {
+                    int q[3] = {c[0] + cxv(jd), c[1] + cyv(jd), c[2] + czv(jd)};
+                    bool ok = true;
+                    for (int a = 0; a < 3; ++a) {
+                        if (q[a] < 0 || q[a] >= L[a]) {
+                            if (P.wall[a]) ok = false;
+                            else q[a] += (q[a] < 0) ? L[a] : -L[a];
+                        }
+                    }
+                    if (!ok) continue;
+                    if (is_solid(q[0], q[1], q[2], o_new, m_new, P)) continue;
+                    if (is_solid(q[0], q[1], q[2], o_old, m_old, P)) continue;  // uncovered too
+                    const long long m = q[0] + (long long)P.lx * (q[1] + (long long)P.ly * q[2]);
+                    for (int l = 0; l < 2; ++l) {
+                        double s = 0.0;
+                        for (int i = 0; i < 19; ++i) s += f[(long long)(19 * l + i) * N + m];
+                        mean[l] += s;
+                    }
+                    ++cnt;
+                }
+                // neighbour-mean densities; the initial densities if no fluid neighbour is left
+                const double rls[2] = {cnt ? mean[0] / cnt : P.rho0[0], cnt ? mean[1] / cnt : P.rho0[1]};
+                double r[3];
+                for (int a = 0; a < 3; ++a) r[a] = rel_axis((double)c[a], st->X[a], L[a], P.wall[a]);
+                const double ub[3] = {st->V[0] + st->Om[1] * r[2] - st->Om[2] * r[1],
+                                      st->V[1] + st->Om[2] * r[0] - st->Om[0] * r[2],
+                                      st->V[2] + st->Om[0] * r[1] - st->Om[1] * r[0]};
+                const long long n = c[0] + (long long)P.lx * (c[1] + (long long)P.ly * c[2]);
+                const double uu = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+                double pm[3] = {0, 0, 0};
+                for (int l = 0; l < 2; ++l) {
+                    for (int i = 0; i < 19; ++i) {
+                        const double cu = ub[0] * cxv(i) + ub[1] * cyv(i) + ub[2] * czv(i);
+                        f[(long long)(19 * l + i) * N + n] =
+                            (float)(wv(i) * rls[l] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+                    }
+                    pm[0] += rls[l] * ub[0]; pm[1] += rls[l] * ub[1]; pm[2] += rls[l] * ub[2];
+                }
+                acc[0] -= pm[0]; acc[1] -= pm[1]; acc[2] -= pm[2];
+                acc[3] -= r[1] * pm[2] - r[2] * pm[1];
+                acc[4] -= r[2] * pm[0] - r[0] * pm[2];
+                acc[5] -= r[0] * pm[1] - r[1] * pm[0];
+                acc[6] -= rls[0];
+                acc[7] -= rls[1];
+            }
+        }
+    }
+    block_sum8<256>(acc, s_red, s_out);
+    if (threadIdx.x < 8) parts[blockIdx.x * 8 + threadIdx.x] = s_out[threadIdx.x];
+}
+
+// (4) Bookkeeping for the next step: pending impulses, fluid count, mass
+// correction delta_l = ledger_l / N_fluid, counterforce, box swap, step + 1.
+// Without a particle only the step counter advances. One block.
+__global__ void __launch_bounds__(256) k_finish(DevState* __restrict__ st, const int* __restrict__ counts,
+                                                const double* __restrict__ parts, int nblocks, KParams P)
+{
+    __shared__ double s_red[(256 / 32) * 8];
+    __shared__ double s_out[8];
+    __shared__ long long s_c[256];
+    if (!P.has_particle) {
+        if (threadIdx.x == 0) {
+            st->step += 1;
+            st->step_u32 = (uint32_t)st->step;
+        }
+        return;
+    }
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long cnt = 0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += parts[b * 8 + k];
+        cnt += counts[b];
+    }
+    s_c[threadIdx.x] = cnt;
+    block_sum8<256>(acc, s_red, s_out);
+    if (threadIdx.x != 0) return;
+    long long solid = 0;
+    for (int k = 0; k < (int)blockDim.x; ++k) solid += s_c[k];
+    for (int a = 0; a < 3; ++a) {
+        st->Ppend[a] = s_out[a];
+        st->Lpend[a] = s_out[3 + a];
+    }
+    const long long nf = P.N - solid;
+    st->nfluid = nf;
+    st->delta[0] = (st->ledger_bb[0] + s_out[6]) / (double)nf;
+    st->delta[1] = (st->ledger_bb[1] + s_out[7]) / (double)nf;
+    st->delta_f[0] = (float)st->delta[0];
+    st->delta_f[1] = (float)st->delta[1];
+    st->fc = P.counterforce ? -st->Fp / (double)nf : 0.0;
+    st->fc_f = (float)st->fc;
+    st->box0[0] = st->box_next[0]; st->box0[1] = st->box_next[1]; st->box0[2] = st->box_next[2];
+    st->cur = 1 - st->cur;
+    st->step += 1;
+    st->step_u32 = (uint32_t)st->step;
+}
+
+// Mark the particle nodes of the current position into mask[cur] and set the
+// box origin, fluid count and counterforce (creation and flbm_set_particle).
+// One block; FP64 inside test as in the step.
+__global__ void __launch_bounds__(1024) k_mark(DevState* st, uint8_t* masks, KParams P)
+{
+    __shared__ long long s_c[1024];
+    __shared__ int s_o[3];
+    if (threadIdx.x == 0) {
+        int o[3];
+        box_origin(st->X, P, o);
+        s_o[0] = o[0]; s_o[1] = o[1]; s_o[2] = o[2];
+    }
+    __syncthreads();
+    const int o[3] = {s_o[0], s_o[1], s_o[2]};
+    const double X[3] = {st->X[0], st->X[1], st->X[2]};
+    const int B3 = P.B * P.B * P.B;
+    uint8_t* mask = masks + (size_t)st->cur * B3;
+    long long cnt = 0;
+    for (int t = threadIdx.x; t < B3; t += blockDim.x) {
+        const bool in = box_node_inside(t, o, X, P);
+        mask[t] = in ? 1 : 0;
+        cnt += in;
+    }
+    s_c[threadIdx.x] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long a = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) a += s_c[k];
+        st->box0[0] = o[0]; st->box0[1] = o[1]; st->box0[2] = o[2];
+        st->nfluid = P.N - a;
+        st->fc = (P.counterforce && st->nfluid > 0) ? -st->Fp / (double)st->nfluid : 0.0;
+        st->fc_f = (float)st->fc;
+        st->delta_f[0] = (float)st->delta[0];
+        st->delta_f[1] = (float)st->delta[1];
+        st->step_u32 = (uint32_t)st->step;
+    }
+}
+
+}  // namespace flbm

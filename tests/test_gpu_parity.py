@@ -111,7 +111,7 @@ def test_channel_small_100_noise_free_steps(flbm, oracle_mod):
         sim.step(1)
         orc.step(1)
     po = orc.particle()
-    assert sim.launches() == 5
+    assert sim.launches() == 9  # density, virtual, shell, bulk, near, update, mark, cover, finish
     pg = sim.particle()
     vimp = po["Fp"] / po["mp"] * 100
     _compare_particle(pg, po, vimp, 100)
