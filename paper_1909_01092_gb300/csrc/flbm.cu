@@ -80,7 +80,7 @@ std::string validate(const flbm_params* p)
     if (p->lx < 1 || p->ly < 1 || p->lz < 1) return "lattice sizes must be >= 1";
     if (p->lz > 65535 || p->ly > 65535 * 256) return "lattice too large for the launch grid";
     const double n = (double)p->lx * p->ly * p->lz;
-    if (n > 4294967295.0) return "more than 2^32 nodes (node index feeds a 32-bit Philox counter)";
+    if (38.0 * n > 4294967295.0) return "more than 2^32/38 nodes (32-bit population indices)";
     const int w[3] = {p->wall_x, p->wall_y, p->wall_z};
     for (int a = 0; a < 3; ++a)
         if (w[a] != 0 && w[a] != 1) return "wall flags must be 0 or 1";
@@ -154,6 +154,8 @@ void fill_kparams(flbm_sim* h)
     k.ncx = std::min(k.gx, (k.B + 2 + k.tx - 1) / k.tx + 2);
     k.ncy = std::min(k.gy, (k.B + 2 + k.ty - 1) / k.ty + 2);
     k.ncz = std::min(p.lz, k.B + 2);
+    k.tau1 = (p.tau_s == 1.0 && p.tau_d == 1.0 && p.tau_g == 1.0) ? 1 : 0;
+    for (int q = 0; q < 38; ++q) k.dirN[q] = (uint32_t)((long long)q * k.N);
     h->ncand = (long long)k.ncx * k.ncy * k.ncz;
     h->box_blocks = (k.B * k.B * k.B + 255) / 256;
 }
@@ -203,19 +205,22 @@ int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
     if (int rc = launch_psi(h, fin, ev)) return rc;
     const bool noise = k.kT > 0.0f;
     const bool part = k.has_particle != 0;
-    if (noise)
-        k_collide_bulk<true><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, k);
-    else
-        k_collide_bulk<false><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, k);
-    if (int rc = launch_check(h, "k_collide_bulk")) return rc;
-    if (part) {
-        const dim3 g(k.ncx, k.ncy, k.ncz);
-        if (noise)
-            k_collide_near<true><<<g, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks, h->partials, k);
-        else
-            k_collide_near<false><<<g, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks, h->partials, k);
-        if (int rc = launch_check(h, "k_collide_near")) return rc;
-    }
+    const dim3 gnear(k.ncx, k.ncy, k.ncz);
+#define FLBM_COLLIDE(NZ, T1)                                                                                  \
+    do {                                                                                                      \
+        k_collide_bulk<NZ, T1><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, k);             \
+        if (int rc = launch_check(h, "k_collide_bulk")) return rc;                                            \
+        if (part) {                                                                                           \
+            k_collide_near<NZ, T1><<<gnear, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks,     \
+                                                                      h->partials, k);                        \
+            if (int rc = launch_check(h, "k_collide_near")) return rc;                                        \
+        }                                                                                                     \
+    } while (0)
+    if (noise && k.tau1) FLBM_COLLIDE(true, true);
+    else if (noise) FLBM_COLLIDE(true, false);
+    else if (k.tau1) FLBM_COLLIDE(false, true);
+    else FLBM_COLLIDE(false, false);
+#undef FLBM_COLLIDE
     record(h, ev, 4);
     if (part) {
         k_update<<<1, 256, 0, h->stream>>>(h->st, h->partials, k);

@@ -176,6 +176,8 @@ struct KParams {
     uint32_t key0, key1;   // Philox key
     uint32_t rk0[10], rk1[10];  // Philox round keys key + r * (0x9E3779B9, 0xBB67AE85)
     int ncx, ncy, ncz;     // candidate tiles per axis around the particle box
+    int tau1;              // every relaxation time equals 1
+    uint32_t dirN[38];     // (19 l + i) * N: offset of population (l, i) in one copy
     int has_particle;
     int B;                 // side of the particle box
     double R;              // sphere radius

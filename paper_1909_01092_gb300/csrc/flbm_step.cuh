@@ -15,6 +15,10 @@
 
 #include "flbm_device.cuh"
 
+#ifndef FLBM_BULK_MINBLOCKS
+#define FLBM_BULK_MINBLOCKS 4  // resident 256-thread blocks per SM the bulk kernel is compiled for
+#endif
+
 namespace flbm {
 
 // Philox4x32-10 with the round keys precomputed on the host (key + r * Weyl).
@@ -49,28 +53,51 @@ __device__ __forceinline__ void box_muller(uint32_t w1, uint32_t w2, float& z0, 
     z1 = -r * s;
 }
 
+// Density and momentum of one component from its 19 populations.
+__device__ __forceinline__ void moments(const float f[19], float& rho, float j[3])
+{
+    const float s1 = f[1] + f[2], s2 = f[3] + f[4], s3 = f[5] + f[6];
+    const float s7 = f[7] + f[8], s9 = f[9] + f[10], s11 = f[11] + f[12];
+    const float s13 = f[13] + f[14], s15 = f[15] + f[16], s17 = f[17] + f[18];
+    const float d7 = f[7] - f[8], d9 = f[9] - f[10], d11 = f[11] - f[12];
+    const float d13 = f[13] - f[14], d15 = f[15] - f[16], d17 = f[17] - f[18];
+    rho = f[0] + (s1 + s2 + s3) + (s7 + s9) + (s11 + s13) + (s15 + s17);
+    j[0] = (f[1] - f[2]) + d7 + d9 + d11 + d13;
+    j[1] = (f[3] - f[4]) + d7 - d9 + d15 + d17;
+    j[2] = (f[5] - f[6]) + d11 - d13 + d15 - d17;
+}
+
 // Collision and push-streaming of one fluid node (Eq. (lbe)). With PARTICLE,
 // solid_nb marks the directions whose neighbour is a particle node; their
-// links take the moving rule and feed acc = (F[3], T[3], ledger[2]).
-template <bool NOISE, bool PARTICLE>
-__device__ __forceinline__ void collide_node(int x, int y, int z, long long n, const float* __restrict__ fin,
+// links take the moving rule and feed acc = (F[3], T[3], ledger[2]). TAU1:
+// every relaxation time is 1, so the post-collision modes depend on the
+// input only through rho_l and j_l, and the ghost modes carry noise only.
+// Population (l, i) of node m lives at index m + P.dirN[19 l + i] (32-bit).
+template <bool NOISE, bool PARTICLE, bool TAU1>
+__device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, const float* __restrict__ fin,
                                              float* __restrict__ fout, const float* __restrict__ psi,
                                              const DevState* __restrict__ st, const KParams& P, uint32_t solid_nb,
                                              double* acc)
 {
-    const long long N = P.N;
     float ma[19], mb[19];
+    float rhoA, rhoB;
     {
         float fa[19], fb[19];
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            fa[i] = __ldg(fin + (long long)i * N + n);
-            fb[i] = __ldg(fin + (long long)(19 + i) * N + n);
+            fa[i] = __ldg(fin + (n + P.dirN[i]));
+            fb[i] = __ldg(fin + (n + P.dirN[19 + i]));
         }
-        to_modes(fa, ma);
-        to_modes(fb, mb);
+        if (TAU1) {
+            moments(fa, ma[0], ma + 1);
+            moments(fb, mb[0], mb + 1);
+        } else {
+            to_modes(fa, ma);
+            to_modes(fb, mb);
+        }
+        rhoA = ma[0];
+        rhoB = mb[0];
     }
-    const float rhoA = ma[0], rhoB = mb[0];
     const float rt = rhoA + rhoB;
 
     // Shan-Chen force, Eq. (sc-force), omega_i = w_i, psi = rho.
@@ -78,10 +105,10 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, long long n, c
     {
         const float* pA = psi + pad_index(x, y, z, P);
         const float* pB = pA + P.padn;
-        const long long sy = P.px, sz = (long long)P.px * P.py;
+        const int sy = P.px, sz = P.px * P.py;
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
-            const long long off = cxv(i) + sy * cyv(i) + sz * czv(i);
+            const int off = cxv(i) + sy * cyv(i) + sz * czv(i);
             const float pa = __ldg(pA + off);
             const float pb = __ldg(pB + off);
             const float w = wv(i);
@@ -120,19 +147,28 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, long long n, c
     // MRT relaxation of each component in moment space, then n_k = m_k / b_k.
     auto relax = [&](float* m, float rl, const float* Fl, float delta) {
         const float uF = u[0] * Fl[0] + u[1] * Fl[1] + u[2] * Fl[2];
-        const float h = 0.5f * (1.0f + P.gs);
         m[0] = rl + delta;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            m[1 + a] = rl * u[a] + P.gd * (m[1 + a] + 0.5f * Fl[a] - rl * u[a]) + 0.5f * Fl[a];
         const float meq[6] = {rl * uu, rl * (3.0f * u[0] * u[0] - uu), rl * (u[1] * u[1] - u[2] * u[2]),
                               rl * u[0] * u[1], rl * u[1] * u[2], rl * u[0] * u[2]};
         const float S[6] = {2.0f * uF, 2.0f * (3.0f * u[0] * Fl[0] - uF), 2.0f * (u[1] * Fl[1] - u[2] * Fl[2]),
                             u[0] * Fl[1] + u[1] * Fl[0], u[1] * Fl[2] + u[2] * Fl[1], u[0] * Fl[2] + u[2] * Fl[0]};
+        if (TAU1) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) m[4 + k] = meq[k] + P.gs * (m[4 + k] - meq[k]) + h * S[k];
+            for (int a = 0; a < 3; ++a) m[1 + a] = rl * u[a] + 0.5f * Fl[a];
 #pragma unroll
-        for (int k = 10; k < 19; ++k) m[k] *= P.gg;
+            for (int k = 0; k < 6; ++k) m[4 + k] = meq[k] + 0.5f * S[k];
+#pragma unroll
+            for (int k = 10; k < 19; ++k) m[k] = 0.0f;
+        } else {
+            const float h = 0.5f * (1.0f + P.gs);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                m[1 + a] = rl * u[a] + P.gd * (m[1 + a] + 0.5f * Fl[a] - rl * u[a]) + 0.5f * Fl[a];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) m[4 + k] = meq[k] + P.gs * (m[4 + k] - meq[k]) + h * S[k];
+#pragma unroll
+            for (int k = 10; k < 19; ++k) m[k] *= P.gg;
+        }
 #pragma unroll
         for (int k = 0; k < 19; ++k) m[k] *= 1.0f / bnorm(k);
     };
@@ -148,7 +184,7 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, long long n, c
         const uint32_t stp = st->step_u32;
 #pragma unroll
         for (int blk = 0; blk < 9; ++blk) {
-            uint32_t r0 = stp, r1 = (uint32_t)n, r2 = (uint32_t)blk, r3 = 0u;
+            uint32_t r0 = stp, r1 = n, r2 = (uint32_t)blk, r3 = 0u;
             philox_rk(r0, r1, r2, r3, P);
             float zn[4];
             box_muller(r0, r1, zn[0], zn[1]);
@@ -166,22 +202,22 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, long long n, c
         }
     }
 
-    // Neighbour offsets; a wall on a side is flagged instead.
+    // Destination offsets along each axis (periodic wrap), and wall flags.
     const int L[3] = {P.lx, P.ly, P.lz};
     const int crd[3] = {x, y, z};
-    const long long stride[3] = {1, (long long)P.lx, (long long)P.lx * P.ly};
-    long long offp[3], offm[3];
-    int wallp = 0, wallm = 0;
+    const int stride[3] = {1, P.lx, P.lx * P.ly};
+    int offp[3], offm[3];
+    uint32_t wallp = 0, wallm = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         offp[a] = stride[a];
         offm[a] = -stride[a];
         if (crd[a] + 1 >= L[a]) {
-            if (P.wall[a]) wallp |= 1 << a;
+            if (P.wall[a]) wallp |= 1u << a;
             else offp[a] = stride[a] * (1 - L[a]);
         }
         if (crd[a] - 1 < 0) {
-            if (P.wall[a]) wallm |= 1 << a;
+            if (P.wall[a]) wallm |= 1u << a;
             else offm[a] = stride[a] * (L[a] - 1);
         }
     }
@@ -193,16 +229,13 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, long long n, c
         float fo[19];
         from_modes(l == 0 ? ma : mb, fo);
         const float rl = l == 0 ? rhoA : rhoB;
-        float* out = fout + (long long)(19 * l) * N;
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             const int cx = cxv(i), cy = cyv(i), cz = czv(i);
-            const bool wall = (cx > 0 && (wallp & 1)) || (cx < 0 && (wallm & 1)) || (cy > 0 && (wallp & 2)) ||
-                              (cy < 0 && (wallm & 2)) || (cz > 0 && (wallp & 4)) || (cz < 0 && (wallm & 4));
-            if (wall) {
-                out[(long long)oppv(i) * N + n] = fo[i];
-                continue;
-            }
+            const uint32_t need_p = (cx > 0 ? 1u : 0u) | (cy > 0 ? 2u : 0u) | (cz > 0 ? 4u : 0u);
+            const uint32_t need_m = (cx < 0 ? 1u : 0u) | (cy < 0 ? 2u : 0u) | (cz < 0 ? 4u : 0u);
+            const bool wall = ((wallp & need_p) | (wallm & need_m)) != 0u;
+            const uint32_t back_idx = n + P.dirN[19 * l + oppv(i)];
             if (PARTICLE && (solid_nb >> i & 1u)) {
                 // f_{-i}(x, t+1) = f*_i(x) - 6 w_i rho_l (u_b . c_i), u_b at the link midpoint.
                 const double r[3] = {rel_axis(x + 0.5 * cx, st->X[0], P.lx, P.wall[0]),
@@ -214,7 +247,7 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, long long n, c
                 const float ubc = (float)(ub[0] * cx + ub[1] * cy + ub[2] * cz);
                 const float corr = 6.0f * wv(i) * rl * ubc;
                 const float back = fo[i] - corr;
-                out[(long long)oppv(i) * N + n] = back;
+                fout[back_idx] = back;
                 const double dp = (double)fo[i] + (double)back;
                 const double fr[3] = {dp * cx, dp * cy, dp * cz};
                 acc[0] += fr[0]; acc[1] += fr[1]; acc[2] += fr[2];
@@ -224,11 +257,12 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, long long n, c
                 acc[6 + l] += corr;
                 continue;
             }
-            long long d = n;
-            if (cx > 0) d += offp[0]; else if (cx < 0) d += offm[0];
-            if (cy > 0) d += offp[1]; else if (cy < 0) d += offm[1];
-            if (cz > 0) d += offp[2]; else if (cz < 0) d += offm[2];
-            out[(long long)i * N + d] = fo[i];
+            int off = 0;
+            if (cx) off += cx > 0 ? offp[0] : offm[0];
+            if (cy) off += cy > 0 ? offp[1] : offm[1];
+            if (cz) off += cz > 0 ? offp[2] : offm[2];
+            const uint32_t push_idx = n + (uint32_t)off + P.dirN[19 * l + i];
+            fout[wall ? back_idx : push_idx] = fo[i];
         }
     }
 }
@@ -236,8 +270,8 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, long long n, c
 // ---------------------------------------------------------------------------
 // Bulk tiles: every tile not next to the particle.
 // ---------------------------------------------------------------------------
-template <bool NOISE>
-__global__ void __launch_bounds__(kThreadsStep, 2)
+template <bool NOISE, bool TAU1>
+__global__ void __launch_bounds__(kThreadsStep, FLBM_BULK_MINBLOCKS)
     k_collide_bulk(const float* __restrict__ fin, float* __restrict__ fout, const float* __restrict__ psi,
                    const DevState* __restrict__ st, KParams P)
 {
@@ -249,8 +283,8 @@ __global__ void __launch_bounds__(kThreadsStep, 2)
     const int y = blockIdx.y * P.ty + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= P.lx || y >= P.ly) return;
-    const long long n = x + (long long)P.lx * (y + (long long)P.ly * z);
-    collide_node<NOISE, false>(x, y, z, n, fin, fout, psi, st, P, 0u, nullptr);
+    const uint32_t n = (uint32_t)x + (uint32_t)P.lx * ((uint32_t)y + (uint32_t)P.ly * (uint32_t)z);
+    collide_node<NOISE, false, TAU1>(x, y, z, n, fin, fout, psi, st, P, 0u, nullptr);
 }
 
 // Candidate c on one axis -> tile index, or -1. e0 = first coordinate of the
@@ -271,7 +305,7 @@ __device__ __forceinline__ int candidate_tile(int c, int o, int T, int gt, int L
 // Near tiles: a fixed grid of candidate tiles around the particle box; each
 // near tile reduces force, torque and mass ledger into partials[candidate].
 // ---------------------------------------------------------------------------
-template <bool NOISE>
+template <bool NOISE, bool TAU1>
 __global__ void __launch_bounds__(kThreadsStep)
     k_collide_near(const float* __restrict__ fin, float* __restrict__ fout, const float* __restrict__ psi,
                    const DevState* __restrict__ st, const uint8_t* __restrict__ masks,
@@ -311,8 +345,8 @@ __global__ void __launch_bounds__(kThreadsStep)
             }
             if (ok && is_solid(q[0], q[1], q[2], o, mask, P)) solid_nb |= 1u << i;
         }
-        const long long n = x + (long long)P.lx * (y + (long long)P.ly * z);
-        collide_node<NOISE, true>(x, y, z, n, fin, fout, psi, st, P, solid_nb, acc);
+        const uint32_t n = (uint32_t)x + (uint32_t)P.lx * ((uint32_t)y + (uint32_t)P.ly * (uint32_t)z);
+        collide_node<NOISE, true, TAU1>(x, y, z, n, fin, fout, psi, st, P, solid_nb, acc);
     }
     block_sum8<kThreadsStep>(acc, s_red, s_out);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
