@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 128-replica ensemble measurement")
     ap.add_argument("--lz", type=int, default=512, help="channel length (shorter only for profiler captures)")
     return ap.parse_args()
 
@@ -173,6 +174,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def ensemble_bench(binding, W, steps: int = 100) -> dict:
+    """The 128-replica ensemble (uneven channels, radii and kT): tuned
+    batched launches replayed as CUDA graphs, against the same replicas
+    stepped one simulation after another with their own launches."""
+    import torch
+
+    plist = W.ensemble_members(128)
+    ens = binding.Ensemble(plist)
+    cfg, _ = ens.tune(steps=4)
+    nodes = ens.nodes()
+    ens.step(4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ens.stream)
+    ens.step(steps)
+    e1.record(ens.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = ens.launches()
+    ens.close()
+    stream = torch.cuda.Stream()
+    sims = [binding.Sim(p, stream=stream) for p in plist]
+    for s in sims:
+        s.step(2)
+    torch.cuda.synchronize()
+    rounds = max(2, steps // 10)
+    e0.record(stream)
+    for _ in range(rounds):
+        for s in sims:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1) / rounds
+    for s in sims:
+        s.close()
+    return {"workload": "ensemble_128_replicas_L16-48_R2.5-6_kT1e-6-1e-4", "replicas": len(plist), "nodes": nodes,
+            "steps": steps, "ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6, "gpu_launches": launches,
+            "config": cfg, "one_at_a_time": {"ms_per_step": ms1, "mlups": nodes / (ms1 * 1e-3) / 1e6,
+                                             "launches_per_step": 9 * len(plist)},
+            "speedup": ms1 / ms}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -249,6 +292,10 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
+    ens = None
+    if rank == 0 and world == 1 and not args.no_ensemble:
+        sim.close()
+        ens = ensemble_bench(binding, W)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -256,7 +303,8 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD if args.lz == 512 else f"channel_128x128x{args.lz}_kT1e-5_R12", "lx": p["lx"], "ly": p["ly"], "lz": p["lz"], "kT": p["kT"],
                            "radius": p["radius"], "g": p["g"], "G": p["G"], "walls": "x,y", "replicas_per_gpu": 1,
                            "l2": "inputs larger than L2 (2.55 GB of populations), no flush"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches}
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches,
+                "ensemble": ens}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:

@@ -182,6 +182,34 @@ const char* flbm_kernel_name(int k);
 /* Number of kernel launches the last flbm_step / flbm_step_timed / flbm_run_host issued. */
 int64_t flbm_last_launch_count(const flbm_t* h);
 
+/* Write the whole simulation state to the file `path` (host path string):
+ * the parameters, the FP64 particle record (position, velocities, pending
+ * impulses, mass-correction ledger, step counter), the particle-node masks
+ * and the current populations. Synchronises the stream. The paper has no
+ * counterpart; this serves runs longer than one process (the paper's
+ * production runs take 10^6 steps, Section 3).
+ * Errors: FLBM_E_INVAL (NULL argument, file cannot be written), FLBM_E_CUDA. */
+int flbm_checkpoint(flbm_t* h, const char* path);
+
+/* Read a file written by flbm_checkpoint into h. The file's lattice sizes,
+ * walls and particle radius must equal h's (they fix the state layout); the
+ * other parameters (kT, G, forces, seed, ...) stay those h was created with,
+ * so a state may be equilibrated under one set and continued under another.
+ * With equal parameters, stepping after a restore gives the same populations
+ * and particle record, bit for bit, as stepping on without the checkpoint.
+ * Synchronises the stream. Errors: FLBM_E_INVAL (NULL, unreadable or
+ * truncated file, wrong format, layout mismatch), FLBM_E_CUDA. */
+int flbm_restore(flbm_t* h, const char* path);
+
+/* CUDA-graph replay for flbm_step: with enable = 1, flbm_step replays a
+ * captured graph of two steps (captured on first use) instead of issuing
+ * each kernel, which removes the per-launch host cost that dominates small
+ * lattices. Results are identical to plain launches. The handle's stream
+ * must not be the legacy default stream (capture is not allowed there):
+ * FLBM_E_UNSUPPORTED then. enable = 0 returns to plain launches.
+ * Errors: FLBM_E_INVAL, FLBM_E_UNSUPPORTED, FLBM_E_CUDA (capture failed). */
+int flbm_use_graphs(flbm_t* h, int enable);
+
 /* Observables of a population field, allocating nothing.
  *
  * For callers that cannot allocate device memory: code whose device memory is
@@ -218,6 +246,79 @@ const char* flbm_error_string(int code);
 
 /* Message of the handle's last failure ("" if none); valid until the next call. */
 const char* flbm_last_error(const flbm_t* h);
+
+/* ------------------------------------------------------------------------
+ * Batched ensemble: many independent simulations (replicas) advanced
+ * together. The paper's velocity statistics (Section 3) are averages over
+ * noise realisations and channel geometries; an ensemble runs them as one
+ * set of batched launches per step instead of one set per replica. Each
+ * replica is exactly the simulation flbm_create would make from its
+ * parameters (same initial state, same Philox stream, same step), so an
+ * ensemble member and a single simulation agree bit for bit under tile
+ * policy 0; other tile policies change only the FP64 summation order of the
+ * particle force.
+ * ------------------------------------------------------------------------ */
+typedef struct flbm_ens flbm_ens_t;
+
+/* Launch configuration of an ensemble (host memory). */
+typedef struct flbm_ens_config {
+    int32_t packing;     /* order of work items in each launch: 0 replica after replica,
+                            1 interleaved (item k of every replica, then item k+1),
+                            2 replica after replica, largest lattice first */
+    int32_t ctas_per_sm; /* persistent blocks per SM of every batched launch (1..8);
+                            0: one block per work item */
+    int32_t tile_policy; /* 0: tile width min(32, next power of two >= lx), as flbm_create;
+                            1: the largest of 32, 16, 8 that divides lx (else as 0) */
+} flbm_ens_config;
+
+/* Create n >= 1 replicas on the current device from the parameter array
+ * p[0..n-1] (host memory; each validated as by flbm_create). cfg NULL
+ * selects {packing 0, ctas_per_sm 4, tile_policy 0}. The library owns all
+ * device memory. With a stream other than the legacy default stream,
+ * flbm_ensemble_step replays captured CUDA graphs of two steps.
+ * Errors: FLBM_E_INVAL (a parameter set is invalid: the message names it),
+ * FLBM_E_NOMEM, FLBM_E_CUDA. */
+int flbm_ensemble_create(const flbm_params* p, int32_t n, const flbm_ens_config* cfg, void* stream,
+                         flbm_ens_t** out);
+
+/* Advance every replica by nsteps >= 0 steps (asynchronous on the stream).
+ * Errors: FLBM_E_INVAL, FLBM_E_CUDA. */
+int flbm_ensemble_step(flbm_ens_t* e, int64_t nsteps);
+
+/* Autotuner: time `steps` >= 2 steps of every candidate configuration (the
+ * three packings x ctas_per_sm in {0, 2, 4} x the two tile policies) with
+ * CUDA events on the stream, keep the fastest, then put every replica back
+ * to its initial state. best (may be NULL) receives the chosen
+ * configuration and ms_best (may be NULL) its milliseconds per step.
+ * Synchronises. Errors: FLBM_E_INVAL, FLBM_E_NOMEM, FLBM_E_CUDA. */
+int flbm_ensemble_tune(flbm_ens_t* e, int32_t steps, flbm_ens_config* best, double* ms_best);
+
+/* Current configuration (host memory, caller-owned out). */
+int flbm_ensemble_config(const flbm_ens_t* e, flbm_ens_config* out);
+
+/* Particle records of all replicas into out[0..n-1] (host memory; replicas
+ * without a particle report their step and fluid count only). Synchronises. */
+int flbm_ensemble_particles(flbm_ens_t* e, flbm_particle* out);
+
+/* Populations of replica r (layout as flbm_read_fields) into host_f.
+ * Synchronises. Errors: FLBM_E_INVAL (r out of range), FLBM_E_CUDA. */
+int flbm_ensemble_read_fields(flbm_ens_t* e, int32_t r, float* host_f);
+
+/* Observables of replica r, as flbm_observables. Synchronises. */
+int flbm_ensemble_observables(flbm_ens_t* e, int32_t r, flbm_obs* out);
+
+/* Total lattice nodes over all replicas (the unit of ensemble MLUPS). */
+int64_t flbm_ensemble_nodes(const flbm_ens_t* e);
+
+/* Kernel launches issued by the last flbm_ensemble_step (graph replays
+ * count the kernels inside the graph). */
+int64_t flbm_ensemble_last_launch_count(const flbm_ens_t* e);
+
+/* Message of the ensemble's last failure ("" if none). */
+const char* flbm_ensemble_last_error(const flbm_ens_t* e);
+
+/* Free everything the ensemble owns; synchronises its stream. */
+void flbm_ensemble_destroy(flbm_ens_t* e);
 
 #ifdef __cplusplus
 }

@@ -24,8 +24,16 @@ EXPORTS = (
     "flbm_read_fields", "flbm_write_fields", "flbm_set_particle", "flbm_run_host",
     "flbm_last_launch_count", "flbm_destroy", "flbm_error_string", "flbm_last_error",
     "flbm_step_timed", "flbm_kernel_name", "flbm_observables_noalloc",
+    "flbm_checkpoint", "flbm_restore", "flbm_use_graphs",
+    "flbm_ensemble_create", "flbm_ensemble_step", "flbm_ensemble_tune", "flbm_ensemble_config",
+    "flbm_ensemble_particles", "flbm_ensemble_read_fields", "flbm_ensemble_observables", "flbm_ensemble_nodes",
+    "flbm_ensemble_last_launch_count", "flbm_ensemble_last_error", "flbm_ensemble_destroy",
 )
 NKERNELS = 5
+
+
+class EnsConfig(ctypes.Structure):
+    _fields_ = [("packing", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("tile_policy", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
@@ -89,6 +97,25 @@ def load(build_if_missing: bool = True):
         lib.flbm_run_host.argtypes = [vp, fp, ctypes.c_int64, fp, ctypes.POINTER(Particle)]
         lib.flbm_step_timed.argtypes = [vp, ctypes.c_int64, dp]
         lib.flbm_observables_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp]
+        lib.flbm_checkpoint.argtypes = [vp, ctypes.c_char_p]
+        lib.flbm_restore.argtypes = [vp, ctypes.c_char_p]
+        lib.flbm_use_graphs.argtypes = [vp, ctypes.c_int]
+        ens_p = ctypes.POINTER(EnsConfig)
+        lib.flbm_ensemble_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, ens_p, vp,
+                                             ctypes.POINTER(vp)]
+        lib.flbm_ensemble_step.argtypes = [vp, ctypes.c_int64]
+        lib.flbm_ensemble_tune.argtypes = [vp, ctypes.c_int32, ens_p, dp]
+        lib.flbm_ensemble_config.argtypes = [vp, ens_p]
+        lib.flbm_ensemble_particles.argtypes = [vp, ctypes.POINTER(Particle)]
+        lib.flbm_ensemble_read_fields.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
+        lib.flbm_ensemble_observables.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(Obs)]
+        lib.flbm_ensemble_nodes.restype = ctypes.c_int64
+        lib.flbm_ensemble_nodes.argtypes = [vp]
+        lib.flbm_ensemble_last_launch_count.restype = ctypes.c_int64
+        lib.flbm_ensemble_last_launch_count.argtypes = [vp]
+        lib.flbm_ensemble_last_error.restype = ctypes.c_char_p
+        lib.flbm_ensemble_last_error.argtypes = [vp]
+        lib.flbm_ensemble_destroy.argtypes = [vp]
         lib.flbm_kernel_name.restype = ctypes.c_char_p
         lib.flbm_kernel_name.argtypes = [ctypes.c_int]
         lib.flbm_last_launch_count.restype = ctypes.c_int64
@@ -138,6 +165,12 @@ def particle_dict(r: Particle) -> dict:
                                                   "delta")}
     d.update(mp=r.mp, Fp=r.Fp, nfluid=r.nfluid, step=r.step)
     return d
+
+
+def obs_dict(r: Obs) -> dict:
+    return dict(mass=np.array(r.mass[:]), momentum=np.array(r.momentum[:]), kinetic=r.kinetic,
+                particle_momentum=np.array(r.particle_momentum[:]), pending_mass=np.array(r.pending_mass[:]),
+                nfluid=r.nfluid, step=r.step, nonfinite=r.nonfinite)
 
 
 class Sim:
@@ -192,6 +225,17 @@ class Sim:
     def step(self, n: int = 1) -> None:
         self._check(self.lib.flbm_step(self.h, int(n)), "flbm_step")
 
+    def use_graphs(self, enable: bool = True) -> None:
+        """Replay flbm_step as captured two-step CUDA graphs (needs a
+        non-default stream)."""
+        self._check(self.lib.flbm_use_graphs(self.h, int(bool(enable))), "flbm_use_graphs")
+
+    def checkpoint(self, path) -> None:
+        self._check(self.lib.flbm_checkpoint(self.h, os.fsencode(path)), "flbm_checkpoint")
+
+    def restore(self, path) -> None:
+        self._check(self.lib.flbm_restore(self.h, os.fsencode(path)), "flbm_restore")
+
     def step_timed(self, n: int) -> dict:
         """Advance n steps; return the summed device milliseconds per kernel class."""
         ms = np.zeros(NKERNELS)
@@ -211,9 +255,7 @@ class Sim:
         rc = self.lib.flbm_observables(self.h, ctypes.byref(r))
         if not (allow_nonfinite and rc == -4):
             self._check(rc, "flbm_observables")
-        return dict(mass=np.array(r.mass[:]), momentum=np.array(r.momentum[:]), kinetic=r.kinetic,
-                    particle_momentum=np.array(r.particle_momentum[:]), pending_mass=np.array(r.pending_mass[:]),
-                    nfluid=r.nfluid, step=r.step, nonfinite=r.nonfinite)
+        return obs_dict(r)
 
     def read_f(self) -> np.ndarray:
         out = np.empty(self.shape, dtype=np.float32)
@@ -247,3 +289,88 @@ class Sim:
         if traj:
             return [particle_dict(tr[k]) for k in range(int(nsteps))]
         return None
+
+
+class Ensemble:
+    """Many independent simulations advanced by batched launches.
+
+    `plist` is a list of parameter dictionaries (one per replica). `config`
+    is None (library default) or a dict with keys packing, ctas_per_sm,
+    tile_policy. Work is issued on `stream` (a torch.cuda.Stream; default a
+    new one, so that steps replay as CUDA graphs).
+    """
+
+    def __init__(self, plist, config=None, stream=None):
+        import torch
+
+        self.lib = load()
+        self.plist = [dict(p) for p in plist]
+        n = len(self.plist)
+        arr = (Params * n)(*[to_params(p) for p in self.plist])
+        self._arr = arr
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        cfg = None
+        if config is not None:
+            cfg = ctypes.byref(EnsConfig(int(config["packing"]), int(config["ctas_per_sm"]),
+                                         int(config["tile_policy"])))
+        h = ctypes.c_void_p()
+        rc = self.lib.flbm_ensemble_create(arr, n, cfg, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != 0:
+            raise FLBMError(f"flbm_ensemble_create: {self.lib.flbm_error_string(rc).decode()}")
+        self.h = h
+        self.n = n
+
+    def _check(self, rc: int, what: str) -> None:
+        if rc != 0:
+            msg = self.lib.flbm_ensemble_last_error(self.h).decode()
+            raise FLBMError(f"{what}: {self.lib.flbm_error_string(rc).decode()} {msg}")
+
+    def step(self, n: int = 1) -> None:
+        self._check(self.lib.flbm_ensemble_step(self.h, int(n)), "flbm_ensemble_step")
+
+    def tune(self, steps: int = 6):
+        """Run the autotuner; return (chosen config dict, ms per step)."""
+        c = EnsConfig()
+        ms = np.zeros(1)
+        self._check(self.lib.flbm_ensemble_tune(self.h, int(steps), ctypes.byref(c), _dptr(ms)), "flbm_ensemble_tune")
+        return {"packing": c.packing, "ctas_per_sm": c.ctas_per_sm, "tile_policy": c.tile_policy}, float(ms[0])
+
+    def config(self) -> dict:
+        c = EnsConfig()
+        self._check(self.lib.flbm_ensemble_config(self.h, ctypes.byref(c)), "flbm_ensemble_config")
+        return {"packing": c.packing, "ctas_per_sm": c.ctas_per_sm, "tile_policy": c.tile_policy}
+
+    def particles(self) -> list:
+        recs = (Particle * self.n)()
+        self._check(self.lib.flbm_ensemble_particles(self.h, recs), "flbm_ensemble_particles")
+        return [particle_dict(r) for r in recs]
+
+    def read_f(self, r: int) -> np.ndarray:
+        p = self.plist[r]
+        out = np.empty((2, 19, p["lz"], p["ly"], p["lx"]), dtype=np.float32)
+        self._check(self.lib.flbm_ensemble_read_fields(self.h, int(r), _fptr(out)), "flbm_ensemble_read_fields")
+        return out
+
+    def observables(self, r: int) -> dict:
+        o = Obs()
+        rc = self.lib.flbm_ensemble_observables(self.h, int(r), ctypes.byref(o))
+        if rc not in (0, -4):
+            self._check(rc, "flbm_ensemble_observables")
+        return obs_dict(o)
+
+    def nodes(self) -> int:
+        return int(self.lib.flbm_ensemble_nodes(self.h))
+
+    def launches(self) -> int:
+        return int(self.lib.flbm_ensemble_last_launch_count(self.h))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.flbm_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

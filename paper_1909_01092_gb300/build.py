@@ -5,6 +5,7 @@ and is rebuilt when any source under csrc/ or the public header is newer.
 """
 from __future__ import annotations
 
+import concurrent.futures
 import glob
 import os
 import platform
@@ -35,22 +36,38 @@ def nvcc() -> str:
     return exe
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    out = lib_path()
-    srcs = _sources()
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= max(os.path.getmtime(s) for s in srcs):
-        return out
-    os.makedirs(BUILD, exist_ok=True)
-    tmp = out + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-I", INCLUDE, "-o", tmp, os.path.join(CSRC, "flbm.cu")]
+def _compile(src: str, obj: str, verbose: bool) -> str:
+    cmd = [nvcc(), *ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17", "-c", "-Xcompiler", "-fPIC",
+           "-I", INCLUDE, "-o", obj, src]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
+        raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n" + r.stdout + r.stderr)
+    return r.stdout + r.stderr
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every csrc/*.cu in parallel (one translation unit each) and
+    link them into the shared library."""
+    out = lib_path()
+    srcs = _sources()
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= max(os.path.getmtime(s) for s in srcs):
+        return out
+    tag = f".tmp{os.getpid()}"
+    objdir = os.path.join(BUILD, f"obj_{platform.machine()}{tag}")
+    os.makedirs(objdir, exist_ok=True)
+    units = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    objs = [os.path.join(objdir, os.path.basename(u)[:-3] + ".o") for u in units]
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(units)) as pool:
+        logs = list(pool.map(lambda uo: _compile(uo[0], uo[1], verbose), zip(units, objs)))
     if verbose:
-        print(r.stdout + r.stderr)
+        print("".join(logs))
+    tmp = out + tag
+    r = subprocess.run([nvcc(), *ARCH_FLAGS, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    shutil.rmtree(objdir, ignore_errors=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
     os.replace(tmp, out)
     return out
 

@@ -12,7 +12,7 @@
 #include <vector>
 
 #include "flbm.h"
-#include "flbm_kernels.cuh"
+#include "flbm_host.cuh"
 
 using namespace flbm;
 
@@ -39,6 +39,9 @@ struct flbm_sim {
     DevState* traj_host = nullptr;
     size_t traj_host_cap = 0;
     std::vector<cudaEvent_t> events;  // pool for flbm_step_timed
+    bool use_graphs = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two steps starting from cur = 0 / 1
+    int64_t graph_launches[2] = {0, 0};            // kernels in each graph
     dim3 grid, block;
     long long ntiles = 0;
     int64_t launches = 0;
@@ -64,100 +67,15 @@ int cuda_fail(flbm_sim* h, cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
     } while (0)
 
-int ceil_pow2(int v)
-{
-    int p = 1;
-    while (p < v) p <<= 1;
-    return p;
-}
-
-bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
-
-// Parameter checks; returns an empty string if valid.
-std::string validate(const flbm_params* p)
-{
-    if (!p) return "params is NULL";
-    if (p->lx < 1 || p->ly < 1 || p->lz < 1) return "lattice sizes must be >= 1";
-    if (p->lz > 65535 || p->ly > 65535 * 256) return "lattice too large for the launch grid";
-    const double n = (double)p->lx * p->ly * p->lz;
-    if (38.0 * n > 4294967295.0) return "more than 2^32/38 nodes (32-bit population indices)";
-    const int w[3] = {p->wall_x, p->wall_y, p->wall_z};
-    for (int a = 0; a < 3; ++a)
-        if (w[a] != 0 && w[a] != 1) return "wall flags must be 0 or 1";
-    if (!(p->tau_s > 0.5) || !(p->tau_d > 0.5) || !(p->tau_g > 0.5)) return "relaxation times must exceed 1/2";
-    if (!std::isfinite(p->G) || !std::isfinite(p->kT) || p->kT < 0.0) return "G must be finite and kT >= 0";
-    if (!(p->rho_a0 >= 0.0) || !(p->rho_b0 >= 0.0) || !(p->rho_a0 + p->rho_b0 > 0.0)) return "initial densities";
-    if (!(p->init_pert >= 0.0 && p->init_pert < 1.0)) return "init_pert must be in [0, 1)";
-    for (int a = 0; a < 3; ++a)
-        if (!std::isfinite(p->fluid_force[a])) return "fluid_force must be finite";
-    if (p->fluid_counterforce != 0 && p->fluid_counterforce != 1) return "fluid_counterforce must be 0 or 1";
-    if (p->radius > 0.0) {
-        if (!finite_pos(p->rho_p_ratio) || !std::isfinite(p->g) || !std::isfinite(p->delta_rho))
-            return "particle parameters must be finite, rho_p_ratio > 0";
-        const int L[3] = {p->lx, p->ly, p->lz};
-        const int B = (int)std::ceil(2.0 * p->radius) + 2;
-        for (int a = 0; a < 3; ++a) {
-            if (!std::isfinite(p->pos0[a])) return "pos0 must be finite";
-            if (w[a]) {
-                if (p->pos0[a] - p->radius < -0.5 || p->pos0[a] + p->radius > L[a] - 0.5)
-                    return "the sphere must lie inside the walls";
-            } else if (B + 2 > L[a]) {
-                return "periodic axis too short for the sphere (need L >= ceil(2R) + 4)";
-            }
-        }
-    }
-    return "";
-}
-
 void fill_kparams(flbm_sim* h)
 {
-    const flbm_params& p = h->p;
     KParams& k = h->kp;
-    std::memset(&k, 0, sizeof(k));
-    k.lx = p.lx; k.ly = p.ly; k.lz = p.lz;
-    k.wall[0] = p.wall_x; k.wall[1] = p.wall_y; k.wall[2] = p.wall_z;
-    k.px = p.lx + 2; k.py = p.ly + 2; k.pz = p.lz + 2;
-    k.N = (long long)p.lx * p.ly * p.lz;
-    k.padn = (long long)k.px * k.py * k.pz;
-    k.tx = std::min(32, ceil_pow2(p.lx));
-    k.ty = kThreads / k.tx;
-    k.gx = (p.lx + k.tx - 1) / k.tx;
-    k.gy = (p.ly + k.ty - 1) / k.ty;
-    k.G = (float)p.G;
-    const double gs = 1.0 - 1.0 / p.tau_s, gd = 1.0 - 1.0 / p.tau_d, gg = 1.0 - 1.0 / p.tau_g;
-    k.gs = (float)gs; k.gd = (float)gd; k.gg = (float)gg;
-    for (int a = 0; a < 3; ++a) k.ext[a] = (float)p.fluid_force[a];
-    k.drho = (float)p.delta_rho;
-    k.kT = (float)p.kT;
-    const double b[19] = {1, 1. / 3, 1. / 3, 1. / 3, 2. / 3, 4. / 3, 4. / 9, 1. / 9, 1. / 9, 1. / 9,
-                          2. / 3, 2. / 3, 2. / 3, 2. / 9, 2. / 9, 2. / 9, 2, 4. / 3, 4. / 9};
-    for (int q = 0; q < 19; ++q) {
-        const double gm = (q <= 9) ? gs : gg;
-        k.nz_mode[q] = (q >= 4) ? (float)std::sqrt((1.0 - gm * gm) / b[q]) : 0.0f;
-    }
-    k.nz_j = (float)std::sqrt(1.0 - gd * gd);
-    k.key0 = (uint32_t)(p.seed & 0xffffffffu);
-    k.key1 = (uint32_t)(p.seed >> 32) ^ p.replica;
-    for (int r = 0; r < 10; ++r) {
-        k.rk0[r] = k.key0 + (uint32_t)r * 0x9E3779B9u;
-        k.rk1[r] = k.key1 + (uint32_t)r * 0xBB67AE85u;
-    }
-    k.has_particle = p.radius > 0.0 ? 1 : 0;
-    k.B = k.has_particle ? (int)std::ceil(2.0 * p.radius) + 2 : 1;
-    k.R = p.radius;
-    k.rho0[0] = p.rho_a0; k.rho0[1] = p.rho_b0;
-    k.counterforce = p.fluid_counterforce;
+    make_kparams(h->p, 0, k);
     h->block = dim3(k.tx, k.ty, 1);
-    h->grid = dim3(k.gx, k.gy, p.lz);
-    h->ntiles = (long long)k.gx * k.gy * p.lz;
-    // Candidate tiles that can meet the particle box grown by one node.
-    k.ncx = std::min(k.gx, (k.B + 2 + k.tx - 1) / k.tx + 2);
-    k.ncy = std::min(k.gy, (k.B + 2 + k.ty - 1) / k.ty + 2);
-    k.ncz = std::min(p.lz, k.B + 2);
-    k.tau1 = (p.tau_s == 1.0 && p.tau_d == 1.0 && p.tau_g == 1.0) ? 1 : 0;
-    for (int q = 0; q < 38; ++q) k.dirN[q] = (uint32_t)((long long)q * k.N);
-    h->ncand = (long long)k.ncx * k.ncy * k.ncz;
-    h->box_blocks = (k.B * k.B * k.B + 255) / 256;
+    h->grid = dim3(k.gx, k.gy, k.lz);
+    h->ntiles = tile_count(k);
+    h->ncand = cand_count(k);
+    h->box_blocks = box_block_count(k);
 }
 
 int launch_check(flbm_sim* h, const char* what)
@@ -237,19 +155,56 @@ int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
     return FLBM_OK;
 }
 
-int copy_particle(const DevState& s, flbm_particle* out)
+// Capture two steps starting from cur = c into h->graph[c] (once).
+int ensure_graph(flbm_sim* h, int c)
 {
-    for (int a = 0; a < 3; ++a) {
-        out->X[a] = s.X[a]; out->V[a] = s.V[a]; out->Vavg[a] = s.Vavg[a]; out->Omega[a] = s.Om[a];
-        out->F[a] = s.F[a]; out->T[a] = s.T[a]; out->P_pending[a] = s.Ppend[a]; out->L_pending[a] = s.Lpend[a];
+    if (h->graph[c]) return FLBM_OK;
+    const int64_t before = h->launches;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_step(h);
+    if (!rc) rc = launch_step(h);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
     }
-    out->delta[0] = s.delta[0];
-    out->delta[1] = s.delta[1];
-    out->mp = s.mp;
-    out->Fp = s.Fp;
-    out->nfluid = s.nfluid;
-    out->step = s.step;
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph[c], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph[c] = nullptr;
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    // Capturing only recorded the kernels: nothing ran, cur is back at c.
+    h->graph_launches[c] = h->launches - before;
+    h->launches = before;
     return FLBM_OK;
+}
+
+// Fixed-size head of a checkpoint file, followed by flbm_params, DevState,
+// the two particle masks and the current populations.
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t lx, ly, lz, wall[3], B;
+    double radius;
+    uint64_t params_bytes, state_bytes, mask_bytes, f_bytes;
+};
+
+void fill_header(const flbm_sim* h, CkptHeader* hd)
+{
+    std::memset(hd, 0, sizeof(*hd));
+    std::memcpy(hd->magic, "FLBMCKP", 8);
+    hd->version = 1;
+    hd->lx = h->p.lx; hd->ly = h->p.ly; hd->lz = h->p.lz;
+    hd->wall[0] = h->p.wall_x; hd->wall[1] = h->p.wall_y; hd->wall[2] = h->p.wall_z;
+    hd->B = h->kp.B;
+    hd->radius = h->kp.has_particle ? h->p.radius : 0.0;
+    hd->params_bytes = sizeof(flbm_params);
+    hd->state_bytes = sizeof(DevState);
+    hd->mask_bytes = (uint64_t)2 * h->kp.B * h->kp.B * h->kp.B;
+    hd->f_bytes = (uint64_t)sizeof(float) * 2 * 19 * h->kp.N;
 }
 
 }  // namespace
@@ -278,7 +233,6 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
     fill_kparams(h);
     const KParams& k = h->kp;
     const size_t need = flbm_state_bytes(p);
-    int rc = FLBM_OK;
     auto bail = [&](int code) {
         flbm_destroy(h);
         return code;
@@ -306,19 +260,8 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
         return bail(FLBM_E_NOMEM);
 
     // Particle state (FP64): Eq. (fp) and the nominal sphere mass and inertia.
-    DevState s;
-    std::memset(&s, 0, sizeof(s));
-    if (k.has_particle) {
-        const double vol = 4.0 / 3.0 * M_PI * p->radius * p->radius * p->radius;
-        const double rho_tot = p->rho_a0 + p->rho_b0;
-        const double rho_p = p->rho_p_ratio * rho_tot;
-        s.mp = vol * rho_p;
-        s.Ip = 0.4 * s.mp * p->radius * p->radius;
-        s.Fp = vol * (rho_p - rho_tot) * p->g;
-        for (int a = 0; a < 3; ++a) s.X[a] = p->pos0[a];
-    }
-    s.nfluid = k.N;
-    if ((rc = cudaMemcpyAsync(h->st, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+    const DevState s = initial_state(*p, k);
+    if (cudaMemcpyAsync(h->st, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         return bail(FLBM_E_CUDA);
     if (cudaMemsetAsync(h->masks, 0, 2 * B3, h->stream) != cudaSuccess) return bail(FLBM_E_CUDA);
     if (cudaMemsetAsync(h->psi, 0, sizeof(float) * 2 * k.padn, h->stream) != cudaSuccess) return bail(FLBM_E_CUDA);
@@ -345,8 +288,93 @@ int flbm_step(flbm_t* h, int64_t nsteps)
 {
     if (!h || nsteps < 0) return fail(h, FLBM_E_INVAL, "invalid handle or step count");
     h->launches = 0;
-    for (int64_t s = 0; s < nsteps; ++s)
+    int64_t s = 0;
+    if (h->use_graphs) {
+        for (; s + 2 <= nsteps; s += 2) {
+            if (int rc = ensure_graph(h, h->cur)) return rc;
+            CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
+            h->launches += h->graph_launches[h->cur];  // two steps bring cur back
+        }
+    }
+    for (; s < nsteps; ++s)
         if (int rc = launch_step(h)) return rc;
+    return FLBM_OK;
+}
+
+int flbm_use_graphs(flbm_t* h, int enable)
+{
+    if (!h || (enable != 0 && enable != 1)) return fail(h, FLBM_E_INVAL, "invalid argument");
+    if (enable && h->stream == nullptr)
+        return fail(h, FLBM_E_UNSUPPORTED, "graph capture needs a stream other than the legacy default stream");
+    h->use_graphs = enable != 0;
+    return FLBM_OK;
+}
+
+int flbm_checkpoint(flbm_t* h, const char* path)
+{
+    if (!h || !path) return fail(h, FLBM_E_INVAL, "NULL argument");
+    const KParams& k = h->kp;
+    CkptHeader hd;
+    fill_header(h, &hd);
+    std::vector<unsigned char> masks(hd.mask_bytes);
+    std::vector<float> f((size_t)2 * 19 * k.N);
+    DevState st;
+    CK(h, cudaMemcpyAsync(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(masks.data(), h->masks, hd.mask_bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(f.data(), h->fbuf[h->cur], hd.f_bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(h, FLBM_E_INVAL, std::string("cannot open ") + path + " for writing");
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1 && std::fwrite(&h->p, sizeof(h->p), 1, fp) == 1 &&
+              std::fwrite(&st, sizeof(st), 1, fp) == 1 &&
+              std::fwrite(masks.data(), 1, hd.mask_bytes, fp) == hd.mask_bytes &&
+              std::fwrite(f.data(), 1, hd.f_bytes, fp) == hd.f_bytes;
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? FLBM_OK : fail(h, FLBM_E_INVAL, std::string("write to ") + path + " failed");
+}
+
+int flbm_restore(flbm_t* h, const char* path)
+{
+    if (!h || !path) return fail(h, FLBM_E_INVAL, "NULL argument");
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(h, FLBM_E_INVAL, std::string("cannot open ") + path);
+    CkptHeader want, got;
+    fill_header(h, &want);
+    flbm_params fp_params;
+    DevState st;
+    std::vector<unsigned char> masks(want.mask_bytes);
+    std::vector<float> f((size_t)2 * 19 * h->kp.N);
+    bool ok = std::fread(&got, sizeof(got), 1, fp) == 1;
+    if (ok && (std::memcmp(got.magic, want.magic, sizeof(got.magic)) != 0 || got.version != want.version ||
+               got.params_bytes != want.params_bytes || got.state_bytes != want.state_bytes)) {
+        std::fclose(fp);
+        return fail(h, FLBM_E_INVAL, std::string(path) + ": not a checkpoint of this library version");
+    }
+    if (ok && (got.lx != want.lx || got.ly != want.ly || got.lz != want.lz || got.wall[0] != want.wall[0] ||
+               got.wall[1] != want.wall[1] || got.wall[2] != want.wall[2] || got.B != want.B ||
+               got.radius != want.radius || got.mask_bytes != want.mask_bytes || got.f_bytes != want.f_bytes)) {
+        std::fclose(fp);
+        return fail(h, FLBM_E_INVAL, std::string(path) + ": lattice, walls or radius differ from this simulation");
+    }
+    ok = ok && std::fread(&fp_params, sizeof(fp_params), 1, fp) == 1 && std::fread(&st, sizeof(st), 1, fp) == 1 &&
+         std::fread(masks.data(), 1, want.mask_bytes, fp) == want.mask_bytes &&
+         std::fread(f.data(), 1, want.f_bytes, fp) == want.f_bytes;
+    std::fclose(fp);
+    if (!ok) return fail(h, FLBM_E_INVAL, std::string(path) + ": truncated checkpoint");
+    // Values derived from the parameters follow this handle's parameters.
+    if (h->kp.has_particle) {
+        const DevState s0 = initial_state(h->p, h->kp);
+        st.mp = s0.mp;
+        st.Ip = s0.Ip;
+        st.Fp = s0.Fp;
+        st.fc = (h->p.fluid_counterforce && st.nfluid > 0) ? -st.Fp / (double)st.nfluid : 0.0;
+        st.fc_f = (float)st.fc;
+    }
+    st.err = 0;
+    CK(h, cudaMemcpyAsync(h->st, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->masks, masks.data(), want.mask_bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->fbuf[h->cur], f.data(), want.f_bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
     return FLBM_OK;
 }
 
@@ -372,18 +400,7 @@ int flbm_observables(flbm_t* h, flbm_obs* out)
     CK(h, cudaMemcpyAsync(v, h->obs_out, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    out->mass[0] = v[0];
-    out->mass[1] = v[1];
-    for (int a = 0; a < 3; ++a) {
-        out->momentum[a] = v[2 + a];
-        out->particle_momentum[a] = s.mp * s.V[a];
-    }
-    out->kinetic = v[5];
-    out->pending_mass[0] = s.delta[0] * (double)s.nfluid;
-    out->pending_mass[1] = s.delta[1] * (double)s.nfluid;
-    out->nfluid = s.nfluid;
-    out->step = s.step;
-    out->nonfinite = (int64_t)v[6];
+    fill_obs(v, s, out);
     return out->nonfinite ? fail(h, FLBM_E_NONFINITE, "non-finite populations") : FLBM_OK;
 }
 
@@ -540,6 +557,8 @@ void flbm_destroy(flbm_t* h)
     cudaFree(h->scratch_rho);
     cudaFree(h->traj_dev);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    for (cudaGraphExec_t g : h->graph)
+        if (g) cudaGraphExecDestroy(g);
     delete[] h->traj_host;
     delete h;
 }

@@ -196,6 +196,7 @@ struct DevState {
     double ledger_bb[2];   // mass removed by the moving-wall term this step
     float delta_f[2];      // delta as float, read by the collide kernels
     float fc_f;            // fc as float
+    float Vf[3], Omf[3];   // V and Omega as float, read by the moving link rule
     uint32_t step_u32;     // step as the 32-bit Philox counter word
     int cur;               // index of the current mask
     int box0[3];           // origin of the particle box (periodic axes in [0, L))

@@ -22,7 +22,7 @@ constexpr int kThreads = 256;
 // Initial state: f = w_i rho_l0 (1 + a (2u - 1)), u from Philox counter
 // (0, node, 0, 1): first word for A, second for B.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_init(float* __restrict__ f, KParams P, float rho_a, float rho_b, float pert)
+static __global__ void __launch_bounds__(kThreads) k_init(float* __restrict__ f, KParams P, float rho_a, float rho_b, float pert)
 {
     const int x = blockIdx.x * P.tx + threadIdx.x;
     const int y = blockIdx.y * P.ty + threadIdx.y;
@@ -43,13 +43,10 @@ __global__ void __launch_bounds__(kThreads) k_init(float* __restrict__ f, KParam
 // ---------------------------------------------------------------------------
 // Densities of fluid nodes into the psi interior; 0 on particle nodes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_density(const float* __restrict__ f, float* __restrict__ psi,
-                                                      const DevState* __restrict__ st,
-                                                      const uint8_t* __restrict__ masks, KParams P)
+__device__ __forceinline__ void density_node(int x, int y, int z, const float* __restrict__ f, float* __restrict__ psi,
+                                             const DevState* __restrict__ st, const uint8_t* __restrict__ masks,
+                                             const KParams& P)
 {
-    const int x = blockIdx.x * P.tx + threadIdx.x;
-    const int y = blockIdx.y * P.ty + threadIdx.y;
-    const int z = blockIdx.z;
     if (x >= P.lx || y >= P.ly) return;
     const long long n = x + (long long)P.lx * (y + (long long)P.ly * z);
     bool solid = false;
@@ -70,16 +67,22 @@ __global__ void __launch_bounds__(kThreads) k_density(const float* __restrict__ 
     psi[P.padn + q] = rb;
 }
 
+static __global__ void __launch_bounds__(kThreads) k_density(const float* __restrict__ f, float* __restrict__ psi,
+                                                             const DevState* __restrict__ st,
+                                                             const uint8_t* __restrict__ masks, KParams P)
+{
+    density_node(blockIdx.x * P.tx + threadIdx.x, blockIdx.y * P.ty + threadIdx.y, blockIdx.z, f, psi, st, masks, P);
+}
+
 // ---------------------------------------------------------------------------
 // Virtual fluid layer (Section 2): a particle node with fluid neighbours gets
 // the mean density of those neighbours, +delta_rho for A and -delta_rho for
 // B, clipped at 0. One thread per node of the particle box.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_virtual(float* __restrict__ psi, const DevState* __restrict__ st,
-                                                      const uint8_t* __restrict__ masks, KParams P)
+__device__ __forceinline__ void virtual_node(int t, float* __restrict__ psi, const DevState* __restrict__ st,
+                                             const uint8_t* __restrict__ masks, const KParams& P)
 {
     const int B = P.B;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= B * B * B) return;
     const uint8_t* mask = masks + (size_t)st->cur * B * B * B;
     if (!mask[t]) return;
@@ -122,15 +125,27 @@ __global__ void __launch_bounds__(kThreads) k_virtual(float* __restrict__ psi, c
     psi[P.padn + q] = vb;
 }
 
+static __global__ void __launch_bounds__(kThreads) k_virtual(float* __restrict__ psi, const DevState* __restrict__ st,
+                                                             const uint8_t* __restrict__ masks, KParams P)
+{
+    virtual_node(blockIdx.x * blockDim.x + threadIdx.x, psi, st, masks, P);
+}
+
+// Shell nodes of the padded psi field: z faces (full padded planes), y faces
+// (interior z), x faces (interior y and z).
+__host__ __device__ __forceinline__ long long shell_count(const KParams& P)
+{
+    return 2LL * P.px * P.py + 2LL * P.px * P.lz + 2LL * P.ly * P.lz;
+}
+
 // ---------------------------------------------------------------------------
 // psi shell: every shell node either maps (through periodic axes) onto an
 // interior node, whose value it copies, or is a wall ghost, which takes the
 // mean over its fluid neighbours (neutral wetting, Section 3).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_shell(float* __restrict__ psi, const DevState* __restrict__ st,
-                                                    const uint8_t* __restrict__ masks, KParams P)
+__device__ __forceinline__ void shell_node(long long t, float* __restrict__ psi, const DevState* __restrict__ st,
+                                           const uint8_t* __restrict__ masks, const KParams& P)
 {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long nzf = 2LL * P.px * P.py;        // z faces, full padded planes
     const long long nyf = 2LL * P.px * P.lz;        // y faces, interior z
     const long long nxf = 2LL * P.ly * P.lz;        // x faces, interior y, z
@@ -200,6 +215,12 @@ __global__ void __launch_bounds__(kThreads) k_shell(float* __restrict__ psi, con
     psi[P.padn + dst] = sb * inv;
 }
 
+static __global__ void __launch_bounds__(kThreads) k_shell(float* __restrict__ psi, const DevState* __restrict__ st,
+                                                           const uint8_t* __restrict__ masks, KParams P)
+{
+    shell_node(blockIdx.x * (long long)blockDim.x + threadIdx.x, psi, st, masks, P);
+}
+
 }  // namespace flbm
 
 #include "flbm_step.cuh"
@@ -209,7 +230,7 @@ namespace flbm {
 // ---------------------------------------------------------------------------
 // Observables: per-tile FP64 partials, then one block sums them in order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_obs_tiles(const float* __restrict__ f, const DevState* __restrict__ st,
+static __global__ void __launch_bounds__(kThreads) k_obs_tiles(const float* __restrict__ f, const DevState* __restrict__ st,
                                                         const uint8_t* __restrict__ masks,
                                                         double* __restrict__ out, KParams P)
 {
@@ -247,7 +268,7 @@ __global__ void __launch_bounds__(kThreads) k_obs_tiles(const float* __restrict_
     }
 }
 
-__global__ void __launch_bounds__(1024) k_obs_final(const double* __restrict__ tiles, long long ntiles,
+static __global__ void __launch_bounds__(1024) k_obs_final(const double* __restrict__ tiles, long long ntiles,
                                                     double* __restrict__ out)
 {
     __shared__ double s_red[(1024 / 32) * 8];
@@ -260,7 +281,7 @@ __global__ void __launch_bounds__(1024) k_obs_final(const double* __restrict__ t
 }
 
 // Unpad psi interior into a dense [2][N] array.
-__global__ void k_unpad(const float* __restrict__ psi, float* __restrict__ out, KParams P)
+static __global__ void k_unpad(const float* __restrict__ psi, float* __restrict__ out, KParams P)
 {
     const int x = blockIdx.x * P.tx + threadIdx.x;
     const int y = blockIdx.y * P.ty + threadIdx.y;

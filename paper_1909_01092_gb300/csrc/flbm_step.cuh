@@ -53,6 +53,23 @@ __device__ __forceinline__ void box_muller(uint32_t w1, uint32_t w2, float& z0, 
     z1 = -r * s;
 }
 
+// FP32 sums over the particle links of one node.
+struct LinkSums {
+    float F[3] = {0.0f, 0.0f, 0.0f};    // force on the particle
+    float T[3] = {0.0f, 0.0f, 0.0f};    // torque about the node (lever c_i / 2)
+    float led[2] = {0.0f, 0.0f};        // mass put in by the moving link rule
+};
+
+// Adds the force m c_i acting at the link midpoint x + c_i / 2.
+__device__ __forceinline__ void link_add(LinkSums& s, float m, int cx, int cy, int cz)
+{
+    const float fr[3] = {m * cx, m * cy, m * cz};
+    s.F[0] += fr[0]; s.F[1] += fr[1]; s.F[2] += fr[2];
+    s.T[0] += 0.5f * (cy * fr[2] - cz * fr[1]);
+    s.T[1] += 0.5f * (cz * fr[0] - cx * fr[2]);
+    s.T[2] += 0.5f * (cx * fr[1] - cy * fr[0]);
+}
+
 // Density and momentum of one component from its 19 populations.
 __device__ __forceinline__ void moments(const float f[19], float& rho, float j[3])
 {
@@ -100,6 +117,20 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, co
     }
     const float rt = rhoA + rhoB;
 
+    // Particle links of this node: FP32 sums of force, torque about the node
+    // (lever c_i / 2) and mass ledger, moved into the FP64 accumulators once
+    // per node; relative position of the node to the particle centre in FP64.
+    LinkSums lk;
+    double rn[3] = {0.0, 0.0, 0.0};
+    float rnf[3] = {0.0f, 0.0f, 0.0f};
+    if (PARTICLE && solid_nb) {
+        rn[0] = rel_axis((double)x, st->X[0], P.lx, P.wall[0]);
+        rn[1] = rel_axis((double)y, st->X[1], P.ly, P.wall[1]);
+        rn[2] = rel_axis((double)z, st->X[2], P.lz, P.wall[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) rnf[a] = (float)rn[a];
+    }
+
     // Shan-Chen force, Eq. (sc-force), omega_i = w_i, psi = rho.
     float ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
     {
@@ -117,15 +148,8 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, co
             if (czv(i)) { ga[2] += (czv(i) * w) * pb; gb[2] += (czv(i) * w) * pa; }
             if (PARTICLE && (solid_nb >> i & 1u)) {
                 // Reaction on the particle of this pair force (virtual layer).
-                const double mag = (double)P.G * w * ((double)rhoA * pb + (double)rhoB * pa);
-                const double fr[3] = {mag * cxv(i), mag * cyv(i), mag * czv(i)};
-                const double r[3] = {rel_axis(x + 0.5 * cxv(i), st->X[0], P.lx, P.wall[0]),
-                                     rel_axis(y + 0.5 * cyv(i), st->X[1], P.ly, P.wall[1]),
-                                     rel_axis(z + 0.5 * czv(i), st->X[2], P.lz, P.wall[2])};
-                acc[0] += fr[0]; acc[1] += fr[1]; acc[2] += fr[2];
-                acc[3] += r[1] * fr[2] - r[2] * fr[1];
-                acc[4] += r[2] * fr[0] - r[0] * fr[2];
-                acc[5] += r[0] * fr[1] - r[1] * fr[0];
+                const float mag = P.G * w * (rhoA * pb + rhoB * pa);
+                link_add(lk, mag, cxv(i), cyv(i), czv(i));
             }
         }
     }
@@ -238,23 +262,17 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, co
             const uint32_t back_idx = n + P.dirN[19 * l + oppv(i)];
             if (PARTICLE && (solid_nb >> i & 1u)) {
                 // f_{-i}(x, t+1) = f*_i(x) - 6 w_i rho_l (u_b . c_i), u_b at the link midpoint.
-                const double r[3] = {rel_axis(x + 0.5 * cx, st->X[0], P.lx, P.wall[0]),
-                                     rel_axis(y + 0.5 * cy, st->X[1], P.ly, P.wall[1]),
-                                     rel_axis(z + 0.5 * cz, st->X[2], P.lz, P.wall[2])};
-                const double ub[3] = {st->V[0] + st->Om[1] * r[2] - st->Om[2] * r[1],
-                                      st->V[1] + st->Om[2] * r[0] - st->Om[0] * r[2],
-                                      st->V[2] + st->Om[0] * r[1] - st->Om[1] * r[0]};
-                const float ubc = (float)(ub[0] * cx + ub[1] * cy + ub[2] * cz);
+                const float r[3] = {rnf[0] + 0.5f * cx, rnf[1] + 0.5f * cy, rnf[2] + 0.5f * cz};
+                const float* V = st->Vf;
+                const float* Om = st->Omf;
+                const float ubc = (V[0] + Om[1] * r[2] - Om[2] * r[1]) * cx +
+                                  (V[1] + Om[2] * r[0] - Om[0] * r[2]) * cy +
+                                  (V[2] + Om[0] * r[1] - Om[1] * r[0]) * cz;
                 const float corr = 6.0f * wv(i) * rl * ubc;
                 const float back = fo[i] - corr;
                 fout[back_idx] = back;
-                const double dp = (double)fo[i] + (double)back;
-                const double fr[3] = {dp * cx, dp * cy, dp * cz};
-                acc[0] += fr[0]; acc[1] += fr[1]; acc[2] += fr[2];
-                acc[3] += r[1] * fr[2] - r[2] * fr[1];
-                acc[4] += r[2] * fr[0] - r[0] * fr[2];
-                acc[5] += r[0] * fr[1] - r[1] * fr[0];
-                acc[6 + l] += corr;
+                link_add(lk, fo[i] + back, cx, cy, cz);
+                lk.led[l] += corr;
                 continue;
             }
             int off = 0;
@@ -265,26 +283,44 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, co
             fout[wall ? back_idx : push_idx] = fo[i];
         }
     }
+    if (PARTICLE && solid_nb) {
+        const double F[3] = {lk.F[0], lk.F[1], lk.F[2]};
+        acc[0] += F[0]; acc[1] += F[1]; acc[2] += F[2];
+        acc[3] += rn[1] * F[2] - rn[2] * F[1] + lk.T[0];
+        acc[4] += rn[2] * F[0] - rn[0] * F[2] + lk.T[1];
+        acc[5] += rn[0] * F[1] - rn[1] * F[0] + lk.T[2];
+        acc[6] += lk.led[0];
+        acc[7] += lk.led[1];
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Bulk tiles: every tile not next to the particle.
 // ---------------------------------------------------------------------------
+// Thread (tx, ty) of tile (bx, by, bz).
 template <bool NOISE, bool TAU1>
-__global__ void __launch_bounds__(kThreadsStep, FLBM_BULK_MINBLOCKS)
-    k_collide_bulk(const float* __restrict__ fin, float* __restrict__ fout, const float* __restrict__ psi,
-                   const DevState* __restrict__ st, KParams P)
+__device__ __forceinline__ void bulk_tile(int bx, int by, int bz, int tx, int ty, const float* __restrict__ fin,
+                                          float* __restrict__ fout, const float* __restrict__ psi,
+                                          const DevState* __restrict__ st, const KParams& P)
 {
     if (P.has_particle) {
         const int o[3] = {st->box0[0], st->box0[1], st->box0[2]};
-        if (tile_near(blockIdx.x, blockIdx.y, blockIdx.z, o, P)) return;
+        if (tile_near(bx, by, bz, o, P)) return;
     }
-    const int x = blockIdx.x * P.tx + threadIdx.x;
-    const int y = blockIdx.y * P.ty + threadIdx.y;
-    const int z = blockIdx.z;
+    const int x = bx * P.tx + tx;
+    const int y = by * P.ty + ty;
+    const int z = bz;
     if (x >= P.lx || y >= P.ly) return;
     const uint32_t n = (uint32_t)x + (uint32_t)P.lx * ((uint32_t)y + (uint32_t)P.ly * (uint32_t)z);
     collide_node<NOISE, false, TAU1>(x, y, z, n, fin, fout, psi, st, P, 0u, nullptr);
+}
+
+template <bool NOISE, bool TAU1>
+static __global__ void __launch_bounds__(kThreadsStep, FLBM_BULK_MINBLOCKS)
+    k_collide_bulk(const float* __restrict__ fin, float* __restrict__ fout, const float* __restrict__ psi,
+                   const DevState* __restrict__ st, KParams P)
+{
+    bulk_tile<NOISE, TAU1>(blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, fin, fout, psi, st, P);
 }
 
 // Candidate c on one axis -> tile index, or -1. e0 = first coordinate of the
@@ -305,30 +341,34 @@ __device__ __forceinline__ int candidate_tile(int c, int o, int T, int gt, int L
 // Near tiles: a fixed grid of candidate tiles around the particle box; each
 // near tile reduces force, torque and mass ledger into partials[candidate].
 // ---------------------------------------------------------------------------
+// Candidate (cx, cy, cz) of the grid around the particle box; thread (tx, ty)
+// of the tile, tid = tx + TX ty. Every thread of the block must call this.
 template <bool NOISE, bool TAU1>
-__global__ void __launch_bounds__(kThreadsStep)
-    k_collide_near(const float* __restrict__ fin, float* __restrict__ fout, const float* __restrict__ psi,
-                   const DevState* __restrict__ st, const uint8_t* __restrict__ masks,
-                   double* __restrict__ partials, KParams P)
+__device__ __forceinline__ void near_tile(int cx, int cy, int cz, int tx, int ty, int tid,
+                                          const float* __restrict__ fin, float* __restrict__ fout,
+                                          const float* __restrict__ psi, const DevState* __restrict__ st,
+                                          const uint8_t* __restrict__ masks, double* __restrict__ partials,
+                                          const KParams& P)
 {
     __shared__ double s_red[(kThreadsStep / 32) * 8];
     __shared__ double s_out[8];
     const int o[3] = {st->box0[0], st->box0[1], st->box0[2]};
-    const int bx = candidate_tile(blockIdx.x, o[0], P.tx, P.gx, P.lx, P.wall[0]);
-    const int by = candidate_tile(blockIdx.y, o[1], P.ty, P.gy, P.ly, P.wall[1]);
-    const int bz = candidate_tile(blockIdx.z, o[2], 1, P.lz, P.lz, P.wall[2]);
-    const long long cand = blockIdx.x + (long long)P.ncx * (blockIdx.y + (long long)P.ncy * blockIdx.z);
+    const int bx = candidate_tile(cx, o[0], P.tx, P.gx, P.lx, P.wall[0]);
+    const int by = candidate_tile(cy, o[1], P.ty, P.gy, P.ly, P.wall[1]);
+    const int bz = candidate_tile(cz, o[2], 1, P.lz, P.lz, P.wall[2]);
+    const long long cand = cx + (long long)P.ncx * (cy + (long long)P.ncy * cz);
     const bool near = bx >= 0 && by >= 0 && bz >= 0 && tile_near(bx, by, bz, o, P);
     if (!near) {
-        if (threadIdx.x < 8 && threadIdx.y == 0) partials[cand * 8 + threadIdx.x] = 0.0;
+        if (tid < 8) partials[cand * 8 + tid] = 0.0;
         return;
     }
     const uint8_t* mask = masks + (size_t)st->cur * P.B * P.B * P.B;
-    const int x = bx * P.tx + threadIdx.x;
-    const int y = by * P.ty + threadIdx.y;
+    const int x = bx * P.tx + tx;
+    const int y = by * P.ty + ty;
     const int z = bz;
     const bool inside = x < P.lx && y < P.ly;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t links = 0;
     if (inside && !is_solid(x, y, z, o, mask, P)) {
         const int L[3] = {P.lx, P.ly, P.lz};
         uint32_t solid_nb = 0;
@@ -347,12 +387,25 @@ __global__ void __launch_bounds__(kThreadsStep)
         }
         const uint32_t n = (uint32_t)x + (uint32_t)P.lx * ((uint32_t)y + (uint32_t)P.ly * (uint32_t)z);
         collide_node<NOISE, true, TAU1>(x, y, z, n, fin, fout, psi, st, P, solid_nb, acc);
+        links = solid_nb;
+    }
+    if (!__syncthreads_or(links != 0)) {  // no particle link in this tile
+        if (tid < 8) partials[cand * 8 + tid] = 0.0;
+        return;
     }
     block_sum8<kThreadsStep>(acc, s_red, s_out);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) partials[cand * 8 + k] = s_out[k];
-    }
+    if (tid < 8) partials[cand * 8 + tid] = s_out[tid];
+    __syncthreads();  // s_out is reused by the next tile of a persistent block
+}
+
+template <bool NOISE, bool TAU1>
+static __global__ void __launch_bounds__(kThreadsStep, TAU1 ? 3 : 2)
+    k_collide_near(const float* __restrict__ fin, float* __restrict__ fout, const float* __restrict__ psi,
+                   const DevState* __restrict__ st, const uint8_t* __restrict__ masks,
+                   double* __restrict__ partials, KParams P)
+{
+    near_tile<NOISE, TAU1>(blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y,
+                           threadIdx.x + blockDim.x * threadIdx.y, fin, fout, psi, st, masks, partials, P);
 }
 
 __device__ __forceinline__ void box_origin(const double X[3], const KParams& P, int o[3])
@@ -394,8 +447,8 @@ __device__ __forceinline__ bool box_node_inside(int t, const int o[3], const dou
 // (1) Sum the near-tile partials in candidate order, leap-frog update (FP64),
 // new box origin. One block.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_update(DevState* __restrict__ st, const double* __restrict__ partials,
-                                                KParams P)
+__device__ __forceinline__ void update_particle(DevState* __restrict__ st, const double* __restrict__ partials,
+                                                const KParams& P)
 {
     __shared__ double s_red[(256 / 32) * 8];
     __shared__ double s_out[8];
@@ -417,6 +470,8 @@ __global__ void __launch_bounds__(256) k_update(DevState* __restrict__ st, const
         st->Vavg[a] = 0.5 * (st->V[a] + vn);
         st->V[a] = vn;
         st->Om[a] += st->T[a] / st->Ip;
+        st->Vf[a] = (float)st->V[a];
+        st->Omf[a] = (float)st->Om[a];
         double xn = st->X[a] + vn;
         if (!P.wall[a]) xn -= L[a] * floor(xn / L[a]);
         st->X[a] = xn;
@@ -428,13 +483,20 @@ __global__ void __launch_bounds__(256) k_update(DevState* __restrict__ st, const
     st->box_next[0] = o[0]; st->box_next[1] = o[1]; st->box_next[2] = o[2];
 }
 
+static __global__ void __launch_bounds__(256) k_update(DevState* __restrict__ st, const double* __restrict__ partials,
+                                                       KParams P)
+{
+    update_particle(st, partials, P);
+}
+
 // (2) Particle nodes at the new position -> mask[1 - cur]; per-block counts.
-__global__ void __launch_bounds__(256) k_mark_next(const DevState* __restrict__ st, uint8_t* __restrict__ masks,
-                                                   int* __restrict__ counts, KParams P)
+// Block blk of 256 box entries.
+__device__ __forceinline__ void mark_next_block(int blk, const DevState* __restrict__ st, uint8_t* __restrict__ masks,
+                                                int* __restrict__ counts, const KParams& P)
 {
     __shared__ int s_cnt[256 / 32];
     const int B3 = P.B * P.B * P.B;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blk * 256 + threadIdx.x;
     const int o[3] = {st->box_next[0], st->box_next[1], st->box_next[2]};
     const double X[3] = {st->X[0], st->X[1], st->X[2]};
     int in = 0;
@@ -448,21 +510,28 @@ __global__ void __launch_bounds__(256) k_mark_next(const DevState* __restrict__ 
     if (threadIdx.x == 0) {
         int a = 0;
         for (int w = 0; w < 256 / 32; ++w) a += s_cnt[w];
-        counts[blockIdx.x] = a;
+        counts[blk] = a;
     }
+    __syncthreads();
+}
+
+static __global__ void __launch_bounds__(256) k_mark_next(const DevState* __restrict__ st, uint8_t* __restrict__ masks,
+                                                          int* __restrict__ counts, KParams P)
+{
+    mark_next_block(blockIdx.x, st, masks, counts, P);
 }
 
 // (3) Cover (new box) and uncover (old box) on the post-stream populations f;
 // per-block FP64 partials of impulse, angular impulse and mass ledger.
-__global__ void __launch_bounds__(256) k_cover(float* __restrict__ f, const DevState* __restrict__ st,
-                                               const uint8_t* __restrict__ masks, double* __restrict__ parts,
-                                               KParams P)
+__device__ __forceinline__ void cover_block(int blk, float* __restrict__ f, const DevState* __restrict__ st,
+                                            const uint8_t* __restrict__ masks, double* __restrict__ parts,
+                                            const KParams& P)
 {
     __shared__ double s_red[(256 / 32) * 8];
     __shared__ double s_out[8];
     const int B = P.B;
     const int B3 = B * B * B;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blk * 256 + threadIdx.x;
     const int cur = st->cur;
     const int o_old[3] = {st->box0[0], st->box0[1], st->box0[2]};
     const int o_new[3] = {st->box_next[0], st->box_next[1], st->box_next[2]};
@@ -555,14 +624,22 @@ __global__ void __launch_bounds__(256) k_cover(float* __restrict__ f, const DevS
         }
     }
     block_sum8<256>(acc, s_red, s_out);
-    if (threadIdx.x < 8) parts[blockIdx.x * 8 + threadIdx.x] = s_out[threadIdx.x];
+    if (threadIdx.x < 8) parts[blk * 8 + threadIdx.x] = s_out[threadIdx.x];
+    __syncthreads();
+}
+
+static __global__ void __launch_bounds__(256) k_cover(float* __restrict__ f, const DevState* __restrict__ st,
+                                                      const uint8_t* __restrict__ masks, double* __restrict__ parts,
+                                                      KParams P)
+{
+    cover_block(blockIdx.x, f, st, masks, parts, P);
 }
 
 // (4) Bookkeeping for the next step: pending impulses, fluid count, mass
 // correction delta_l = ledger_l / N_fluid, counterforce, box swap, step + 1.
 // Without a particle only the step counter advances. One block.
-__global__ void __launch_bounds__(256) k_finish(DevState* __restrict__ st, const int* __restrict__ counts,
-                                                const double* __restrict__ parts, int nblocks, KParams P)
+__device__ __forceinline__ void finish_step(DevState* __restrict__ st, const int* __restrict__ counts,
+                                            const double* __restrict__ parts, int nblocks, const KParams& P)
 {
     __shared__ double s_red[(256 / 32) * 8];
     __shared__ double s_out[8];
@@ -604,10 +681,16 @@ __global__ void __launch_bounds__(256) k_finish(DevState* __restrict__ st, const
     st->step_u32 = (uint32_t)st->step;
 }
 
+static __global__ void __launch_bounds__(256) k_finish(DevState* __restrict__ st, const int* __restrict__ counts,
+                                                       const double* __restrict__ parts, int nblocks, KParams P)
+{
+    finish_step(st, counts, parts, nblocks, P);
+}
+
 // Mark the particle nodes of the current position into mask[cur] and set the
 // box origin, fluid count and counterforce (creation and flbm_set_particle).
 // One block; FP64 inside test as in the step.
-__global__ void __launch_bounds__(1024) k_mark(DevState* st, uint8_t* masks, KParams P)
+static __global__ void __launch_bounds__(1024) k_mark(DevState* st, uint8_t* masks, KParams P)
 {
     __shared__ long long s_c[1024];
     __shared__ int s_o[3];
@@ -639,6 +722,10 @@ __global__ void __launch_bounds__(1024) k_mark(DevState* st, uint8_t* masks, KPa
         st->delta_f[0] = (float)st->delta[0];
         st->delta_f[1] = (float)st->delta[1];
         st->step_u32 = (uint32_t)st->step;
+        for (int a = 0; a < 3; ++a) {
+            st->Vf[a] = (float)st->V[a];
+            st->Omf[a] = (float)st->Om[a];
+        }
     }
 }
 
