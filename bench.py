@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-ensemble", action="store_true", help="skip the 128-replica ensemble measurement")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the 128-replica ensemble and the adjoint measurements")
     ap.add_argument("--lz", type=int, default=512, help="channel length (shorter only for profiler captures)")
     return ap.parse_args()
 
@@ -141,6 +142,27 @@ def dist_init():
     return world, rank, local
 
 
+def rank_workload(W, rank: int, lz: int = 512) -> dict:
+    """Rank r's simulation: the benchmarked channel with Philox replica index r
+    (independent noise; replicas only, no data exchanged between ranks)."""
+    return W.channel_large(replica=rank, lz=lz)
+
+
+def max_over_ranks(value: float, dist=None, device: str = "cpu") -> float:
+    """The largest of every rank's value (the job's time is its slowest rank)."""
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(nodes: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job node updates per second over all ranks, in millions."""
+    return nodes * steps * world / (ms * 1e-3) / 1e6
+
+
 def run_reference(args):
     world, rank, _ = dist_init()
     if rank != 0:
@@ -216,6 +238,38 @@ def ensemble_bench(binding, W, steps: int = 100) -> dict:
             "speedup": ms1 / ms}
 
 
+def adjoint_bench(binding, W, steps: int = 2000, every: int = 100) -> dict:
+    """Gradient of the time-averaged settling velocity on the 64x64x128
+    noise-free channel (R=8, delta_rho=0.3, G=1.2) by the adjoint with
+    checkpoints every `every` steps, against the plain forward step of the
+    same channel."""
+    import torch
+
+    p = W.channel_adjoint()
+    nodes = p["lx"] * p["ly"] * p["lz"]
+    fwd = binding.Sim(p)
+    fwd.step(5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(fwd.stream)
+    fwd.step(steps)
+    e1.record(fwd.stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / steps
+    fwd.close()
+    sim = binding.Sim(p)
+    r = sim.adjoint(steps, every)
+    sim.close()
+    ms = (r["ms_forward"] + r["ms_reverse"]) / steps
+    return {"workload": "adjoint_channel_64x64x128_R8_drho0.3_T2000_K100", "steps": steps, "checkpoint_every": every,
+            "J": r["J"], "grad": {"g": r["dJ_dg"], "delta_rho": r["dJ_ddelta_rho"], "G": r["dJ_dG"]},
+            "ms_per_step": ms, "ms_forward_per_step": r["ms_forward"] / steps,
+            "ms_reverse_per_step": r["ms_reverse"] / steps, "mlups": nodes / (ms * 1e-3) / 1e6,
+            "device_bytes": r["device_bytes"], "plain_forward": {"ms_per_step": fwd_ms,
+                                                                 "mlups": nodes / (fwd_ms * 1e-3) / 1e6},
+            "cost_vs_plain_forward": ms / fwd_ms}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -229,7 +283,7 @@ def run_ours(args):
 
     from paper_1909_01092_gb300 import binding, workloads as W
 
-    p = W.channel_large(replica=rank, lz=args.lz)
+    p = rank_workload(W, rank, args.lz)
     nodes = p["lx"] * p["ly"] * p["lz"]
     sim = binding.Sim(p)
     stream = sim.stream
@@ -253,11 +307,8 @@ def run_ours(args):
     ck = clocks.stop()
     launches = sim.launches()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = nodes * args.steps * world / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = aggregate_mlups(nodes, args.steps, world, ms_max)
 
     # End to end through the C-ABI with host buffers: the initial populations
     # go host->device from pinned memory, every step's particle record and the
@@ -269,13 +320,10 @@ def run_ours(args):
     t0 = time.perf_counter()
     sim.run_host(f_host, args.steps, f_out=f_out, traj=True)
     t1 = time.perf_counter()
-    tt = torch.tensor([t1 - t0], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(t1 - t0, dist, "cuda")
     fbytes = f_host.nbytes
     rec = binding.record_bytes()  # bytes of one particle record
-    e2e = {"value": nodes * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
+    e2e = {"value": aggregate_mlups(nodes, args.steps, world, e2e_s * 1e3), "unit": "MLUPS",
            "h2d_bytes_per_step": fbytes / args.steps, "d2h_bytes_per_step": (fbytes + rec * args.steps) / args.steps,
            "api": "flbm_run_host"}
 
@@ -292,10 +340,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
-    ens = None
+    ens = adj = None
     if rank == 0 and world == 1 and not args.no_ensemble:
         sim.close()
         ens = ensemble_bench(binding, W)
+        adj = adjoint_bench(binding, W)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -304,7 +353,7 @@ def run_ours(args):
                            "radius": p["radius"], "g": p["g"], "G": p["G"], "walls": "x,y", "replicas_per_gpu": 1,
                            "l2": "inputs larger than L2 (2.55 GB of populations), no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches,
-                "ensemble": ens}
+                "ensemble": ens, "adjoint": adj}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:

@@ -248,6 +248,39 @@ const char* flbm_error_string(int code);
 const char* flbm_last_error(const flbm_t* h);
 
 /* ------------------------------------------------------------------------
+ * Adjoint of the noise-free step.
+ * ------------------------------------------------------------------------ */
+
+/* Result of flbm_adjoint_run (host memory, filled by the library). */
+typedef struct flbm_adjoint_result {
+    double J;                /* (1/T) sum_{n<T} Vavg_z(n): time-averaged settling velocity */
+    double dJ_dg;            /* dJ / d g (body-force density of Section 3, Eq. (fp)) */
+    double dJ_ddelta_rho;    /* dJ / d delta_rho (wetting shift of the virtual layer, Section 2) */
+    double dJ_dG;            /* dJ / d G (Shan-Chen coupling, Eq. (sc-force)) */
+    int64_t steps;           /* T */
+    int32_t checkpoint_every;/* K actually used (min(K, T)) */
+    int32_t reserved;
+    double device_bytes;     /* device memory the call allocated (checkpoints, tape, adjoint fields) */
+    double ms_forward;       /* device time of the forward run with checkpoints */
+    double ms_reverse;       /* device time of the segment recomputes and the reverse sweep */
+} flbm_adjoint_result;
+
+/* Run T = nsteps steps from h's current state and return J and its gradient
+ * with respect to (g, delta_rho, G) by the discrete adjoint of the step,
+ * with the state checkpointed every checkpoint_every steps and each segment
+ * recomputed (with a tape of the moments rho_l, j_l) before it is swept
+ * backwards: memory (T/K) x populations + K x 8 floats per node. The
+ * adjoint holds the step's discrete sets fixed (particle nodes, links,
+ * covered and uncovered nodes): J is differentiated along the forward
+ * trajectory. On return h has advanced T steps, exactly as flbm_step(h, T)
+ * would leave it. The paper computes no gradients; this differentiates its
+ * noise-free method.
+ * Requires a particle (radius > 0), kT = 0, every relaxation time 1 and
+ * fluid_counterforce = 0: FLBM_E_UNSUPPORTED otherwise. Synchronises.
+ * Errors: FLBM_E_INVAL, FLBM_E_UNSUPPORTED, FLBM_E_NOMEM, FLBM_E_CUDA. */
+int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_every, flbm_adjoint_result* out);
+
+/* ------------------------------------------------------------------------
  * Batched ensemble: many independent simulations (replicas) advanced
  * together. The paper's velocity statistics (Section 3) are averages over
  * noise realisations and channel geometries; an ensemble runs them as one

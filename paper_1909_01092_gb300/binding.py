@@ -24,12 +24,19 @@ EXPORTS = (
     "flbm_read_fields", "flbm_write_fields", "flbm_set_particle", "flbm_run_host",
     "flbm_last_launch_count", "flbm_destroy", "flbm_error_string", "flbm_last_error",
     "flbm_step_timed", "flbm_kernel_name", "flbm_observables_noalloc",
-    "flbm_checkpoint", "flbm_restore", "flbm_use_graphs",
+    "flbm_checkpoint", "flbm_restore", "flbm_use_graphs", "flbm_adjoint_run",
     "flbm_ensemble_create", "flbm_ensemble_step", "flbm_ensemble_tune", "flbm_ensemble_config",
     "flbm_ensemble_particles", "flbm_ensemble_read_fields", "flbm_ensemble_observables", "flbm_ensemble_nodes",
     "flbm_ensemble_last_launch_count", "flbm_ensemble_last_error", "flbm_ensemble_destroy",
 )
 NKERNELS = 5
+
+
+class AdjResult(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_double), ("dJ_dg", ctypes.c_double), ("dJ_ddelta_rho", ctypes.c_double),
+                ("dJ_dG", ctypes.c_double), ("steps", ctypes.c_int64), ("checkpoint_every", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("device_bytes", ctypes.c_double), ("ms_forward", ctypes.c_double),
+                ("ms_reverse", ctypes.c_double)]
 
 
 class EnsConfig(ctypes.Structure):
@@ -100,6 +107,7 @@ def load(build_if_missing: bool = True):
         lib.flbm_checkpoint.argtypes = [vp, ctypes.c_char_p]
         lib.flbm_restore.argtypes = [vp, ctypes.c_char_p]
         lib.flbm_use_graphs.argtypes = [vp, ctypes.c_int]
+        lib.flbm_adjoint_run.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(AdjResult)]
         ens_p = ctypes.POINTER(EnsConfig)
         lib.flbm_ensemble_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, ens_p, vp,
                                              ctypes.POINTER(vp)]
@@ -224,6 +232,15 @@ class Sim:
 
     def step(self, n: int = 1) -> None:
         self._check(self.lib.flbm_step(self.h, int(n)), "flbm_step")
+
+    def adjoint(self, steps: int, checkpoint_every: int = 100) -> dict:
+        """J = time-averaged settling velocity over the next `steps` steps and
+        its gradient (dJ/dg, dJ/d delta_rho, dJ/dG) by the discrete adjoint;
+        the simulation advances `steps` steps."""
+        r = AdjResult()
+        self._check(self.lib.flbm_adjoint_run(self.h, int(steps), int(checkpoint_every), ctypes.byref(r)),
+                    "flbm_adjoint_run")
+        return {k: getattr(r, k) for k, _ in AdjResult._fields_ if k != "reserved"}
 
     def use_graphs(self, enable: bool = True) -> None:
         """Replay flbm_step as captured two-step CUDA graphs (needs a
@@ -374,3 +391,30 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+def settling_velocity(p: dict, steps: int, checkpoint_every: int = 100, v0=None):
+    """torch.autograd.Function factory: returns f(g, delta_rho, G) -> J, the
+    time-averaged settling velocity of `steps` noise-free steps of workload
+    `p` (started at rest, or with particle velocity v0), whose backward pass
+    is the hand-written adjoint of the step (flbm_adjoint_run)."""
+    import torch
+
+    class _SettlingVelocity(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, g, delta_rho, G):
+            q = dict(p, g=float(g), delta_rho=float(delta_rho), G=float(G))
+            sim = Sim(q)
+            if v0 is not None:
+                sim.set_particle(q["pos0"], v0, (0.0, 0.0, 0.0))
+            r = sim.adjoint(steps, checkpoint_every)
+            sim.close()
+            ctx.save_for_backward(torch.tensor([r["dJ_dg"], r["dJ_ddelta_rho"], r["dJ_dG"]], dtype=torch.float64))
+            return torch.tensor(r["J"], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (gr,) = ctx.saved_tensors
+            return gout * gr[0], gout * gr[1], gout * gr[2]
+
+    return _SettlingVelocity.apply

@@ -12,41 +12,9 @@
 #include <vector>
 
 #include "flbm.h"
-#include "flbm_host.cuh"
+#include "flbm_sim.cuh"
 
 using namespace flbm;
-
-struct flbm_sim {
-    flbm_params p;
-    KParams kp;
-    cudaStream_t stream = nullptr;
-    float* fbuf[2] = {nullptr, nullptr};
-    void* f_owned = nullptr;
-    int cur = 0;  // fbuf[cur] holds the current state
-    float* psi = nullptr;
-    DevState* st = nullptr;
-    uint8_t* masks = nullptr;
-    double* partials = nullptr;    // per candidate near tile: force, torque, ledger
-    int* box_counts = nullptr;      // per block of the particle box: particle nodes
-    double* box_parts = nullptr;    // per block of the particle box: cover/uncover sums
-    int box_blocks = 0;
-    long long ncand = 0;
-    double* obs_tiles = nullptr;
-    double* obs_out = nullptr;
-    float* scratch_rho = nullptr;
-    DevState* traj_dev = nullptr;
-    size_t traj_cap = 0;
-    DevState* traj_host = nullptr;
-    size_t traj_host_cap = 0;
-    std::vector<cudaEvent_t> events;  // pool for flbm_step_timed
-    bool use_graphs = false;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two steps starting from cur = 0 / 1
-    int64_t graph_launches[2] = {0, 0};            // kernels in each graph
-    dim3 grid, block;
-    long long ntiles = 0;
-    int64_t launches = 0;
-    std::string err;
-};
 
 namespace {
 
@@ -208,6 +176,11 @@ void fill_header(const flbm_sim* h, CkptHeader* hd)
 }
 
 }  // namespace
+
+namespace flbm {
+int sim_step(flbm_sim* h, cudaEvent_t* ev) { return launch_step(h, ev); }
+int sim_fail(flbm_sim* h, int code, const std::string& msg) { return fail(h, code, msg); }
+}  // namespace flbm
 
 extern "C" {
 

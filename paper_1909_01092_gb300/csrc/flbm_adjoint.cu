@@ -1,0 +1,1059 @@
+// Discrete adjoint of the noise-free FLBM step (declared in include/flbm.h as
+// flbm_adjoint_run): gradient of the time-averaged settling velocity
+//   J = (1/T) sum_{n<T} Vavg_z(n),  Vavg(n) = (V_n + V_{n+1}) / 2,
+// with respect to the body force g of Eq. (fp), the wetting shift delta_rho of
+// the virtual layer (Section 2) and the Shan-Chen coupling G of Eq. (sc-force).
+//
+// Scope: kT = 0, every relaxation time 1 (the paper's choice), no fluid
+// counterforce. The sets of particle nodes, links and covered/uncovered nodes
+// of each step are those of the forward run (the map is piecewise smooth in
+// the parameters; between changes of these sets it is differentiated exactly).
+//
+// Structure. With tau = 1 the populations of a node enter a step only through
+// rho_l = sum_i f_li and j_l = sum_i f_li c_i, so the adjoint of the
+// post-streaming populations is affine in c_i:
+//     lambda_f_li(x) = a_l(x) + c_i . b_l(x)
+// and the adjoint state is the field (a_A, a_B, b_A, b_B): 8 floats per node.
+// The forward run keeps a checkpoint every K steps; each segment is
+// recomputed from its checkpoint while a tape of the moments (rho_l, j_l: 8
+// floats per node), the particle record and the particle masks of every step
+// is written, and the segment is then swept backwards. Per reverse step:
+//   ka_pre       adjoint of the mass ledger (delta_l = ledger_l / N_fluid)
+//   ka_cover     adjoint of cover/uncover at the new position
+//   ka_cover_mean  uncovered nodes' neighbour means -> a_l of those neighbours
+//   ka_update    leap-frog Newton-Euler update (FP64), dJ/dg
+//   ka_psi_tape, k_virtual, k_shell   density field of the step from the tape
+//   ka_node_bulk, ka_node_near  streaming (pull of the adjoint), moving
+//                links, Shan-Chen reaction, collision (flbm_adjoint_math.h)
+//                per fluid node; tiles away from / near the particle
+//   ka_lpsi, ka_lpsi_shell  adjoint of psi at particle nodes (virtual layer,
+//                Shan-Chen reaction) and wall ghosts (mean over fluid neighbours)
+//   ka_final     a_l of fluid nodes: Shan-Chen stencil transposed, plus the
+//                shares of the neighbour means they entered
+//   ka_reduce    per-tile partials -> particle adjoint, dJ/dG, dJ/d delta_rho
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "flbm.h"
+#include "flbm_adjoint_math.h"
+#include "flbm_sim.cuh"
+
+using namespace flbm;
+
+namespace flbm_adjoint {
+
+// Adjoint of the particle state and gradient sums, FP64 (one per run).
+struct AdjState {
+    double lX[3], lV[3], lOm[3], lP[3], lL[3], ld[2];  // adjoint of the step's input state (n+1 on entry, n on exit)
+    double lF[3], lT[3], lled[2];                      // adjoint of the step's force, torque, mass ledger
+    double grad[3];                                    // dJ/dg, dJ/d delta_rho, dJ/dG
+    double J;                                          // sum of Vavg_z over the forward steps
+    float lFf[3], lTf[3], lledf[2], lPf[3], lLf[3];    // float copies for the node kernels
+};
+
+// Type of the adjoint fields (a, b, lambda g, lambda psi) and of the node
+// arithmetic that produces them. Double by default: with float32 the
+// adjoint of a weakly coupled parameter (G in a dilute mixture) loses about
+// 1e-3 relative accuracy over a few tens of steps, because the adjoint
+// density field carries large smooth parts whose neighbour differences set
+// the momentum adjoint. Building with -DFLBM_ADJ_REAL=float trades that for
+// speed.
+#ifndef FLBM_ADJ_REAL
+#define FLBM_ADJ_REAL double
+#endif
+using adj_t = FLBM_ADJ_REAL;
+
+constexpr int kT = 256;  // threads per block
+constexpr int kNodeParts = 12;  // per tile: lX[3], lV[3], lOm[3], dJ/dG, ld[2]
+
+// Periodic-aware neighbour of (x,y,z) along c; false if it leaves through a wall.
+__device__ __forceinline__ bool nbr(int x, int y, int z, int cx, int cy, int cz, const KParams& P, int q[3])
+{
+    const int c[3] = {x + cx, y + cy, z + cz};
+    const int L[3] = {P.lx, P.ly, P.lz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int v = c[a];
+        if (v < 0 || v >= L[a]) {
+            if (P.wall[a]) return false;
+            v += (v < 0) ? L[a] : -L[a];
+        }
+        q[a] = v;
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t lin(int x, int y, int z, const KParams& P)
+{
+    return (uint32_t)x + (uint32_t)P.lx * ((uint32_t)y + (uint32_t)P.ly * (uint32_t)z);
+}
+
+__device__ __forceinline__ const uint8_t* cur_mask(const DevState* s, const uint8_t* masks, const KParams& P)
+{
+    return masks + (size_t)s->cur * P.B * P.B * P.B;
+}
+
+__device__ __forceinline__ bool solid_at(int x, int y, int z, const DevState* s, const uint8_t* m, const KParams& P)
+{
+    if (!P.has_particle) return false;
+    const int o[3] = {s->box0[0], s->box0[1], s->box0[2]};
+    return is_solid(x, y, z, o, m, P);
+}
+
+// ---------------------------------------------------------------------------
+// Moments tape: rho_A, rho_B, j_A, j_B of every node (raw sums of the
+// populations in the buffer, particle nodes included).
+// ---------------------------------------------------------------------------
+static __global__ void __launch_bounds__(kT) ka_tape(const float* __restrict__ f, float* __restrict__ tape, KParams P)
+{
+    const int x = blockIdx.x * P.tx + threadIdx.x;
+    const int y = blockIdx.y * P.ty + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= P.lx || y >= P.ly) return;
+    const uint32_t n = lin(x, y, z, P);
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        float fl[19], r, j[3];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) fl[i] = f[n + P.dirN[19 * l + i]];
+        r = 0.0f;
+        j[0] = j[1] = j[2] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            r += fl[i];
+            j[0] += cxv(i) * fl[i];
+            j[1] += cyv(i) * fl[i];
+            j[2] += czv(i) * fl[i];
+        }
+        tape[(size_t)l * P.N + n] = r;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) tape[(size_t)(2 + 3 * l + a) * P.N + n] = j[a];
+    }
+}
+
+// Sum of Vavg_z of the step just taken (one thread).
+static __global__ void ka_accJ(const DevState* __restrict__ st, AdjState* __restrict__ adj)
+{
+    adj->J += st->Vavg[2];
+}
+
+// Interior of the density field of a step from its tape (0 on particle nodes).
+static __global__ void __launch_bounds__(kT) ka_psi_tape(const float* __restrict__ tape, float* __restrict__ psi,
+                                                         const DevState* __restrict__ s, const uint8_t* __restrict__ masks,
+                                                         KParams P)
+{
+    const int x = blockIdx.x * P.tx + threadIdx.x;
+    const int y = blockIdx.y * P.ty + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= P.lx || y >= P.ly) return;
+    const uint32_t n = lin(x, y, z, P);
+    const bool sol = solid_at(x, y, z, s, cur_mask(s, masks, P), P);
+    const long long q = pad_index(x, y, z, P);
+    psi[q] = sol ? 0.0f : tape[n];
+    psi[P.padn + q] = sol ? 0.0f : tape[P.N + n];
+}
+
+// ---------------------------------------------------------------------------
+// Mass ledger: delta_l(n+1) = ledger_l / N_fluid(n+1). Float copies of the
+// adjoints the box and node kernels read. One thread.
+// ---------------------------------------------------------------------------
+static __global__ void ka_pre(AdjState* __restrict__ a, const DevState* __restrict__ s1)
+{
+    for (int l = 0; l < 2; ++l) {
+        a->lled[l] = a->ld[l] / (double)s1->nfluid;
+        a->lledf[l] = (float)a->lled[l];
+    }
+    for (int k = 0; k < 3; ++k) {
+        a->lPf[k] = (float)a->lP[k];
+        a->lLf[k] = (float)a->lL[k];
+    }
+}
+
+// Modes 0..9 of sum_i e_k(c_i) f_i (the to_modes basis), any precision.
+template <class T>
+__device__ __forceinline__ void project10(const T f[19], T m[10])
+{
+    const T s1 = f[1] + f[2], d1 = f[1] - f[2];
+    const T s2 = f[3] + f[4], d2 = f[3] - f[4];
+    const T s3 = f[5] + f[6], d3 = f[5] - f[6];
+    const T s7 = f[7] + f[8], d7 = f[7] - f[8];
+    const T s9 = f[9] + f[10], d9 = f[9] - f[10];
+    const T s11 = f[11] + f[12], d11 = f[11] - f[12];
+    const T s13 = f[13] + f[14], d13 = f[13] - f[14];
+    const T s15 = f[15] + f[16], d15 = f[15] - f[16];
+    const T s17 = f[17] + f[18], d17 = f[17] - f[18];
+    const T sxy = s7 + s9, sxz = s11 + s13, syz = s15 + s17;
+    const T sdg = sxy + sxz + syz;
+    m[0] = f[0] + (s1 + s2 + s3) + sdg;
+    m[1] = d1 + d7 + d9 + d11 + d13;
+    m[2] = d2 + d7 - d9 + d15 + d17;
+    m[3] = d3 + d11 - d13 + d15 - d17;
+    m[4] = sdg - f[0];
+    m[5] = T(2) * s1 - s2 - s3 + sxy + sxz - T(2) * syz;
+    m[6] = s2 - s3 + sxy - sxz;
+    m[7] = s7 - s9;
+    m[8] = s15 - s17;
+    m[9] = s11 - s13;
+}
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// ---------------------------------------------------------------------------
+// Cover/uncover adjoint (Section 2). s0/m0: state and masks of step n (old
+// position), s1/m1: of step n+1 (new position X', velocities V', Omega').
+// Covered node c (fluid at n, particle at n+1): its post-stream populations
+// fed P_pending (j), L_pending ((c - X') x j) and the ledger (rho_l), so
+//   a_l(c) = lambda_ledger_l,  b_l(c) = lambda_P + lambda_L x (c - X').
+// Uncovered node c: f(c) = f^eq(mean_l, u_b) with u_b = V' + Omega' x (c - X');
+// since sum_i f^eq_i = rho and sum_i f^eq_i c_i = rho u, the incoming adjoint
+// (a_l, b_l) of c gives lambda_mean_l = a_l + b_l . u_b and lambda_u_b =
+// sum_l mean_l b_l, plus the particle's payment of the momentum and the
+// ledger. lambda_mean_l / cnt goes to uv[] for ka_cover_mean. Per-block
+// partials: lambda X', lambda V', lambda Omega'.
+// ---------------------------------------------------------------------------
+static __global__ void __launch_bounds__(kT) ka_cover(adj_t* __restrict__ lam1, const float* __restrict__ tape1,
+                                                      const DevState* __restrict__ s0, const uint8_t* __restrict__ mk0,
+                                                      const DevState* __restrict__ s1, const uint8_t* __restrict__ mk1,
+                                                      const AdjState* __restrict__ adj, adj_t* __restrict__ uv,
+                                                      double* __restrict__ parts, KParams P)
+{
+    __shared__ double s_red[(kT / 32) * 8];
+    __shared__ double s_out[8];
+    const int B = P.B, B3 = B * B * B;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint8_t* m0 = cur_mask(s0, mk0, P);
+    const uint8_t* m1 = cur_mask(s1, mk1, P);
+    const int o0[3] = {s0->box0[0], s0->box0[1], s0->box0[2]};
+    const int o1[3] = {s1->box0[0], s1->box0[1], s1->box0[2]};
+    const int L[3] = {P.lx, P.ly, P.lz};
+    const size_t N = P.N;
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // lX'[3], lV'[3], lOm'[3]
+    if (t < B3) {
+        const int d[3] = {t % B, (t / B) % B, t / (B * B)};
+        uv[t] = adj_t(0);
+        uv[B3 + t] = adj_t(0);
+        if (m1[t]) {  // covered
+            int c[3];
+            for (int a = 0; a < 3; ++a) {
+                c[a] = o1[a] + d[a];
+                if (!P.wall[a] && c[a] >= L[a]) c[a] -= L[a];
+            }
+            if (!is_solid(c[0], c[1], c[2], o0, m0, P)) {
+                const uint32_t n = lin(c[0], c[1], c[2], P);
+                double r[3], lb[3], j[3], t3[3];
+                for (int a = 0; a < 3; ++a) r[a] = rel_axis((double)c[a], s1->X[a], L[a], P.wall[a]);
+                cross3(adj->lL, r, lb);
+                for (int a = 0; a < 3; ++a) lb[a] += adj->lP[a];
+                for (int l = 0; l < 2; ++l) {
+                    lam1[(size_t)l * N + n] = (adj_t)adj->lled[l];
+                    for (int a = 0; a < 3; ++a) lam1[(size_t)(2 + 3 * l + a) * N + n] = (adj_t)lb[a];
+                }
+                for (int a = 0; a < 3; ++a) j[a] = (double)tape1[(2 + a) * N + n] + (double)tape1[(5 + a) * N + n];
+                cross3(j, adj->lL, t3);  // d/dX' of lambda_L . ((c - X') x j) = -(j x lambda_L)
+                for (int a = 0; a < 3; ++a) acc[a] -= t3[a];
+            }
+        }
+        if (m0[t]) {  // uncovered
+            int c[3];
+            for (int a = 0; a < 3; ++a) {
+                c[a] = o0[a] + d[a];
+                if (!P.wall[a] && c[a] >= L[a]) c[a] -= L[a];
+            }
+            if (!is_solid(c[0], c[1], c[2], o1, m1, P)) {
+                double mean[2] = {0.0, 0.0};
+                int cnt = 0;
+                for (int jd = 1; jd < 19; ++jd) {
+                    int q[3];
+                    if (!nbr(c[0], c[1], c[2], cxv(jd), cyv(jd), czv(jd), P, q)) continue;
+                    if (is_solid(q[0], q[1], q[2], o1, m1, P) || is_solid(q[0], q[1], q[2], o0, m0, P)) continue;
+                    const uint32_t m = lin(q[0], q[1], q[2], P);
+                    mean[0] += tape1[m];
+                    mean[1] += tape1[N + m];
+                    ++cnt;
+                }
+                const double rl[2] = {cnt ? mean[0] / cnt : P.rho0[0], cnt ? mean[1] / cnt : P.rho0[1]};
+                double r[3], w[3], ub[3], lq[3];
+                for (int a = 0; a < 3; ++a) r[a] = rel_axis((double)c[a], s1->X[a], L[a], P.wall[a]);
+                cross3(s1->Om, r, w);
+                for (int a = 0; a < 3; ++a) ub[a] = s1->V[a] + w[a];
+                cross3(adj->lL, r, lq);
+                for (int a = 0; a < 3; ++a) lq[a] += adj->lP[a];  // lambda_P + lambda_L x d
+                const uint32_t n = lin(c[0], c[1], c[2], P);
+                double lub[3] = {0, 0, 0};
+                const double rsum = rl[0] + rl[1];
+                double lqub = lq[0] * ub[0] + lq[1] * ub[1] + lq[2] * ub[2];
+                for (int l = 0; l < 2; ++l) {
+                    const double al = lam1[(size_t)l * N + n];
+                    double bl[3];
+                    for (int a = 0; a < 3; ++a) bl[a] = lam1[(size_t)(2 + 3 * l + a) * N + n];
+                    const double lmean = al + bl[0] * ub[0] + bl[1] * ub[1] + bl[2] * ub[2] - lqub - adj->lled[l];
+                    if (cnt) uv[(size_t)l * B3 + t] = (adj_t)(lmean / cnt);
+                    for (int a = 0; a < 3; ++a) lub[a] += rl[l] * bl[a];
+                }
+                for (int a = 0; a < 3; ++a) lub[a] -= rsum * lq[a];
+                // u_b = V' + Omega' x d, d = c - X'
+                double t1[3], t2[3], pm[3], t4[3];
+                cross3(r, lub, t1);           // lambda Omega' += d x lambda_u_b
+                cross3(lub, s1->Om, t2);      // lambda X' -= lambda_u_b x Omega'
+                for (int a = 0; a < 3; ++a) pm[a] = rsum * ub[a];
+                cross3(pm, adj->lL, t4);      // lambda X' += pm x lambda_L (from -d x pm)
+                for (int a = 0; a < 3; ++a) {
+                    acc[a] += -t2[a] + t4[a];
+                    acc[3 + a] += lub[a];
+                    acc[6 + a] += t1[a];
+                }
+            }
+        }
+    }
+    double v8[8];
+    for (int k = 0; k < 8; ++k) v8[k] = acc[k];
+    block_sum8<kT>(v8, s_red, s_out);
+    if (threadIdx.x < 8) parts[blockIdx.x * 9 + threadIdx.x] = s_out[threadIdx.x];
+    __syncthreads();
+    double v1[8] = {acc[8], 0, 0, 0, 0, 0, 0, 0};
+    block_sum8<kT>(v1, s_red, s_out);
+    if (threadIdx.x == 0) parts[blockIdx.x * 9 + 8] = s_out[0];
+}
+
+// Neighbours of uncovered nodes that fed the neighbour mean: fluid at n and
+// at n+1. Gathers uv of uncovered neighbours into a_l. One thread per node of
+// the old box grown by one.
+static __global__ void __launch_bounds__(kT) ka_cover_mean(adj_t* __restrict__ lam1, const DevState* __restrict__ s0,
+                                                           const uint8_t* __restrict__ mk0,
+                                                           const DevState* __restrict__ s1,
+                                                           const uint8_t* __restrict__ mk1, const adj_t* __restrict__ uv,
+                                                           KParams P)
+{
+    const int B = P.B, G = B + 2, B3 = B * B * B;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= G * G * G) return;
+    const uint8_t* m0 = cur_mask(s0, mk0, P);
+    const uint8_t* m1 = cur_mask(s1, mk1, P);
+    const int o0[3] = {s0->box0[0], s0->box0[1], s0->box0[2]};
+    const int o1[3] = {s1->box0[0], s1->box0[1], s1->box0[2]};
+    const int L[3] = {P.lx, P.ly, P.lz};
+    const int d[3] = {t % G, (t / G) % G, t / (G * G)};
+    int m[3];
+    for (int a = 0; a < 3; ++a) {
+        m[a] = o0[a] - 1 + d[a];
+        if (m[a] < 0 || m[a] >= L[a]) {
+            if (P.wall[a]) return;
+            m[a] += (m[a] < 0) ? L[a] : -L[a];
+        }
+    }
+    if (is_solid(m[0], m[1], m[2], o0, m0, P) || is_solid(m[0], m[1], m[2], o1, m1, P)) return;
+    adj_t add[2] = {adj_t(0), adj_t(0)};
+    for (int jd = 1; jd < 19; ++jd) {
+        int c[3];
+        if (!nbr(m[0], m[1], m[2], cxv(jd), cyv(jd), czv(jd), P, c)) continue;
+        if (!is_solid(c[0], c[1], c[2], o0, m0, P) || is_solid(c[0], c[1], c[2], o1, m1, P)) continue;
+        const int e = box_rel(c[0], o0[0], L[0], P.wall[0]) +
+                      B * (box_rel(c[1], o0[1], L[1], P.wall[1]) + B * box_rel(c[2], o0[2], L[2], P.wall[2]));
+        add[0] += uv[e];
+        add[1] += uv[B3 + e];
+    }
+    if (add[0] != adj_t(0) || add[1] != adj_t(0)) {
+        const uint32_t n = lin(m[0], m[1], m[2], P);
+        lam1[n] += add[0];
+        lam1[P.N + n] += add[1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Leap-frog update adjoint (FP64, one thread): V' = V + (F + F_p z)/m_p,
+// X' = X + V', Omega' = Omega + T/I_p, plus the two halves of Vavg in J.
+// On exit lX, lV, lOm, lP, lL hold the adjoint of step n's input state
+// without the link terms ka_node adds; dJ/dg accumulates.
+// ---------------------------------------------------------------------------
+static __global__ void ka_update(AdjState* __restrict__ a, const double* __restrict__ parts, int nblocks,
+                                 const DevState* __restrict__ s0, double inv2T, double dFp_dg)
+{
+    double c[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nblocks; ++b)
+        for (int k = 0; k < 9; ++k) c[k] += parts[b * 9 + k];
+    double lXp[3], lVp[3], lOmp[3];
+    for (int k = 0; k < 3; ++k) {
+        lXp[k] = a->lX[k] + c[k];
+        lOmp[k] = a->lOm[k] + c[6 + k];
+        lVp[k] = a->lV[k] + c[3 + k] + lXp[k] + (k == 2 ? inv2T : 0.0);
+    }
+    for (int k = 0; k < 3; ++k) {
+        a->lF[k] = lVp[k] / s0->mp;
+        a->lT[k] = lOmp[k] / s0->Ip;
+        a->lFf[k] = (float)a->lF[k];
+        a->lTf[k] = (float)a->lT[k];
+        a->lX[k] = lXp[k];
+        a->lV[k] = lVp[k] + (k == 2 ? inv2T : 0.0);
+        a->lOm[k] = lOmp[k];
+        a->lP[k] = a->lF[k];
+        a->lL[k] = a->lT[k];
+    }
+    a->grad[0] += lVp[2] * dFp_dg / s0->mp;
+}
+
+// ---------------------------------------------------------------------------
+// Per fluid node of step n: adjoint of streaming (pulled from the
+// destinations' (a, b) in lam1), of the moving links and the Shan-Chen
+// reaction on the particle, and of the collision (adj_modes). Writes the
+// node's b_l and the local part of a_l into lam0, lambda g_l into lg, and
+// per-tile partials (link terms of lambda X, V, Omega; dJ/dG; lambda delta).
+// ---------------------------------------------------------------------------
+// Thread (tx, ty) of tile (bx, by, bz); every thread of the block calls it.
+// PARTICLE: the tile is near the particle (links, reaction); else it has none.
+template <bool PARTICLE>
+__device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty, const float* __restrict__ tape,
+                                         const float* __restrict__ psi, const adj_t* __restrict__ lam1,
+                                         adj_t* __restrict__ lam0, adj_t* __restrict__ lg,
+                                         const DevState* __restrict__ s0, const uint8_t* __restrict__ mk0,
+                                         const AdjState* __restrict__ adj, double* __restrict__ parts,
+                                         const KParams& P)
+{
+    __shared__ double s_red[(kT / 32) * 8];
+    __shared__ double s_out[8];
+    const int x = bx * P.tx + tx;
+    const int y = by * P.ty + ty;
+    const int z = bz;
+    const size_t N = P.N;
+    double acc[kNodeParts];
+#pragma unroll
+    for (int k = 0; k < kNodeParts; ++k) acc[k] = 0.0;
+    if (x < P.lx && y < P.ly) {
+        const uint8_t* m0 = cur_mask(s0, mk0, P);
+        const uint32_t n = lin(x, y, z, P);
+        if (PARTICLE && solid_at(x, y, z, s0, m0, P)) {
+            for (int k = 0; k < 8; ++k) lam0[k * N + n] = adj_t(0);
+            for (int k = 0; k < 6; ++k) lg[k * N + n] = adj_t(0);
+        } else {
+            float rho[2], j[2][3], g[2][3];
+            for (int l = 0; l < 2; ++l) {
+                rho[l] = tape[l * N + n];
+                for (int a = 0; a < 3; ++a) j[l][a] = tape[(2 + 3 * l + a) * N + n];
+            }
+            const float* pA = psi + pad_index(x, y, z, P);
+            const float* pB = pA + P.padn;
+            const int sy = P.px, sz = P.px * P.py;
+            for (int a = 0; a < 3; ++a) g[0][a] = g[1][a] = 0.0f;
+            uint32_t solid_nb = 0, wall_nb = 0;
+            uint32_t qidx[19];
+            qidx[0] = n;
+#pragma unroll
+            for (int i = 1; i < 19; ++i) {
+                const int off = cxv(i) + sy * cyv(i) + sz * czv(i);
+                const float w = wv(i);
+                const float pa = pA[off], pb = pB[off];
+                g[0][0] += cxv(i) * w * pb; g[0][1] += cyv(i) * w * pb; g[0][2] += czv(i) * w * pb;
+                g[1][0] += cxv(i) * w * pa; g[1][1] += cyv(i) * w * pa; g[1][2] += czv(i) * w * pa;
+                int q[3];
+                if (!nbr(x, y, z, cxv(i), cyv(i), czv(i), P, q)) {
+                    wall_nb |= 1u << i;
+                    qidx[i] = n;
+                } else {
+                    qidx[i] = lin(q[0], q[1], q[2], P);
+                    if (PARTICLE && solid_at(q[0], q[1], q[2], s0, m0, P)) solid_nb |= 1u << i;
+                }
+            }
+            // Particle-link constants of this node: lever of each link, u_b . c_i
+            // (float, as the forward step), forward post-collision populations.
+            float rnf[3] = {0.f, 0.f, 0.f};
+            float fo[2][19];
+            const float ext[3] = {P.ext[0], P.ext[1], P.ext[2]};
+            if (PARTICLE && solid_nb) {
+                for (int a = 0; a < 3; ++a) {
+                    const int c = a == 0 ? x : (a == 1 ? y : z);
+                    const int L = a == 0 ? P.lx : (a == 1 ? P.ly : P.lz);
+                    rnf[a] = (float)rel_axis((double)c, s0->X[a], L, P.wall[a]);
+                }
+                float ms[2][10];
+                fwd_modes<float>(rho, j, g, ext, P.G, ms);
+#pragma unroll
+                for (int l = 0; l < 2; ++l) {
+                    float nm[19];
+                    for (int k = 0; k < 19; ++k) nm[k] = k < 10 ? ms[l][k] / bnorm(k) : 0.0f;
+                    nm[0] = ms[l][0] + s0->delta_f[l];
+                    from_modes(nm, fo[l]);
+                }
+            }
+            const float* lF = adj->lFf;
+            const float* lT = adj->lTf;
+            adj_t lrx[2] = {adj_t(0), adj_t(0)};  // extra adjoint of rho_l from links and the reaction
+            adj_t lm[2][10];
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                const adj_t ax = lam1[(size_t)l * N + n];
+                const adj_t bx[3] = {lam1[(2 + 3 * l) * N + n], lam1[(3 + 3 * l) * N + n], lam1[(4 + 3 * l) * N + n]};
+                adj_t wl[19];
+                double ldl = 0.0;
+#pragma unroll
+                for (int i = 0; i < 19; ++i) {
+                    const int cx = cxv(i), cy = cyv(i), cz = czv(i);
+                    adj_t v;
+                    if ((wall_nb | solid_nb) >> i & 1u) {
+                        v = ax - (cx * bx[0] + cy * bx[1] + cz * bx[2]);
+                        if (PARTICLE && (solid_nb >> i & 1u)) {
+                            const float d[3] = {rnf[0] + 0.5f * cx, rnf[1] + 0.5f * cy, rnf[2] + 0.5f * cz};
+                            const float kap = cx * (lF[0] + lT[1] * d[2] - lT[2] * d[1]) +
+                                              cy * (lF[1] + lT[2] * d[0] - lT[0] * d[2]) +
+                                              cz * (lF[2] + lT[0] * d[1] - lT[1] * d[0]);
+                            const float* V = s0->Vf;
+                            const float* Om = s0->Omf;
+                            const float ubc = (V[0] + Om[1] * d[2] - Om[2] * d[1]) * cx +
+                                              (V[1] + Om[2] * d[0] - Om[0] * d[2]) * cy +
+                                              (V[2] + Om[0] * d[1] - Om[1] * d[0]) * cz;
+                            const adj_t lcorr = -v - kap + adj->lledf[l];
+                            lrx[l] += lcorr * adj_t(6.0f * wv(i) * ubc);
+                            const double lub = (double)lcorr * 6.0 * wv(i) * rho[l];  // lambda (u_b . c_i)
+                            const double lb[3] = {lub * cx, lub * cy, lub * cz};
+                            acc[3] += lb[0]; acc[4] += lb[1]; acc[5] += lb[2];
+                            acc[6] += d[1] * lb[2] - d[2] * lb[1];
+                            acc[7] += d[2] * lb[0] - d[0] * lb[2];
+                            acc[8] += d[0] * lb[1] - d[1] * lb[0];
+                            acc[0] -= lb[1] * Om[2] - lb[2] * Om[1];
+                            acc[1] -= lb[2] * Om[0] - lb[0] * Om[2];
+                            acc[2] -= lb[0] * Om[1] - lb[1] * Om[0];
+                            // lever of the exchanged momentum (2 f* - corr) c_i
+                            const double dp = 2.0 * fo[l][i] - 6.0 * wv(i) * rho[l] * ubc;
+                            const double fr[3] = {dp * cx, dp * cy, dp * cz};
+                            acc[0] -= fr[1] * lT[2] - fr[2] * lT[1];
+                            acc[1] -= fr[2] * lT[0] - fr[0] * lT[2];
+                            acc[2] -= fr[0] * lT[1] - fr[1] * lT[0];
+                            v += adj_t(2) * kap;
+                        }
+                    } else {
+                        const uint32_t q = qidx[i];
+                        v = lam1[(size_t)l * N + q];
+                        if (cx) v += cx * lam1[(2 + 3 * l) * N + q];
+                        if (cy) v += cy * lam1[(3 + 3 * l) * N + q];
+                        if (cz) v += cz * lam1[(4 + 3 * l) * N + q];
+                    }
+                    wl[i] = adj_t(wv(i)) * v;
+                    ldl += wl[i];
+                }
+                acc[10 + l] += ldl;
+                adj_t mm[10];
+                project10<adj_t>(wl, mm);
+                for (int k = 0; k < 10; ++k) lm[l][k] = mm[k] / adj_t(bnorm(k));
+            }
+            // Shan-Chen reaction on the particle: F += G w_i (rhoA psiB(q) + rhoB psiA(q)) c_i.
+            if (PARTICLE && solid_nb) {
+#pragma unroll
+                for (int i = 1; i < 19; ++i) {
+                    if (!(solid_nb >> i & 1u)) continue;
+                    const int cx = cxv(i), cy = cyv(i), cz = czv(i);
+                    const int off = cx + sy * cy + sz * cz;
+                    const float pa = pA[off], pb = pB[off];
+                    const float d[3] = {rnf[0] + 0.5f * cx, rnf[1] + 0.5f * cy, rnf[2] + 0.5f * cz};
+                    const float kap = cx * (lF[0] + lT[1] * d[2] - lT[2] * d[1]) +
+                                      cy * (lF[1] + lT[2] * d[0] - lT[0] * d[2]) +
+                                      cz * (lF[2] + lT[0] * d[1] - lT[1] * d[0]);
+                    const float w = wv(i);
+                    acc[9] += (double)kap * w * (rho[0] * pb + rho[1] * pa);
+                    lrx[0] += adj_t(kap * P.G * w * pb);
+                    lrx[1] += adj_t(kap * P.G * w * pa);
+                    const double mag = (double)P.G * w * (rho[0] * pb + rho[1] * pa);
+                    const double fr[3] = {mag * cx, mag * cy, mag * cz};
+                    acc[0] -= fr[1] * lT[2] - fr[2] * lT[1];
+                    acc[1] -= fr[2] * lT[0] - fr[0] * lT[2];
+                    acc[2] -= fr[0] * lT[1] - fr[1] * lT[0];
+                }
+            }
+            adj_t rr[2], jr[2][3], gr[2][3], er[3], lrho[2], lj[2][3], lgv[2][3], lG;
+            for (int l = 0; l < 2; ++l) {
+                rr[l] = rho[l];
+                for (int a = 0; a < 3; ++a) {
+                    jr[l][a] = j[l][a];
+                    gr[l][a] = g[l][a];
+                }
+            }
+            for (int a = 0; a < 3; ++a) er[a] = ext[a];
+            adj_modes<adj_t>(rr, jr, gr, er, adj_t(P.G), lm, lrho, lj, lgv, lG);
+            acc[9] += lG;
+            for (int l = 0; l < 2; ++l) {
+                lam0[(size_t)l * N + n] = lrho[l] + lrx[l];
+                for (int a = 0; a < 3; ++a) {
+                    lam0[(size_t)(2 + 3 * l + a) * N + n] = lj[l][a];
+                    lg[(size_t)(3 * l + a) * N + n] = lgv[l][a];
+                }
+            }
+        }
+    }
+    double v8[8];
+    for (int k = 0; k < 8; ++k) v8[k] = acc[k];
+    const long long tile = bx + (long long)P.gx * (by + (long long)P.gy * bz);
+    const int tid = tx + P.tx * ty;
+    if (PARTICLE) {
+        block_sum8<kT>(v8, s_red, s_out);
+        if (tid < 8) parts[tile * kNodeParts + tid] = s_out[tid];
+        __syncthreads();
+    } else if (tid < 9) {
+        parts[tile * kNodeParts + tid] = 0.0;  // no link terms away from the particle
+    }
+    for (int k = 0; k < 8; ++k) v8[k] = k < kNodeParts - 8 ? acc[8 + k] : 0.0;
+    block_sum8<kT>(v8, s_red, s_out);
+    if (tid < kNodeParts - 8) parts[tile * kNodeParts + 8 + tid] = s_out[tid];
+}
+
+// Tiles away from the particle (all tiles when there is none).
+static __global__ void __launch_bounds__(kT, sizeof(adj_t) == 4 ? 3 : 2) ka_node_bulk(const float* __restrict__ tape, const float* __restrict__ psi,
+                                                          const adj_t* __restrict__ lam1, adj_t* __restrict__ lam0,
+                                                          adj_t* __restrict__ lg, const DevState* __restrict__ s0,
+                                                          const uint8_t* __restrict__ mk0,
+                                                          const AdjState* __restrict__ adj, double* __restrict__ parts,
+                                                          KParams P)
+{
+    if (P.has_particle) {
+        const int o[3] = {s0->box0[0], s0->box0[1], s0->box0[2]};
+        if (tile_near(blockIdx.x, blockIdx.y, blockIdx.z, o, P)) return;
+    }
+    adj_tile<false>(blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, tape, psi, lam1, lam0, lg, s0, mk0,
+                    adj, parts, P);
+}
+
+// Tiles near the particle: the candidate grid of the forward step.
+static __global__ void __launch_bounds__(kT) ka_node_near(const float* __restrict__ tape, const float* __restrict__ psi,
+                                                          const adj_t* __restrict__ lam1, adj_t* __restrict__ lam0,
+                                                          adj_t* __restrict__ lg, const DevState* __restrict__ s0,
+                                                          const uint8_t* __restrict__ mk0,
+                                                          const AdjState* __restrict__ adj, double* __restrict__ parts,
+                                                          KParams P)
+{
+    const int o[3] = {s0->box0[0], s0->box0[1], s0->box0[2]};
+    const int bx = candidate_tile(blockIdx.x, o[0], P.tx, P.gx, P.lx, P.wall[0]);
+    const int by = candidate_tile(blockIdx.y, o[1], P.ty, P.gy, P.ly, P.wall[1]);
+    const int bz = candidate_tile(blockIdx.z, o[2], 1, P.lz, P.lz, P.wall[2]);
+    if (bx < 0 || by < 0 || bz < 0 || !tile_near(bx, by, bz, o, P)) return;
+    adj_tile<true>(bx, by, bz, threadIdx.x, threadIdx.y, tape, psi, lam1, lam0, lg, s0, mk0, adj, parts, P);
+}
+
+// Fluid-neighbour count of lattice point q (wrapped on periodic axes), as the
+// virtual layer and the wall ghosts use it.
+__device__ __forceinline__ int fluid_count(const int q[3], const DevState* s0, const uint8_t* m0, const KParams& P)
+{
+    int cnt = 0;
+    for (int jd = 1; jd < 19; ++jd) {
+        int r[3];
+        if (!nbr(q[0], q[1], q[2], cxv(jd), cyv(jd), czv(jd), P, r)) continue;
+        if (solid_at(r[0], r[1], r[2], s0, m0, P)) continue;
+        ++cnt;
+    }
+    return cnt;
+}
+
+// lambda psi_l at padded point p (in range on every periodic axis): the
+// Shan-Chen stencil transposed, g_A reads psi_B and g_B reads psi_A.
+__device__ __forceinline__ void lpsi_gather(const int p[3], const adj_t* __restrict__ lg, const KParams& P, adj_t out[2])
+{
+    const size_t N = P.N;
+    adj_t la = adj_t(0), lb = adj_t(0);
+    for (int i = 1; i < 19; ++i) {
+        int x[3];
+        if (!nbr(p[0], p[1], p[2], -cxv(i), -cyv(i), -czv(i), P, x)) continue;
+        // a source outside the domain (p is a ghost and -c_i points further out) is skipped by nbr()
+        const uint32_t s = lin(x[0], x[1], x[2], P);
+        const adj_t w = wv(i);
+        const adj_t cx = cxv(i), cy = cyv(i), cz = czv(i);
+        lb += w * (cx * lg[0 * N + s] + cy * lg[1 * N + s] + cz * lg[2 * N + s]);
+        la += w * (cx * lg[3 * N + s] + cy * lg[4 * N + s] + cz * lg[5 * N + s]);
+    }
+    out[0] = la;
+    out[1] = lb;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of psi at the particle nodes (one thread per entry of the particle
+// box). A particle node with fluid neighbours (virtual layer) gets lambda
+// psi plus the Shan-Chen reaction's dependence on it, then
+// mu_l = lambda psi_l / cnt where the clip at 0 is inactive, written at the
+// node's place in lpsi; dJ/d delta_rho partial per block.
+// ---------------------------------------------------------------------------
+static __global__ void __launch_bounds__(kT) ka_lpsi(const adj_t* __restrict__ lg, const float* __restrict__ psi,
+                                                     adj_t* __restrict__ lpsi, const DevState* __restrict__ s0,
+                                                     const uint8_t* __restrict__ mk0, const AdjState* __restrict__ adj,
+                                                     double* __restrict__ parts2, KParams P)
+{
+    __shared__ double s_red[(kT / 32) * 8];
+    __shared__ double s_out[8];
+    const int B = P.B;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint8_t* m0 = cur_mask(s0, mk0, P);
+    double dd = 0.0;
+    if (t < B * B * B && m0[t]) {
+        const int L[3] = {P.lx, P.ly, P.lz};
+        const int dlt[3] = {t % B, (t / B) % B, t / (B * B)};
+        int p[3];
+        for (int a = 0; a < 3; ++a) {
+            p[a] = s0->box0[a] + dlt[a];
+            if (!P.wall[a] && p[a] >= L[a]) p[a] -= L[a];
+        }
+        const int x = p[0], y = p[1], z = p[2];
+        adj_t lp[2];
+        lpsi_gather(p, lg, P, lp);
+        const long long pi = pad_index(x, y, z, P);
+        {
+            const int cnt = fluid_count(p, s0, m0, P);
+            adj_t mu[2] = {adj_t(0), adj_t(0)};
+            if (cnt) {
+                const float* lF = adj->lFf;
+                const float* lT = adj->lTf;
+                for (int i = 1; i < 19; ++i) {  // fluid x = p - c_i reads psi(p) along +c_i
+                    int q[3];
+                    if (!nbr(x, y, z, -cxv(i), -cyv(i), -czv(i), P, q)) continue;
+                    if (solid_at(q[0], q[1], q[2], s0, m0, P)) continue;
+                    const int cx = cxv(i), cy = cyv(i), cz = czv(i);
+                    float d[3];
+                    for (int a = 0; a < 3; ++a) {
+                        const int c = q[a];
+                        const int L = a == 0 ? P.lx : (a == 1 ? P.ly : P.lz);
+                        const float cc = a == 0 ? cx : (a == 1 ? cy : cz);
+                        d[a] = (float)rel_axis((double)c, s0->X[a], L, P.wall[a]) + 0.5f * cc;
+                    }
+                    const float kap = cx * (lF[0] + lT[1] * d[2] - lT[2] * d[1]) +
+                                      cy * (lF[1] + lT[2] * d[0] - lT[0] * d[2]) +
+                                      cz * (lF[2] + lT[0] * d[1] - lT[1] * d[0]);
+                    const long long qi = pad_index(q[0], q[1], q[2], P);
+                    lp[1] += adj_t(kap * P.G * wv(i) * psi[qi]);           // d/d psiB(p) of rhoA(q) psiB(p)
+                    lp[0] += adj_t(kap * P.G * wv(i) * psi[P.padn + qi]);  // d/d psiA(p) of rhoB(q) psiA(p)
+                }
+                const bool actA = psi[pi] > 0.0f, actB = psi[P.padn + pi] > 0.0f;
+                if (actA) { mu[0] = lp[0] / adj_t(cnt); dd += lp[0]; }
+                if (actB) { mu[1] = lp[1] / adj_t(cnt); dd -= lp[1]; }
+            }
+            lpsi[pi] = mu[0];
+            lpsi[P.padn + pi] = mu[1];
+        }
+    }
+    double v8[8] = {dd, 0, 0, 0, 0, 0, 0, 0};
+    block_sum8<kT>(v8, s_red, s_out);
+    if (threadIdx.x == 0) parts2[blockIdx.x] = s_out[0];
+}
+
+// Wall ghosts of the psi shell (points outside along a wall axis, in range on
+// the periodic axes): mu_l = lambda psi_l / cnt, the mean over fluid neighbours.
+static __global__ void __launch_bounds__(kT) ka_lpsi_shell(const adj_t* __restrict__ lg, adj_t* __restrict__ lpsi,
+                                                           const DevState* __restrict__ s0,
+                                                           const uint8_t* __restrict__ mk0, KParams P)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nzf = 2LL * P.px * P.py, nyf = 2LL * P.px * P.lz, nxf = 2LL * P.ly * P.lz;
+    int p[3];
+    if (t < nzf) {
+        const long long r = t % ((long long)P.px * P.py);
+        p[0] = (int)(r % P.px) - 1;
+        p[1] = (int)(r / P.px) - 1;
+        p[2] = (t < nzf / 2) ? -1 : P.lz;
+    } else if (t < nzf + nyf) {
+        const long long u = t - nzf, r = u % ((long long)P.px * P.lz);
+        p[0] = (int)(r % P.px) - 1;
+        p[2] = (int)(r / P.px);
+        p[1] = (u < nyf / 2) ? -1 : P.ly;
+    } else if (t < nzf + nyf + nxf) {
+        const long long u = t - nzf - nyf, r = u % ((long long)P.ly * P.lz);
+        p[1] = (int)(r % P.ly);
+        p[2] = (int)(r / P.ly);
+        p[0] = (u < nxf / 2) ? -1 : P.lx;
+    } else {
+        return;
+    }
+    const int L[3] = {P.lx, P.ly, P.lz};
+    bool ghost = false;
+    for (int a = 0; a < 3; ++a) {
+        const bool out = p[a] < 0 || p[a] >= L[a];
+        if (out && !P.wall[a]) return;  // a periodic copy: its reads are attributed to the interior point
+        ghost |= out;
+    }
+    if (!ghost) return;
+    const uint8_t* m0 = cur_mask(s0, mk0, P);
+    adj_t lp[2];
+    lpsi_gather(p, lg, P, lp);
+    const int cnt = fluid_count(p, s0, m0, P);
+    const long long dst = (long long)(p[0] + 1) + (long long)P.px * ((p[1] + 1) + (long long)P.py * (p[2] + 1));
+    lpsi[dst] = cnt ? lp[0] / adj_t(cnt) : adj_t(0);
+    lpsi[P.padn + dst] = cnt ? lp[1] / adj_t(cnt) : adj_t(0);
+}
+
+// a_l of fluid nodes: lambda psi of the node (the Shan-Chen stencil
+// transposed) plus mu of every particle node and wall ghost among its
+// neighbours (each averaged this node's density).
+static __global__ void __launch_bounds__(kT) ka_final(adj_t* __restrict__ lam0, const adj_t* __restrict__ lg,
+                                                      const adj_t* __restrict__ lpsi, const DevState* __restrict__ s0,
+                                                      const uint8_t* __restrict__ mk0, KParams P)
+{
+    const int x = blockIdx.x * P.tx + threadIdx.x;
+    const int y = blockIdx.y * P.ty + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= P.lx || y >= P.ly) return;
+    const uint8_t* m0 = cur_mask(s0, mk0, P);
+    if (solid_at(x, y, z, s0, m0, P)) return;
+    const int p[3] = {x, y, z};
+    adj_t add[2];
+    lpsi_gather(p, lg, P, add);  // psi = rho on this fluid node
+    const int L[3] = {P.lx, P.ly, P.lz};
+    for (int i = 1; i < 19; ++i) {
+        int r[3] = {x + cxv(i), y + cyv(i), z + czv(i)};
+        bool ghost = false;
+        for (int a = 0; a < 3; ++a) {
+            if (r[a] < 0 || r[a] >= L[a]) {
+                if (P.wall[a]) ghost = true;
+                else r[a] += (r[a] < 0) ? L[a] : -L[a];
+            }
+        }
+        if (!ghost && !solid_at(r[0], r[1], r[2], s0, m0, P)) continue;
+        const long long q = (long long)(r[0] + 1) + (long long)P.px * ((r[1] + 1) + (long long)P.py * (r[2] + 1));
+        add[0] += lpsi[q];
+        add[1] += lpsi[P.padn + q];
+    }
+    const uint32_t n = lin(x, y, z, P);
+    lam0[n] += add[0];
+    lam0[P.N + n] += add[1];
+}
+
+// Per-tile partials -> adjoint of step n's particle state and the gradient
+// sums. One block: each thread sums a fixed stride of tiles, then a fixed
+// reduction tree (deterministic).
+static __global__ void __launch_bounds__(kT) ka_reduce(AdjState* __restrict__ a, const double* __restrict__ parts,
+                                                       long long ntiles, const double* __restrict__ parts2, int nbox)
+{
+    __shared__ double s_red[(kT / 32) * 8];
+    __shared__ double s_out[8];
+    __shared__ double s_res[16];
+    double s[kNodeParts + 1];
+    for (int k = 0; k <= kNodeParts; ++k) s[k] = 0.0;
+    for (long long t = threadIdx.x; t < ntiles; t += blockDim.x)
+        for (int k = 0; k < kNodeParts; ++k) s[k] += parts[t * kNodeParts + k];
+    for (int t = threadIdx.x; t < nbox; t += blockDim.x) s[kNodeParts] += parts2[t];
+    double v[8];
+    for (int k = 0; k < 8; ++k) v[k] = s[k];
+    block_sum8<kT>(v, s_red, s_out);
+    if (threadIdx.x < 8) s_res[threadIdx.x] = s_out[threadIdx.x];
+    __syncthreads();
+    for (int k = 0; k < 8; ++k) v[k] = (8 + k <= kNodeParts) ? s[8 + k] : 0.0;
+    block_sum8<kT>(v, s_red, s_out);
+    if (threadIdx.x != 0) return;
+    for (int k = 0; k < 3; ++k) {
+        a->lX[k] += s_res[k];
+        a->lV[k] += s_res[3 + k];
+        a->lOm[k] += (k < 2) ? s_res[6 + k] : s_out[0];
+    }
+    a->grad[2] += s_out[1];
+    a->ld[0] = s_out[2];
+    a->ld[1] = s_out[3];
+    a->grad[1] += s_out[4];
+}
+
+}  // namespace flbm_adjoint
+
+using namespace flbm_adjoint;
+
+namespace {
+
+// Device buffers of one adjoint run.
+struct AdjBuffers {
+    std::vector<void*> owned;
+    float* ck_f = nullptr;     // checkpoints: populations (current copy)
+    DevState* ck_st = nullptr; // checkpoints: particle record
+    uint8_t* ck_m = nullptr;   // checkpoints: both particle masks
+    float* tape = nullptr;     // K+1 moment fields
+    DevState* tape_st = nullptr;
+    uint8_t* tape_m = nullptr;
+    adj_t* lam[2] = {nullptr, nullptr};
+    adj_t* lgf = nullptr;
+    adj_t* lpsi = nullptr;
+    adj_t* uv = nullptr;
+    double* parts = nullptr;
+    double* parts2 = nullptr;
+    double* cparts = nullptr;
+    AdjState* adj = nullptr;
+    size_t bytes = 0;
+
+    template <class T>
+    bool alloc(T*& p, size_t n)
+    {
+        void* v = nullptr;
+        if (cudaMalloc(&v, n * sizeof(T)) != cudaSuccess) return false;
+        owned.push_back(v);
+        bytes += n * sizeof(T);
+        p = static_cast<T*>(v);
+        return true;
+    }
+    ~AdjBuffers()
+    {
+        for (void* v : owned) cudaFree(v);
+    }
+};
+
+int acheck(flbm_sim* h, const char* what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return sim_fail(h, FLBM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return FLBM_OK;
+}
+
+#define ACK(h, call)                                                                                              \
+    do {                                                                                                          \
+        cudaError_t e_ = (call);                                                                                  \
+        if (e_ != cudaSuccess) return sim_fail((h), FLBM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Copy the handle's state (current populations, particle record, masks) to or from a slot.
+int save_state(flbm_sim* h, float* f, DevState* st, uint8_t* m, size_t mbytes)
+{
+    const size_t fbytes = sizeof(float) * 2 * 19 * h->kp.N;
+    ACK(h, cudaMemcpyAsync(f, h->fbuf[h->cur], fbytes, cudaMemcpyDeviceToDevice, h->stream));
+    ACK(h, cudaMemcpyAsync(st, h->st, sizeof(DevState), cudaMemcpyDeviceToDevice, h->stream));
+    ACK(h, cudaMemcpyAsync(m, h->masks, mbytes, cudaMemcpyDeviceToDevice, h->stream));
+    return FLBM_OK;
+}
+
+int load_state(flbm_sim* h, const float* f, const DevState* st, const uint8_t* m, size_t mbytes)
+{
+    const size_t fbytes = sizeof(float) * 2 * 19 * h->kp.N;
+    ACK(h, cudaMemcpyAsync(h->fbuf[h->cur], f, fbytes, cudaMemcpyDeviceToDevice, h->stream));
+    ACK(h, cudaMemcpyAsync(h->st, st, sizeof(DevState), cudaMemcpyDeviceToDevice, h->stream));
+    ACK(h, cudaMemcpyAsync(h->masks, m, mbytes, cudaMemcpyDeviceToDevice, h->stream));
+    return FLBM_OK;
+}
+
+// One reverse step: tape slot kk is step n's input state, slot kk+1 step n+1's.
+int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, adj_t* L1, adj_t* L0, double inv2T, double dFp_dg)
+{
+    const KParams& k = h->kp;
+    const size_t N = k.N, B3 = (size_t)k.B * k.B * k.B, mbytes = 2 * B3;
+    const float* tn = b.tape + (size_t)kk * 8 * N;
+    const float* t1 = tn + 8 * N;
+    const DevState* s0 = b.tape_st + kk;
+    const DevState* s1 = s0 + 1;
+    const uint8_t* m0 = b.tape_m + (size_t)kk * mbytes;
+    const uint8_t* m1 = m0 + mbytes;
+    cudaStream_t st = h->stream;
+    ka_pre<<<1, 1, 0, st>>>(b.adj, s1);
+    if (int rc = acheck(h, "ka_pre")) return rc;
+    ka_cover<<<h->box_blocks, kT, 0, st>>>(L1, t1, s0, m0, s1, m1, b.adj, b.uv, b.cparts, k);
+    if (int rc = acheck(h, "ka_cover")) return rc;
+    const int G3 = (k.B + 2) * (k.B + 2) * (k.B + 2);
+    ka_cover_mean<<<(G3 + kT - 1) / kT, kT, 0, st>>>(L1, s0, m0, s1, m1, b.uv, k);
+    if (int rc = acheck(h, "ka_cover_mean")) return rc;
+    ka_update<<<1, 1, 0, st>>>(b.adj, b.cparts, h->box_blocks, s0, inv2T, dFp_dg);
+    if (int rc = acheck(h, "ka_update")) return rc;
+    ka_psi_tape<<<h->grid, h->block, 0, st>>>(tn, h->psi, s0, m0, k);
+    if (int rc = acheck(h, "ka_psi_tape")) return rc;
+    k_virtual<<<(unsigned)((B3 + kThreads - 1) / kThreads), kThreads, 0, st>>>(h->psi, s0, m0, k);
+    if (int rc = acheck(h, "k_virtual")) return rc;
+    const unsigned nbs = (unsigned)((shell_count(k) + kThreads - 1) / kThreads);
+    k_shell<<<nbs, kThreads, 0, st>>>(h->psi, s0, m0, k);
+    if (int rc = acheck(h, "k_shell")) return rc;
+    ka_node_bulk<<<h->grid, h->block, 0, st>>>(tn, h->psi, L1, L0, b.lgf, s0, m0, b.adj, b.parts, k);
+    if (int rc = acheck(h, "ka_node_bulk")) return rc;
+    ka_node_near<<<dim3(k.ncx, k.ncy, k.ncz), h->block, 0, st>>>(tn, h->psi, L1, L0, b.lgf, s0, m0, b.adj, b.parts, k);
+    if (int rc = acheck(h, "ka_node_near")) return rc;
+    ka_lpsi<<<h->box_blocks, kT, 0, st>>>(b.lgf, h->psi, b.lpsi, s0, m0, b.adj, b.parts2, k);
+    if (int rc = acheck(h, "ka_lpsi")) return rc;
+    ka_lpsi_shell<<<nbs, kT, 0, st>>>(b.lgf, b.lpsi, s0, m0, k);
+    if (int rc = acheck(h, "ka_lpsi_shell")) return rc;
+    ka_final<<<h->grid, h->block, 0, st>>>(L0, b.lgf, b.lpsi, s0, m0, k);
+    if (int rc = acheck(h, "ka_final")) return rc;
+    ka_reduce<<<1, kT, 0, st>>>(b.adj, b.parts, h->ntiles, b.parts2, h->box_blocks);
+    return acheck(h, "ka_reduce");
+}
+
+}  // namespace
+
+extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_every, flbm_adjoint_result* out)
+{
+    if (!h || !out || nsteps < 1 || checkpoint_every < 1) return sim_fail(h, FLBM_E_INVAL, "invalid argument");
+    const KParams& k = h->kp;
+    const flbm_params& p = h->p;
+    if (!k.has_particle || p.kT != 0.0 || !k.tau1 || p.fluid_counterforce)
+        return sim_fail(h, FLBM_E_UNSUPPORTED,
+                        "the adjoint needs a particle, kT = 0, every relaxation time 1 and no counterforce");
+    std::memset(out, 0, sizeof(*out));
+    const int64_t T = nsteps;
+    const int K = (int)std::min<int64_t>(checkpoint_every, T);
+    const int64_t nck = (T + K - 1) / K;
+    const size_t N = k.N, B3 = (size_t)k.B * k.B * k.B, mbytes = 2 * B3;
+    const size_t fN = 2 * 19 * N;
+    AdjBuffers b;
+    if (!b.alloc(b.ck_f, (size_t)(nck + 1) * fN) || !b.alloc(b.ck_st, (size_t)(nck + 1)) ||
+        !b.alloc(b.ck_m, (size_t)(nck + 1) * mbytes) || !b.alloc(b.tape, (size_t)(K + 1) * 8 * N) ||
+        !b.alloc(b.tape_st, (size_t)(K + 1)) || !b.alloc(b.tape_m, (size_t)(K + 1) * mbytes) ||
+        !b.alloc(b.lam[0], 8 * N) || !b.alloc(b.lam[1], 8 * N) || !b.alloc(b.lgf, 6 * N) ||
+        !b.alloc(b.lpsi, (size_t)(2 * k.padn)) || !b.alloc(b.uv, 2 * B3) ||
+        !b.alloc(b.parts, (size_t)h->ntiles * kNodeParts) || !b.alloc(b.parts2, (size_t)h->box_blocks) ||
+        !b.alloc(b.cparts, (size_t)h->box_blocks * 9) || !b.alloc(b.adj, 1))
+        return sim_fail(h, FLBM_E_NOMEM, "adjoint checkpoints and tape");
+    cudaStream_t st = h->stream;
+    ACK(h, cudaMemsetAsync(b.adj, 0, sizeof(AdjState), st));
+    ACK(h, cudaMemsetAsync(b.lam[0], 0, sizeof(adj_t) * 8 * N, st));
+    ACK(h, cudaMemsetAsync(b.lpsi, 0, sizeof(adj_t) * 2 * k.padn, st));
+    cudaEvent_t ev[3];
+    for (auto& e : ev) ACK(h, cudaEventCreate(&e));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard()
+        {
+            for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+        }
+    } guard{ev};
+    cudaEventRecord(ev[0], st);
+    // Forward run: checkpoints every K steps, the sum of Vavg_z.
+    for (int64_t s = 0; s < T; ++s) {
+        if (s % K == 0) {
+            const int64_t c = s / K;
+            if (int rc = save_state(h, b.ck_f + c * fN, b.ck_st + c, b.ck_m + c * mbytes, mbytes)) return rc;
+        }
+        if (int rc = sim_step(h)) return rc;
+        ka_accJ<<<1, 1, 0, st>>>(h->st, b.adj);
+        if (int rc = acheck(h, "ka_accJ")) return rc;
+    }
+    if (int rc = save_state(h, b.ck_f + nck * fN, b.ck_st + nck, b.ck_m + nck * mbytes, mbytes)) return rc;
+    cudaEventRecord(ev[1], st);
+    // Reverse sweep, segment by segment from the last.
+    const double vol = 4.0 / 3.0 * M_PI * p.radius * p.radius * p.radius;
+    const double dFp_dg = vol * (p.rho_p_ratio - 1.0) * (p.rho_a0 + p.rho_b0);
+    const double inv2T = 0.5 / (double)T;
+    int lcur = 0;  // b.lam[lcur] is the adjoint of the later state
+    for (int64_t c = nck - 1; c >= 0; --c) {
+        const int64_t s0 = c * K;
+        const int Ls = (int)std::min<int64_t>(K, T - s0);
+        if (int rc = load_state(h, b.ck_f + c * fN, b.ck_st + c, b.ck_m + c * mbytes, mbytes)) return rc;
+        for (int kk = 0; kk <= Ls; ++kk) {
+            ka_tape<<<h->grid, h->block, 0, st>>>(h->fbuf[h->cur], b.tape + (size_t)kk * 8 * N, k);
+            if (int rc = acheck(h, "ka_tape")) return rc;
+            ACK(h, cudaMemcpyAsync(b.tape_st + kk, h->st, sizeof(DevState), cudaMemcpyDeviceToDevice, st));
+            ACK(h, cudaMemcpyAsync(b.tape_m + (size_t)kk * mbytes, h->masks, mbytes, cudaMemcpyDeviceToDevice, st));
+            if (kk < Ls)
+                if (int rc = sim_step(h)) return rc;
+        }
+        for (int kk = Ls - 1; kk >= 0; --kk) {
+            if (int rc = reverse_step(h, b, kk, b.lam[lcur], b.lam[1 - lcur], inv2T, dFp_dg)) return rc;
+            lcur = 1 - lcur;
+        }
+    }
+    if (int rc = load_state(h, b.ck_f + nck * fN, b.ck_st + nck, b.ck_m + nck * mbytes, mbytes)) return rc;
+    cudaEventRecord(ev[2], st);
+    AdjState a;
+    ACK(h, cudaMemcpyAsync(&a, b.adj, sizeof(a), cudaMemcpyDeviceToHost, st));
+    ACK(h, cudaStreamSynchronize(st));
+    float f0 = 0.0f, f1 = 0.0f;
+    cudaEventElapsedTime(&f0, ev[0], ev[1]);
+    cudaEventElapsedTime(&f1, ev[1], ev[2]);
+    out->J = a.J / (double)T;
+    out->dJ_dg = a.grad[0];
+    out->dJ_ddelta_rho = a.grad[1];
+    out->dJ_dG = a.grad[2];
+    out->steps = T;
+    out->checkpoint_every = K;
+    out->device_bytes = (double)b.bytes;
+    out->ms_forward = f0;
+    out->ms_reverse = f1;
+    return FLBM_OK;
+}

@@ -1,0 +1,108 @@
+// Node-level arithmetic of the noise-free collision with every relaxation
+// time 1 (Section 2, Eq. (lbe) with Eq. (sc-force) as source), forward and
+// transposed, as plain C++ that the CUDA kernels and a host test both compile.
+//
+// With tau = 1 every post-collision mode is a function of the component
+// densities rho_l, momenta j_l and Shan-Chen sums g_l = sum_i w_i psi_lbar(x+c_i) c_i:
+//   F_l   = -G rho_l g_l + (rho_l / rho_t) ext                       (force density)
+//   u     = (j_A + j_B + (F_A + F_B) / 2) / rho_t                    (v^(H))
+//   m*_0  = rho_l,   m*_{1..3} = rho_l u + F_l / 2
+//   m*_4  = rho_l u.u + u.F_l          m*_5 = rho_l (3 ux^2 - u.u) + 3 ux Flx - u.F_l
+//   m*_6  = rho_l (uy^2 - uz^2) + uy Fly - uz Flz
+//   m*_7  = rho_l ux uy + (ux Fly + uy Flx)/2, and m*_8 (y,z), m*_9 (x,z) alike
+//   ghost modes 10..18 = 0.
+// adj_modes() is the transpose of the Jacobian of this map: given the adjoint
+// of m*_{0..9} of both components it returns the adjoints of rho_l, j_l, g_l
+// and the derivative with respect to G.
+#pragma once
+
+#ifdef __CUDACC__
+#define FLBM_HD __host__ __device__ __forceinline__
+#else
+#define FLBM_HD inline
+#endif
+
+namespace flbm {
+
+template <class T>
+FLBM_HD void fwd_modes(const T rho[2], const T j[2][3], const T g[2][3], const T ext[3], T G, T ms[2][10])
+{
+    const T rt = rho[0] + rho[1];
+    T F[2][3], u[3];
+    for (int l = 0; l < 2; ++l)
+        for (int a = 0; a < 3; ++a) F[l][a] = -G * rho[l] * g[l][a] + rho[l] / rt * ext[a];
+    for (int a = 0; a < 3; ++a) u[a] = (j[0][a] + j[1][a] + T(0.5) * (F[0][a] + F[1][a])) / rt;
+    const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int l = 0; l < 2; ++l) {
+        const T r = rho[l];
+        const T* Fl = F[l];
+        const T uF = u[0] * Fl[0] + u[1] * Fl[1] + u[2] * Fl[2];
+        ms[l][0] = r;
+        for (int a = 0; a < 3; ++a) ms[l][1 + a] = r * u[a] + T(0.5) * Fl[a];
+        ms[l][4] = r * uu + uF;
+        ms[l][5] = r * (T(3) * u[0] * u[0] - uu) + T(3) * u[0] * Fl[0] - uF;
+        ms[l][6] = r * (u[1] * u[1] - u[2] * u[2]) + u[1] * Fl[1] - u[2] * Fl[2];
+        ms[l][7] = r * u[0] * u[1] + T(0.5) * (u[0] * Fl[1] + u[1] * Fl[0]);
+        ms[l][8] = r * u[1] * u[2] + T(0.5) * (u[1] * Fl[2] + u[2] * Fl[1]);
+        ms[l][9] = r * u[0] * u[2] + T(0.5) * (u[0] * Fl[2] + u[2] * Fl[0]);
+    }
+}
+
+// lm: adjoint of m*_{0..9} per component. Outputs are overwritten.
+template <class T>
+FLBM_HD void adj_modes(const T rho[2], const T j[2][3], const T g[2][3], const T ext[3], T G, const T lm[2][10],
+                       T lrho[2], T lj[2][3], T lg[2][3], T& lG)
+{
+    const T rt = rho[0] + rho[1];
+    T F[2][3], u[3];
+    for (int l = 0; l < 2; ++l)
+        for (int a = 0; a < 3; ++a) F[l][a] = -G * rho[l] * g[l][a] + rho[l] / rt * ext[a];
+    for (int a = 0; a < 3; ++a) u[a] = (j[0][a] + j[1][a] + T(0.5) * (F[0][a] + F[1][a])) / rt;
+    const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+
+    // Modes -> (rho_l, u, F_l) with u and F_l held as independent inputs.
+    T lu[3] = {T(0), T(0), T(0)};
+    T lF[2][3];
+    for (int l = 0; l < 2; ++l) {
+        const T r = rho[l];
+        const T* Fl = F[l];
+        const T* L = lm[l];
+        lrho[l] = L[0] + L[1] * u[0] + L[2] * u[1] + L[3] * u[2] + L[4] * uu + L[5] * (T(3) * u[0] * u[0] - uu) +
+                  L[6] * (u[1] * u[1] - u[2] * u[2]) + L[7] * u[0] * u[1] + L[8] * u[1] * u[2] + L[9] * u[0] * u[2];
+        lF[l][0] = T(0.5) * L[1] + u[0] * (L[4] + T(2) * L[5]) + T(0.5) * (L[7] * u[1] + L[9] * u[2]);
+        lF[l][1] = T(0.5) * L[2] + u[1] * (L[4] - L[5] + L[6]) + T(0.5) * (L[7] * u[0] + L[8] * u[2]);
+        lF[l][2] = T(0.5) * L[3] + u[2] * (L[4] - L[5] - L[6]) + T(0.5) * (L[8] * u[1] + L[9] * u[0]);
+        lu[0] += r * L[1] + L[4] * (T(2) * r * u[0] + Fl[0]) + L[5] * (T(4) * r * u[0] + T(2) * Fl[0]) +
+                 L[7] * (r * u[1] + T(0.5) * Fl[1]) + L[9] * (r * u[2] + T(0.5) * Fl[2]);
+        lu[1] += r * L[2] + (L[4] - L[5] + L[6]) * (T(2) * r * u[1] + Fl[1]) + L[7] * (r * u[0] + T(0.5) * Fl[0]) +
+                 L[8] * (r * u[2] + T(0.5) * Fl[2]);
+        lu[2] += r * L[3] + (L[4] - L[5] - L[6]) * (T(2) * r * u[2] + Fl[2]) + L[8] * (r * u[1] + T(0.5) * Fl[1]) +
+                 L[9] * (r * u[0] + T(0.5) * Fl[0]);
+    }
+    // u = (j_A + j_B + (F_A + F_B)/2) / rho_t
+    T ul = T(0);
+    for (int a = 0; a < 3; ++a) ul += lu[a] * u[a];
+    for (int l = 0; l < 2; ++l) {
+        lrho[l] -= ul / rt;
+        for (int a = 0; a < 3; ++a) {
+            lj[l][a] = lu[a] / rt;
+            lF[l][a] += T(0.5) * lu[a] / rt;
+        }
+    }
+    // F_l = -G rho_l g_l + (rho_l / rho_t) ext
+    T eF[2];
+    for (int l = 0; l < 2; ++l) eF[l] = lF[l][0] * ext[0] + lF[l][1] * ext[1] + lF[l][2] * ext[2];
+    const T es = (rho[0] * eF[0] + rho[1] * eF[1]) / (rt * rt);
+    lG = T(0);
+    for (int l = 0; l < 2; ++l) {
+        T gl = T(0);
+        for (int a = 0; a < 3; ++a) {
+            gl += g[l][a] * lF[l][a];
+            lg[l][a] = -G * rho[l] * lF[l][a];
+        }
+        lrho[l] += -G * gl + eF[l] / rt - es;
+        lG += -rho[l] * gl;
+    }
+}
+
+}  // namespace flbm

@@ -271,17 +271,22 @@ __device__ __forceinline__ double rel_axis(double r, double X, int L, int wall)
 
 // Block-wide sum of 8 doubles into out[0..7] (thread 0 holds the result in
 // s_out). Fixed reduction tree: deterministic.
+// A thread may pass active = false when all its v are 0: warps with no active
+// thread then skip their shuffles (FP64 arithmetic is a slow pipe).
 template <int NT>
-__device__ __forceinline__ void block_sum8(double v[8], double* s_red, double* s_out)
+__device__ __forceinline__ void block_sum8(double v[8], double* s_red, double* s_out, bool active = true)
 {
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int lane = tid & 31, warp = tid >> 5;
     const int nwarp = (blockDim.x * blockDim.y + 31) >> 5;
+    const bool warp_any = __any_sync(0xffffffffu, active);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         double a = v[k];
+        if (warp_any) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+            for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+        }
         if (lane == 0) s_red[warp * 8 + k] = a;
     }
     __syncthreads();

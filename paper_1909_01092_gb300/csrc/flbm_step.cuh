@@ -393,7 +393,7 @@ __device__ __forceinline__ void near_tile(int cx, int cy, int cz, int tx, int ty
         if (tid < 8) partials[cand * 8 + tid] = 0.0;
         return;
     }
-    block_sum8<kThreadsStep>(acc, s_red, s_out);
+    block_sum8<kThreadsStep>(acc, s_red, s_out, links != 0);
     if (tid < 8) partials[cand * 8 + tid] = s_out[tid];
     __syncthreads();  // s_out is reused by the next tile of a persistent block
 }

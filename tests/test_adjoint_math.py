@@ -1,0 +1,97 @@
+"""Host check of the node-level collision adjoint the CUDA adjoint kernels use
+(paper_1909_01092_gb300/csrc/flbm_adjoint_math.h): adj_modes must be the
+transpose of the Jacobian of fwd_modes. Compiled here with g++ in double
+precision; checked against central finite differences of fwd_modes through
+the identity <lambda, J v> = <J^T lambda, v> for random lambda and v."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_1909_01092_gb300", "csrc")
+
+SHIM = r"""
+#include "flbm_adjoint_math.h"
+extern "C" void fwd(const double* in, double G, double* ms) {
+    const double rho[2] = {in[0], in[1]};
+    const double j[2][3] = {{in[2], in[3], in[4]}, {in[5], in[6], in[7]}};
+    const double g[2][3] = {{in[8], in[9], in[10]}, {in[11], in[12], in[13]}};
+    const double ext[3] = {in[14], in[15], in[16]};
+    double m[2][10];
+    flbm::fwd_modes<double>(rho, j, g, ext, G, m);
+    for (int l = 0; l < 2; ++l) for (int k = 0; k < 10; ++k) ms[10 * l + k] = m[l][k];
+}
+extern "C" void adj(const double* in, double G, const double* lmf, double* out) {
+    const double rho[2] = {in[0], in[1]};
+    const double j[2][3] = {{in[2], in[3], in[4]}, {in[5], in[6], in[7]}};
+    const double g[2][3] = {{in[8], in[9], in[10]}, {in[11], in[12], in[13]}};
+    const double ext[3] = {in[14], in[15], in[16]};
+    double lm[2][10];
+    for (int l = 0; l < 2; ++l) for (int k = 0; k < 10; ++k) lm[l][k] = lmf[10 * l + k];
+    double lrho[2], lj[2][3], lg[2][3], lG;
+    flbm::adj_modes<double>(rho, j, g, ext, G, lm, lrho, lj, lg, lG);
+    out[0] = lrho[0]; out[1] = lrho[1];
+    for (int l = 0; l < 2; ++l) for (int a = 0; a < 3; ++a) { out[2 + 3 * l + a] = lj[l][a]; out[8 + 3 * l + a] = lg[l][a]; }
+    out[14] = lG;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def shim(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("adjmath")
+    src = d / "shim.cpp"
+    src.write_text(SHIM)
+    lib = d / "libshim.so"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC, "-o", str(lib), str(src)], check=True)
+    L = ctypes.CDLL(str(lib))
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.fwd.argtypes = [dp, ctypes.c_double, dp]
+    L.adj.argtypes = [dp, ctypes.c_double, dp, dp]
+    return L
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _fwd(L, x, G):
+    ms = np.zeros(20)
+    L.fwd(_p(np.ascontiguousarray(x)), G, _p(ms))
+    return ms
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_adjoint_is_jacobian_transpose(shim, seed):
+    rng = np.random.default_rng(seed)
+    x = np.concatenate([[1.0 + 0.1 * rng.standard_normal(), 0.05 + 0.01 * rng.standard_normal()],
+                        0.05 * rng.standard_normal(6), 0.1 * rng.standard_normal(6),
+                        (1e-3 * rng.standard_normal(3)) if seed % 2 else np.zeros(3)])
+    G = 1.2 + 0.3 * rng.standard_normal()
+    lm = rng.standard_normal(20)
+    out = np.zeros(15)
+    shim.adj(_p(x), G, _p(lm), _p(out))
+    v = rng.standard_normal(17)
+    v[14:] = 0.0  # ext is a constant, not an input
+    vG = rng.standard_normal()
+    h = 1e-5
+    jv = (_fwd(shim, x + h * v, G + h * vG) - _fwd(shim, x - h * v, G - h * vG)) / (2 * h)
+    lhs = lm @ jv
+    rhs = out[:14] @ v[:14] + out[14] * vG
+    assert abs(lhs - rhs) <= 1e-8 * max(1.0, abs(lhs))
+
+
+def test_modes_at_rest_are_the_equilibrium(shim):
+    """Zero momentum and force: m*_0 = rho_l, every other mode 0 (the rest
+    state of Section 2's collision)."""
+    x = np.zeros(17)
+    x[0], x[1] = 1.0, 0.05
+    ms = _fwd(shim, x, 1.2)
+    assert ms[0] == 1.0 and ms[10] == 0.05
+    assert np.all(ms[1:10] == 0.0) and np.all(ms[11:20] == 0.0)
