@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true",
-                    help="skip the 128-replica ensemble and the adjoint measurements")
+                    help="skip the ensemble, adjoint and small-configuration measurements")
     ap.add_argument("--lz", type=int, default=512, help="channel length (shorter only for profiler captures)")
     return ap.parse_args()
 
@@ -238,6 +238,38 @@ def ensemble_bench(binding, W, steps: int = 100) -> dict:
             "speedup": ms1 / ms}
 
 
+def small_bench(binding, W, steps: int = 2000) -> list:
+    """The two small channels (16x16x32 noise-free R=3; 32x32x64 kT=1e-5 R=4):
+    their populations (2.5 and 20 MB) stay in L2 and a step is a few
+    microseconds of work per kernel, so they are launch-bound. Each is timed
+    with graph replay (two-step CUDA graphs on a dedicated stream) and with
+    plain launches from the host."""
+    import torch
+
+    out = []
+    for name, p in (("channel_16x16x32_R3_noise_free", W.channel_small()),
+                    ("channel_32x32x64_R4_kT1e-5", W.channel_fluct())):
+        nodes = p["lx"] * p["ly"] * p["lz"]
+        res = {"workload": name, "nodes": nodes, "steps": steps, "l2_resident": True}
+        for mode in ("graphs", "launches"):
+            sim = binding.Sim(p, stream=torch.cuda.Stream())
+            if mode == "graphs":
+                sim.use_graphs(True)
+            sim.step(20)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(sim.stream)
+            sim.step(steps)
+            e1.record(sim.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            res[mode] = {"ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6}
+            sim.close()
+        res["graph_speedup"] = res["launches"]["ms_per_step"] / res["graphs"]["ms_per_step"]
+        out.append(res)
+    return out
+
+
 def adjoint_bench(binding, W, steps: int = 2000, every: int = 100) -> dict:
     """Gradient of the time-averaged settling velocity on the 64x64x128
     noise-free channel (R=8, delta_rho=0.3, G=1.2) by the adjoint with
@@ -340,11 +372,13 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
-    ens = adj = None
+    nfluid = sim.particle()["nfluid"]
+    ens = adj = small = None
     if rank == 0 and world == 1 and not args.no_ensemble:
         sim.close()
         ens = ensemble_bench(binding, W)
         adj = adjoint_bench(binding, W)
+        small = small_bench(binding, W)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -353,7 +387,8 @@ def run_ours(args):
                            "radius": p["radius"], "g": p["g"], "G": p["G"], "walls": "x,y", "replicas_per_gpu": 1,
                            "l2": "inputs larger than L2 (2.55 GB of populations), no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches,
-                "ensemble": ens, "adjoint": adj}
+                "fluid_only_mlups": aggregate_mlups(nfluid, args.steps, world, ms_max),
+                "ensemble": ens, "adjoint": adj, "small_configs": small}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:

@@ -57,17 +57,21 @@ struct AdjState {
     float lFf[3], lTf[3], lledf[2], lPf[3], lLf[3];    // float copies for the node kernels
 };
 
-// Type of the adjoint fields (a, b, lambda g, lambda psi) and of the node
-// arithmetic that produces them. Double by default: with float32 the
-// adjoint of a weakly coupled parameter (G in a dilute mixture) loses about
-// 1e-3 relative accuracy over a few tens of steps, because the adjoint
-// density field carries large smooth parts whose neighbour differences set
-// the momentum adjoint. Building with -DFLBM_ADJ_REAL=float trades that for
-// speed.
-#ifndef FLBM_ADJ_REAL
-#define FLBM_ADJ_REAL double
+// Precision. The adjoint fields carry large smooth parts (the adjoints of
+// conserved totals) whose neighbour differences set the result: a_l, b_l for
+// the momentum and stress adjoints, lambda g_l (= -G rho_l lambda F_l, which
+// inherits b_l / 2) for the adjoint of psi. Stored in float32 they cost a
+// weakly coupled gradient (G or delta_rho in a dilute mixture) 1e-3 to 5e-2
+// relative accuracy within tens of steps. So every adjoint field is FP64
+// (lam_t, aux_t) and the large parts enter exactly; only the neighbour
+// differences (a(x+c_i) - a(x)) + c_i . (b(x+c_i) - b(x)) go through the
+// float32 mode projection and collision transpose (adj_modes), the large
+// part through adj_modes_ab in FP64.
+#ifndef FLBM_ADJ_AUX
+#define FLBM_ADJ_AUX double
 #endif
-using adj_t = FLBM_ADJ_REAL;
+using lam_t = double;
+using aux_t = FLBM_ADJ_AUX;
 
 constexpr int kT = 256;  // threads per block
 constexpr int kNodeParts = 12;  // per tile: lX[3], lV[3], lOm[3], dJ/dG, ld[2]
@@ -222,10 +226,10 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 // ledger. lambda_mean_l / cnt goes to uv[] for ka_cover_mean. Per-block
 // partials: lambda X', lambda V', lambda Omega'.
 // ---------------------------------------------------------------------------
-static __global__ void __launch_bounds__(kT) ka_cover(adj_t* __restrict__ lam1, const float* __restrict__ tape1,
+static __global__ void __launch_bounds__(kT) ka_cover(lam_t* __restrict__ lam1, const float* __restrict__ tape1,
                                                       const DevState* __restrict__ s0, const uint8_t* __restrict__ mk0,
                                                       const DevState* __restrict__ s1, const uint8_t* __restrict__ mk1,
-                                                      const AdjState* __restrict__ adj, adj_t* __restrict__ uv,
+                                                      const AdjState* __restrict__ adj, lam_t* __restrict__ uv,
                                                       double* __restrict__ parts, KParams P)
 {
     __shared__ double s_red[(kT / 32) * 8];
@@ -241,8 +245,8 @@ static __global__ void __launch_bounds__(kT) ka_cover(adj_t* __restrict__ lam1, 
     double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // lX'[3], lV'[3], lOm'[3]
     if (t < B3) {
         const int d[3] = {t % B, (t / B) % B, t / (B * B)};
-        uv[t] = adj_t(0);
-        uv[B3 + t] = adj_t(0);
+        uv[t] = 0.0;
+        uv[B3 + t] = 0.0;
         if (m1[t]) {  // covered
             int c[3];
             for (int a = 0; a < 3; ++a) {
@@ -256,8 +260,8 @@ static __global__ void __launch_bounds__(kT) ka_cover(adj_t* __restrict__ lam1, 
                 cross3(adj->lL, r, lb);
                 for (int a = 0; a < 3; ++a) lb[a] += adj->lP[a];
                 for (int l = 0; l < 2; ++l) {
-                    lam1[(size_t)l * N + n] = (adj_t)adj->lled[l];
-                    for (int a = 0; a < 3; ++a) lam1[(size_t)(2 + 3 * l + a) * N + n] = (adj_t)lb[a];
+                    lam1[(size_t)l * N + n] = adj->lled[l];
+                    for (int a = 0; a < 3; ++a) lam1[(size_t)(2 + 3 * l + a) * N + n] = lb[a];
                 }
                 for (int a = 0; a < 3; ++a) j[a] = (double)tape1[(2 + a) * N + n] + (double)tape1[(5 + a) * N + n];
                 cross3(j, adj->lL, t3);  // d/dX' of lambda_L . ((c - X') x j) = -(j x lambda_L)
@@ -298,7 +302,7 @@ static __global__ void __launch_bounds__(kT) ka_cover(adj_t* __restrict__ lam1, 
                     double bl[3];
                     for (int a = 0; a < 3; ++a) bl[a] = lam1[(size_t)(2 + 3 * l + a) * N + n];
                     const double lmean = al + bl[0] * ub[0] + bl[1] * ub[1] + bl[2] * ub[2] - lqub - adj->lled[l];
-                    if (cnt) uv[(size_t)l * B3 + t] = (adj_t)(lmean / cnt);
+                    if (cnt) uv[(size_t)l * B3 + t] = lmean / cnt;
                     for (int a = 0; a < 3; ++a) lub[a] += rl[l] * bl[a];
                 }
                 for (int a = 0; a < 3; ++a) lub[a] -= rsum * lq[a];
@@ -329,10 +333,10 @@ static __global__ void __launch_bounds__(kT) ka_cover(adj_t* __restrict__ lam1, 
 // Neighbours of uncovered nodes that fed the neighbour mean: fluid at n and
 // at n+1. Gathers uv of uncovered neighbours into a_l. One thread per node of
 // the old box grown by one.
-static __global__ void __launch_bounds__(kT) ka_cover_mean(adj_t* __restrict__ lam1, const DevState* __restrict__ s0,
+static __global__ void __launch_bounds__(kT) ka_cover_mean(lam_t* __restrict__ lam1, const DevState* __restrict__ s0,
                                                            const uint8_t* __restrict__ mk0,
                                                            const DevState* __restrict__ s1,
-                                                           const uint8_t* __restrict__ mk1, const adj_t* __restrict__ uv,
+                                                           const uint8_t* __restrict__ mk1, const lam_t* __restrict__ uv,
                                                            KParams P)
 {
     const int B = P.B, G = B + 2, B3 = B * B * B;
@@ -353,7 +357,7 @@ static __global__ void __launch_bounds__(kT) ka_cover_mean(adj_t* __restrict__ l
         }
     }
     if (is_solid(m[0], m[1], m[2], o0, m0, P) || is_solid(m[0], m[1], m[2], o1, m1, P)) return;
-    adj_t add[2] = {adj_t(0), adj_t(0)};
+    lam_t add[2] = {0.0, 0.0};
     for (int jd = 1; jd < 19; ++jd) {
         int c[3];
         if (!nbr(m[0], m[1], m[2], cxv(jd), cyv(jd), czv(jd), P, c)) continue;
@@ -363,7 +367,7 @@ static __global__ void __launch_bounds__(kT) ka_cover_mean(adj_t* __restrict__ l
         add[0] += uv[e];
         add[1] += uv[B3 + e];
     }
-    if (add[0] != adj_t(0) || add[1] != adj_t(0)) {
+    if (add[0] != 0.0 || add[1] != 0.0) {
         const uint32_t n = lin(m[0], m[1], m[2], P);
         lam1[n] += add[0];
         lam1[P.N + n] += add[1];
@@ -413,8 +417,8 @@ static __global__ void ka_update(AdjState* __restrict__ a, const double* __restr
 // PARTICLE: the tile is near the particle (links, reaction); else it has none.
 template <bool PARTICLE>
 __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty, const float* __restrict__ tape,
-                                         const float* __restrict__ psi, const adj_t* __restrict__ lam1,
-                                         adj_t* __restrict__ lam0, adj_t* __restrict__ lg,
+                                         const float* __restrict__ psi, const lam_t* __restrict__ lam1,
+                                         lam_t* __restrict__ lam0, aux_t* __restrict__ lg,
                                          const DevState* __restrict__ s0, const uint8_t* __restrict__ mk0,
                                          const AdjState* __restrict__ adj, double* __restrict__ parts,
                                          const KParams& P)
@@ -432,8 +436,8 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
         const uint8_t* m0 = cur_mask(s0, mk0, P);
         const uint32_t n = lin(x, y, z, P);
         if (PARTICLE && solid_at(x, y, z, s0, m0, P)) {
-            for (int k = 0; k < 8; ++k) lam0[k * N + n] = adj_t(0);
-            for (int k = 0; k < 6; ++k) lg[k * N + n] = adj_t(0);
+            for (int k = 0; k < 8; ++k) lam0[k * N + n] = 0.0;
+            for (int k = 0; k < 6; ++k) lg[k * N + n] = 0.0f;
         } else {
             float rho[2], j[2][3], g[2][3];
             for (int l = 0; l < 2; ++l) {
@@ -486,20 +490,25 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
             }
             const float* lF = adj->lFf;
             const float* lT = adj->lTf;
-            adj_t lrx[2] = {adj_t(0), adj_t(0)};  // extra adjoint of rho_l from links and the reaction
-            adj_t lm[2][10];
+            double lrx[2] = {0.0, 0.0};  // extra adjoint of rho_l from links and the reaction
+            double axd[2], bxd[2][3];      // a_l, b_l of this node (FP64)
+            float lm[2][10];               // mode adjoint of the neighbour differences
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
-                const adj_t ax = lam1[(size_t)l * N + n];
-                const adj_t bx[3] = {lam1[(2 + 3 * l) * N + n], lam1[(3 + 3 * l) * N + n], lam1[(4 + 3 * l) * N + n]};
-                adj_t wl[19];
-                double ldl = 0.0;
+                axd[l] = lam1[(size_t)l * N + n];
+                for (int a = 0; a < 3; ++a) bxd[l][a] = lam1[(size_t)(2 + 3 * l + a) * N + n];
+                const double ax = axd[l];
+                const double* bx = bxd[l];
+                float wl[19];
+                float wsum = 0.0f;
 #pragma unroll
                 for (int i = 0; i < 19; ++i) {
                     const int cx = cxv(i), cy = cyv(i), cz = czv(i);
-                    adj_t v;
+                    // dv = lambda f*_li - a_l(x) - c_i . b_l(x): small, float32 is enough.
+                    float dv;
                     if ((wall_nb | solid_nb) >> i & 1u) {
-                        v = ax - (cx * bx[0] + cy * bx[1] + cz * bx[2]);
+                        const double cb = cx * bx[0] + cy * bx[1] + cz * bx[2];
+                        dv = (float)(-2.0 * cb);  // bounce-back reads (x, -c_i): a - c_i . b
                         if (PARTICLE && (solid_nb >> i & 1u)) {
                             const float d[3] = {rnf[0] + 0.5f * cx, rnf[1] + 0.5f * cy, rnf[2] + 0.5f * cz};
                             const float kap = cx * (lF[0] + lT[1] * d[2] - lT[2] * d[1]) +
@@ -510,9 +519,9 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                             const float ubc = (V[0] + Om[1] * d[2] - Om[2] * d[1]) * cx +
                                               (V[1] + Om[2] * d[0] - Om[0] * d[2]) * cy +
                                               (V[2] + Om[0] * d[1] - Om[1] * d[0]) * cz;
-                            const adj_t lcorr = -v - kap + adj->lledf[l];
-                            lrx[l] += lcorr * adj_t(6.0f * wv(i) * ubc);
-                            const double lub = (double)lcorr * 6.0 * wv(i) * rho[l];  // lambda (u_b . c_i)
+                            const double lcorr = -(ax - cb) - (double)kap + adj->lled[l];
+                            lrx[l] += lcorr * (6.0 * wv(i) * ubc);
+                            const double lub = lcorr * 6.0 * wv(i) * rho[l];  // lambda (u_b . c_i)
                             const double lb[3] = {lub * cx, lub * cy, lub * cz};
                             acc[3] += lb[0]; acc[4] += lb[1]; acc[5] += lb[2];
                             acc[6] += d[1] * lb[2] - d[2] * lb[1];
@@ -527,22 +536,22 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                             acc[0] -= fr[1] * lT[2] - fr[2] * lT[1];
                             acc[1] -= fr[2] * lT[0] - fr[0] * lT[2];
                             acc[2] -= fr[0] * lT[1] - fr[1] * lT[0];
-                            v += adj_t(2) * kap;
+                            dv += 2.0f * kap;
                         }
                     } else {
                         const uint32_t q = qidx[i];
-                        v = lam1[(size_t)l * N + q];
-                        if (cx) v += cx * lam1[(2 + 3 * l) * N + q];
-                        if (cy) v += cy * lam1[(3 + 3 * l) * N + q];
-                        if (cz) v += cz * lam1[(4 + 3 * l) * N + q];
+                        dv = (float)(lam1[(size_t)l * N + q] - ax);
+                        if (cx) dv += cx * (float)(lam1[(2 + 3 * l) * N + q] - bx[0]);
+                        if (cy) dv += cy * (float)(lam1[(3 + 3 * l) * N + q] - bx[1]);
+                        if (cz) dv += cz * (float)(lam1[(4 + 3 * l) * N + q] - bx[2]);
                     }
-                    wl[i] = adj_t(wv(i)) * v;
-                    ldl += wl[i];
+                    wl[i] = wv(i) * dv;
+                    wsum += wl[i];
                 }
-                acc[10 + l] += ldl;
-                adj_t mm[10];
-                project10<adj_t>(wl, mm);
-                for (int k = 0; k < 10; ++k) lm[l][k] = mm[k] / adj_t(bnorm(k));
+                acc[10 + l] += ax + (double)wsum;  // sum_i w_i lambda f*_li (mass correction)
+                float mm[10];
+                project10<float>(wl, mm);
+                for (int k = 0; k < 10; ++k) lm[l][k] = mm[k] / bnorm(k);
             }
             // Shan-Chen reaction on the particle: F += G w_i (rhoA psiB(q) + rhoB psiA(q)) c_i.
             if (PARTICLE && solid_nb) {
@@ -558,8 +567,8 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                                       cz * (lF[2] + lT[0] * d[1] - lT[1] * d[0]);
                     const float w = wv(i);
                     acc[9] += (double)kap * w * (rho[0] * pb + rho[1] * pa);
-                    lrx[0] += adj_t(kap * P.G * w * pb);
-                    lrx[1] += adj_t(kap * P.G * w * pa);
+                    lrx[0] += (double)(kap * P.G * w * pb);
+                    lrx[1] += (double)(kap * P.G * w * pa);
                     const double mag = (double)P.G * w * (rho[0] * pb + rho[1] * pa);
                     const double fr[3] = {mag * cx, mag * cy, mag * cz};
                     acc[0] -= fr[1] * lT[2] - fr[2] * lT[1];
@@ -567,22 +576,26 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                     acc[2] -= fr[0] * lT[1] - fr[1] * lT[0];
                 }
             }
-            adj_t rr[2], jr[2][3], gr[2][3], er[3], lrho[2], lj[2][3], lgv[2][3], lG;
+            // Transpose of the collision: the float32 part from the differences, the
+            // FP64 part from (a_l, b_l) of this node (modes 0..3 only).
+            float lrho[2], lj[2][3], lgv[2][3], lG;
+            adj_modes<float>(rho, j, g, ext, P.G, lm, lrho, lj, lgv, lG);
+            double rd[2], jd[2][3], gd[2][3], ed[3], lrd[2], ljd[2][3], lgd[2][3], lGd;
             for (int l = 0; l < 2; ++l) {
-                rr[l] = rho[l];
+                rd[l] = rho[l];
                 for (int a = 0; a < 3; ++a) {
-                    jr[l][a] = j[l][a];
-                    gr[l][a] = g[l][a];
+                    jd[l][a] = j[l][a];
+                    gd[l][a] = g[l][a];
                 }
             }
-            for (int a = 0; a < 3; ++a) er[a] = ext[a];
-            adj_modes<adj_t>(rr, jr, gr, er, adj_t(P.G), lm, lrho, lj, lgv, lG);
-            acc[9] += lG;
+            for (int a = 0; a < 3; ++a) ed[a] = ext[a];
+            adj_modes_ab<double>(rd, jd, gd, ed, (double)P.G, axd, bxd, lrd, ljd, lgd, lGd);
+            acc[9] += lGd + (double)lG;
             for (int l = 0; l < 2; ++l) {
-                lam0[(size_t)l * N + n] = lrho[l] + lrx[l];
+                lam0[(size_t)l * N + n] = lrd[l] + (double)lrho[l] + lrx[l];
                 for (int a = 0; a < 3; ++a) {
-                    lam0[(size_t)(2 + 3 * l + a) * N + n] = lj[l][a];
-                    lg[(size_t)(3 * l + a) * N + n] = lgv[l][a];
+                    lam0[(size_t)(2 + 3 * l + a) * N + n] = ljd[l][a] + (double)lj[l][a];
+                    lg[(size_t)(3 * l + a) * N + n] = (aux_t)(lgd[l][a] + (double)lgv[l][a]);
                 }
             }
         }
@@ -604,9 +617,9 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
 }
 
 // Tiles away from the particle (all tiles when there is none).
-static __global__ void __launch_bounds__(kT, sizeof(adj_t) == 4 ? 3 : 2) ka_node_bulk(const float* __restrict__ tape, const float* __restrict__ psi,
-                                                          const adj_t* __restrict__ lam1, adj_t* __restrict__ lam0,
-                                                          adj_t* __restrict__ lg, const DevState* __restrict__ s0,
+static __global__ void __launch_bounds__(kT, 2) ka_node_bulk(const float* __restrict__ tape, const float* __restrict__ psi,
+                                                          const lam_t* __restrict__ lam1, lam_t* __restrict__ lam0,
+                                                          aux_t* __restrict__ lg, const DevState* __restrict__ s0,
                                                           const uint8_t* __restrict__ mk0,
                                                           const AdjState* __restrict__ adj, double* __restrict__ parts,
                                                           KParams P)
@@ -621,8 +634,8 @@ static __global__ void __launch_bounds__(kT, sizeof(adj_t) == 4 ? 3 : 2) ka_node
 
 // Tiles near the particle: the candidate grid of the forward step.
 static __global__ void __launch_bounds__(kT) ka_node_near(const float* __restrict__ tape, const float* __restrict__ psi,
-                                                          const adj_t* __restrict__ lam1, adj_t* __restrict__ lam0,
-                                                          adj_t* __restrict__ lg, const DevState* __restrict__ s0,
+                                                          const lam_t* __restrict__ lam1, lam_t* __restrict__ lam0,
+                                                          aux_t* __restrict__ lg, const DevState* __restrict__ s0,
                                                           const uint8_t* __restrict__ mk0,
                                                           const AdjState* __restrict__ adj, double* __restrict__ parts,
                                                           KParams P)
@@ -651,17 +664,17 @@ __device__ __forceinline__ int fluid_count(const int q[3], const DevState* s0, c
 
 // lambda psi_l at padded point p (in range on every periodic axis): the
 // Shan-Chen stencil transposed, g_A reads psi_B and g_B reads psi_A.
-__device__ __forceinline__ void lpsi_gather(const int p[3], const adj_t* __restrict__ lg, const KParams& P, adj_t out[2])
+__device__ __forceinline__ void lpsi_gather(const int p[3], const aux_t* __restrict__ lg, const KParams& P, aux_t out[2])
 {
     const size_t N = P.N;
-    adj_t la = adj_t(0), lb = adj_t(0);
+    aux_t la = aux_t(0), lb = aux_t(0);
     for (int i = 1; i < 19; ++i) {
         int x[3];
         if (!nbr(p[0], p[1], p[2], -cxv(i), -cyv(i), -czv(i), P, x)) continue;
         // a source outside the domain (p is a ghost and -c_i points further out) is skipped by nbr()
         const uint32_t s = lin(x[0], x[1], x[2], P);
-        const adj_t w = wv(i);
-        const adj_t cx = cxv(i), cy = cyv(i), cz = czv(i);
+        const aux_t w = wv(i);
+        const aux_t cx = cxv(i), cy = cyv(i), cz = czv(i);
         lb += w * (cx * lg[0 * N + s] + cy * lg[1 * N + s] + cz * lg[2 * N + s]);
         la += w * (cx * lg[3 * N + s] + cy * lg[4 * N + s] + cz * lg[5 * N + s]);
     }
@@ -676,8 +689,8 @@ __device__ __forceinline__ void lpsi_gather(const int p[3], const adj_t* __restr
 // mu_l = lambda psi_l / cnt where the clip at 0 is inactive, written at the
 // node's place in lpsi; dJ/d delta_rho partial per block.
 // ---------------------------------------------------------------------------
-static __global__ void __launch_bounds__(kT) ka_lpsi(const adj_t* __restrict__ lg, const float* __restrict__ psi,
-                                                     adj_t* __restrict__ lpsi, const DevState* __restrict__ s0,
+static __global__ void __launch_bounds__(kT) ka_lpsi(const aux_t* __restrict__ lg, const float* __restrict__ psi,
+                                                     aux_t* __restrict__ lpsi, const DevState* __restrict__ s0,
                                                      const uint8_t* __restrict__ mk0, const AdjState* __restrict__ adj,
                                                      double* __restrict__ parts2, KParams P)
 {
@@ -696,12 +709,12 @@ static __global__ void __launch_bounds__(kT) ka_lpsi(const adj_t* __restrict__ l
             if (!P.wall[a] && p[a] >= L[a]) p[a] -= L[a];
         }
         const int x = p[0], y = p[1], z = p[2];
-        adj_t lp[2];
+        aux_t lp[2];
         lpsi_gather(p, lg, P, lp);
         const long long pi = pad_index(x, y, z, P);
         {
             const int cnt = fluid_count(p, s0, m0, P);
-            adj_t mu[2] = {adj_t(0), adj_t(0)};
+            aux_t mu[2] = {aux_t(0), aux_t(0)};
             if (cnt) {
                 const float* lF = adj->lFf;
                 const float* lT = adj->lTf;
@@ -721,12 +734,12 @@ static __global__ void __launch_bounds__(kT) ka_lpsi(const adj_t* __restrict__ l
                                       cy * (lF[1] + lT[2] * d[0] - lT[0] * d[2]) +
                                       cz * (lF[2] + lT[0] * d[1] - lT[1] * d[0]);
                     const long long qi = pad_index(q[0], q[1], q[2], P);
-                    lp[1] += adj_t(kap * P.G * wv(i) * psi[qi]);           // d/d psiB(p) of rhoA(q) psiB(p)
-                    lp[0] += adj_t(kap * P.G * wv(i) * psi[P.padn + qi]);  // d/d psiA(p) of rhoB(q) psiA(p)
+                    lp[1] += aux_t(kap * P.G * wv(i) * psi[qi]);           // d/d psiB(p) of rhoA(q) psiB(p)
+                    lp[0] += aux_t(kap * P.G * wv(i) * psi[P.padn + qi]);  // d/d psiA(p) of rhoB(q) psiA(p)
                 }
                 const bool actA = psi[pi] > 0.0f, actB = psi[P.padn + pi] > 0.0f;
-                if (actA) { mu[0] = lp[0] / adj_t(cnt); dd += lp[0]; }
-                if (actB) { mu[1] = lp[1] / adj_t(cnt); dd -= lp[1]; }
+                if (actA) { mu[0] = lp[0] / aux_t(cnt); dd += lp[0]; }
+                if (actB) { mu[1] = lp[1] / aux_t(cnt); dd -= lp[1]; }
             }
             lpsi[pi] = mu[0];
             lpsi[P.padn + pi] = mu[1];
@@ -739,7 +752,7 @@ static __global__ void __launch_bounds__(kT) ka_lpsi(const adj_t* __restrict__ l
 
 // Wall ghosts of the psi shell (points outside along a wall axis, in range on
 // the periodic axes): mu_l = lambda psi_l / cnt, the mean over fluid neighbours.
-static __global__ void __launch_bounds__(kT) ka_lpsi_shell(const adj_t* __restrict__ lg, adj_t* __restrict__ lpsi,
+static __global__ void __launch_bounds__(kT) ka_lpsi_shell(const aux_t* __restrict__ lg, aux_t* __restrict__ lpsi,
                                                            const DevState* __restrict__ s0,
                                                            const uint8_t* __restrict__ mk0, KParams P)
 {
@@ -773,19 +786,19 @@ static __global__ void __launch_bounds__(kT) ka_lpsi_shell(const adj_t* __restri
     }
     if (!ghost) return;
     const uint8_t* m0 = cur_mask(s0, mk0, P);
-    adj_t lp[2];
+    aux_t lp[2];
     lpsi_gather(p, lg, P, lp);
     const int cnt = fluid_count(p, s0, m0, P);
     const long long dst = (long long)(p[0] + 1) + (long long)P.px * ((p[1] + 1) + (long long)P.py * (p[2] + 1));
-    lpsi[dst] = cnt ? lp[0] / adj_t(cnt) : adj_t(0);
-    lpsi[P.padn + dst] = cnt ? lp[1] / adj_t(cnt) : adj_t(0);
+    lpsi[dst] = cnt ? lp[0] / aux_t(cnt) : aux_t(0);
+    lpsi[P.padn + dst] = cnt ? lp[1] / aux_t(cnt) : aux_t(0);
 }
 
 // a_l of fluid nodes: lambda psi of the node (the Shan-Chen stencil
 // transposed) plus mu of every particle node and wall ghost among its
 // neighbours (each averaged this node's density).
-static __global__ void __launch_bounds__(kT) ka_final(adj_t* __restrict__ lam0, const adj_t* __restrict__ lg,
-                                                      const adj_t* __restrict__ lpsi, const DevState* __restrict__ s0,
+static __global__ void __launch_bounds__(kT) ka_final(lam_t* __restrict__ lam0, const aux_t* __restrict__ lg,
+                                                      const aux_t* __restrict__ lpsi, const DevState* __restrict__ s0,
                                                       const uint8_t* __restrict__ mk0, KParams P)
 {
     const int x = blockIdx.x * P.tx + threadIdx.x;
@@ -795,7 +808,7 @@ static __global__ void __launch_bounds__(kT) ka_final(adj_t* __restrict__ lam0, 
     const uint8_t* m0 = cur_mask(s0, mk0, P);
     if (solid_at(x, y, z, s0, m0, P)) return;
     const int p[3] = {x, y, z};
-    adj_t add[2];
+    aux_t add[2];
     lpsi_gather(p, lg, P, add);  // psi = rho on this fluid node
     const int L[3] = {P.lx, P.ly, P.lz};
     for (int i = 1; i < 19; ++i) {
@@ -865,10 +878,10 @@ struct AdjBuffers {
     float* tape = nullptr;     // K+1 moment fields
     DevState* tape_st = nullptr;
     uint8_t* tape_m = nullptr;
-    adj_t* lam[2] = {nullptr, nullptr};
-    adj_t* lgf = nullptr;
-    adj_t* lpsi = nullptr;
-    adj_t* uv = nullptr;
+    lam_t* lam[2] = {nullptr, nullptr};
+    aux_t* lgf = nullptr;
+    aux_t* lpsi = nullptr;
+    lam_t* uv = nullptr;
     double* parts = nullptr;
     double* parts2 = nullptr;
     double* cparts = nullptr;
@@ -924,7 +937,7 @@ int load_state(flbm_sim* h, const float* f, const DevState* st, const uint8_t* m
 }
 
 // One reverse step: tape slot kk is step n's input state, slot kk+1 step n+1's.
-int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, adj_t* L1, adj_t* L0, double inv2T, double dFp_dg)
+int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, double inv2T, double dFp_dg)
 {
     const KParams& k = h->kp;
     const size_t N = k.N, B3 = (size_t)k.B * k.B * k.B, mbytes = 2 * B3;
@@ -992,8 +1005,8 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
         return sim_fail(h, FLBM_E_NOMEM, "adjoint checkpoints and tape");
     cudaStream_t st = h->stream;
     ACK(h, cudaMemsetAsync(b.adj, 0, sizeof(AdjState), st));
-    ACK(h, cudaMemsetAsync(b.lam[0], 0, sizeof(adj_t) * 8 * N, st));
-    ACK(h, cudaMemsetAsync(b.lpsi, 0, sizeof(adj_t) * 2 * k.padn, st));
+    ACK(h, cudaMemsetAsync(b.lam[0], 0, sizeof(lam_t) * 8 * N, st));
+    ACK(h, cudaMemsetAsync(b.lpsi, 0, sizeof(aux_t) * 2 * k.padn, st));
     cudaEvent_t ev[3];
     for (auto& e : ev) ACK(h, cudaEventCreate(&e));
     struct EvGuard {

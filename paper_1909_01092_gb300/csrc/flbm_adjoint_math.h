@@ -105,4 +105,48 @@ FLBM_HD void adj_modes(const T rho[2], const T j[2][3], const T g[2][3], const T
     }
 }
 
+// adj_modes for an adjoint whose only nonzero modes are m*_0 = a_l and
+// m*_{1..3} = b_l (the part of lambda f_li = a_l + c_i . b_l that is the same
+// at every neighbour): the same outputs, with far fewer operations.
+template <class T>
+FLBM_HD void adj_modes_ab(const T rho[2], const T j[2][3], const T g[2][3], const T ext[3], T G, const T a[2],
+                          const T b[2][3], T lrho[2], T lj[2][3], T lg[2][3], T& lG)
+{
+    const T rt = rho[0] + rho[1];
+    T F[2][3], u[3];
+    for (int l = 0; l < 2; ++l)
+        for (int c = 0; c < 3; ++c) F[l][c] = -G * rho[l] * g[l][c] + rho[l] / rt * ext[c];
+    for (int c = 0; c < 3; ++c) u[c] = (j[0][c] + j[1][c] + T(0.5) * (F[0][c] + F[1][c])) / rt;
+    T lu[3] = {T(0), T(0), T(0)};
+    T lF[2][3];
+    for (int l = 0; l < 2; ++l) {
+        lrho[l] = a[l] + b[l][0] * u[0] + b[l][1] * u[1] + b[l][2] * u[2];
+        for (int c = 0; c < 3; ++c) {
+            lF[l][c] = T(0.5) * b[l][c];
+            lu[c] += rho[l] * b[l][c];
+        }
+    }
+    const T ul = lu[0] * u[0] + lu[1] * u[1] + lu[2] * u[2];
+    for (int l = 0; l < 2; ++l) {
+        lrho[l] -= ul / rt;
+        for (int c = 0; c < 3; ++c) {
+            lj[l][c] = lu[c] / rt;
+            lF[l][c] += T(0.5) * lu[c] / rt;
+        }
+    }
+    T eF[2];
+    for (int l = 0; l < 2; ++l) eF[l] = lF[l][0] * ext[0] + lF[l][1] * ext[1] + lF[l][2] * ext[2];
+    const T es = (rho[0] * eF[0] + rho[1] * eF[1]) / (rt * rt);
+    lG = T(0);
+    for (int l = 0; l < 2; ++l) {
+        T gl = T(0);
+        for (int c = 0; c < 3; ++c) {
+            gl += g[l][c] * lF[l][c];
+            lg[l][c] = -G * rho[l] * lF[l][c];
+        }
+        lrho[l] += -G * gl + eF[l] / rt - es;
+        lG += -rho[l] * gl;
+    }
+}
+
 }  // namespace flbm

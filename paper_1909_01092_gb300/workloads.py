@@ -129,5 +129,23 @@ def random_populations(p: dict, seed: int, amp: float = 0.05, vel: float = 0.02)
     return out
 
 
+def layered_populations(p: dict, rho_major: float = 2.21, rho_minor: float = 0.09, axis: int = 2,
+                        lo: int | None = None, hi: int | None = None) -> np.ndarray:
+    """Two-phase initial state, shape (2, 19, lz, ly, lx), float64: nodes with
+    lo <= coordinate < hi along `axis` hold rho_A = rho_major, rho_B =
+    rho_minor, the rest the opposite, each at rest (w_i rho_l). Defaults: the
+    middle half of the axis. The densities default to the bulk values the
+    paper prints for G = 1.5."""
+    L = (p["lx"], p["ly"], p["lz"])[axis]
+    lo = L // 4 if lo is None else lo
+    hi = 3 * L // 4 if hi is None else hi
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    coord = np.indices((p["lz"], p["ly"], p["lx"]))[2 - axis]
+    inside = (coord >= lo) & (coord < hi)
+    rA = np.where(inside, rho_major, rho_minor)
+    rB = np.where(inside, rho_minor, rho_major)
+    return np.stack([w[:, None, None, None] * rA[None], w[:, None, None, None] * rB[None]])
+
+
 def copy_params(p: dict) -> dict:
     return copy.deepcopy(p)

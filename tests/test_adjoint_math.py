@@ -38,6 +38,19 @@ extern "C" void adj(const double* in, double G, const double* lmf, double* out) 
     for (int l = 0; l < 2; ++l) for (int a = 0; a < 3; ++a) { out[2 + 3 * l + a] = lj[l][a]; out[8 + 3 * l + a] = lg[l][a]; }
     out[14] = lG;
 }
+extern "C" void adj_ab(const double* in, double G, const double* ab, double* out) {
+    const double rho[2] = {in[0], in[1]};
+    const double j[2][3] = {{in[2], in[3], in[4]}, {in[5], in[6], in[7]}};
+    const double g[2][3] = {{in[8], in[9], in[10]}, {in[11], in[12], in[13]}};
+    const double ext[3] = {in[14], in[15], in[16]};
+    const double a[2] = {ab[0], ab[1]};
+    const double b[2][3] = {{ab[2], ab[3], ab[4]}, {ab[5], ab[6], ab[7]}};
+    double lrho[2], lj[2][3], lg[2][3], lG;
+    flbm::adj_modes_ab<double>(rho, j, g, ext, G, a, b, lrho, lj, lg, lG);
+    out[0] = lrho[0]; out[1] = lrho[1];
+    for (int l = 0; l < 2; ++l) for (int c = 0; c < 3; ++c) { out[2 + 3 * l + c] = lj[l][c]; out[8 + 3 * l + c] = lg[l][c]; }
+    out[14] = lG;
+}
 """
 
 
@@ -54,6 +67,7 @@ def shim(tmp_path_factory):
     dp = ctypes.POINTER(ctypes.c_double)
     L.fwd.argtypes = [dp, ctypes.c_double, dp]
     L.adj.argtypes = [dp, ctypes.c_double, dp, dp]
+    L.adj_ab.argtypes = [dp, ctypes.c_double, dp, dp]
     return L
 
 
@@ -95,3 +109,19 @@ def test_modes_at_rest_are_the_equilibrium(shim):
     ms = _fwd(shim, x, 1.2)
     assert ms[0] == 1.0 and ms[10] == 0.05
     assert np.all(ms[1:10] == 0.0) and np.all(ms[11:20] == 0.0)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_density_momentum_part_equals_the_general_transpose(shim, seed):
+    """adj_modes_ab(a, b) = adj_modes with m*_0 = a, m*_1..3 = b, other modes 0."""
+    rng = np.random.default_rng(100 + seed)
+    x = np.concatenate([[1.0, 0.05], 0.05 * rng.standard_normal(6), 0.1 * rng.standard_normal(6),
+                        1e-3 * rng.standard_normal(3)])
+    ab = rng.standard_normal(8)
+    lm = np.zeros(20)
+    lm[0], lm[10] = ab[0], ab[1]
+    lm[1:4], lm[11:14] = ab[2:5], ab[5:8]
+    o1, o2 = np.zeros(15), np.zeros(15)
+    shim.adj(_p(x), 1.3, _p(lm), _p(o1))
+    shim.adj_ab(_p(x), 1.3, _p(ab), _p(o2))
+    assert np.allclose(o1, o2, rtol=1e-13, atol=1e-15)

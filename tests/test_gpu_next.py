@@ -1,0 +1,68 @@
+"""Configurations beyond the benchmarked ones, each against the FP64 oracle:
+a phase-separated mixture at the paper's G = 1.5 with the particle sitting on
+the A/B interface, and the closed channel (walls on all three axes) of the
+paper's production runs (Section 3)."""
+import numpy as np
+import pytest
+
+from paper_1909_01092_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL_F = 1e-5
+
+
+@pytest.fixture(scope="module")
+def flbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_01092_gb300 import binding
+
+    binding.load(build_if_missing=True)
+    return binding
+
+
+def _run(flbm, oracle_mod, p, f0, X, V, steps):
+    sim = flbm.Sim(p)
+    orc = oracle_mod.Oracle(p)
+    f32 = f0.astype(np.float32)
+    sim.write_f(f32)
+    orc.set_f(f32.astype(np.float64))
+    sim.set_particle(X, V)
+    orc.set_particle(X, V)
+    sim.step(steps)
+    orc.step(steps)
+    fluid = ~orc.fields()["solid"]
+    g, o = sim.read_f()[:, :, fluid].astype(np.float64), orc.get_f()[:, :, fluid]
+    err = float(np.max(np.abs(g - o) / np.mean(np.abs(o), axis=2, keepdims=True)))
+    return sim, orc, err
+
+
+@pytest.mark.parametrize("kT,drho", [(0.0, 0.3), (1e-5, -0.3)])
+def test_particle_on_the_interface_of_a_separated_mixture(flbm, oracle_mod, kT, drho):
+    p = W.channel_small(G=1.5, rho_a0=2.21, rho_b0=0.09, kT=kT, delta_rho=drho, g=1e-4, radius=3.0)
+    f0 = W.layered_populations(p)  # A-rich slab 8 <= z < 24, interfaces at z = 8 and 24
+    X = (p["pos0"][0], p["pos0"][1], 8.0)
+    sim, orc, err = _run(flbm, oracle_mod, p, f0, X, (0.0, 0.0, 0.0), 60)
+    assert err < RTOL_F, f"max rel err {err:.3e}"
+    pg, po = sim.particle(), orc.particle()
+    scale = max(np.max(np.abs(po["V"])), 1e-9)
+    assert np.max(np.abs(pg["V"] - po["V"])) <= 1e-4 * scale
+    assert pg["nfluid"] == po["nfluid"]
+    # the slab stays separated: A-rich in the middle, B-rich outside
+    rho = orc.fields()["rho"]
+    assert rho[0, 16].mean() > 1.5 and rho[0, 0].mean() < 0.5
+
+
+def test_closed_channel(flbm, oracle_mod):
+    """Walls on x, y and z, a moving particle, noise."""
+    p = W.params(lx=12, ly=12, lz=24, wall=(1, 1, 1), radius=3.0, rho_p_ratio=1.5, g=1e-4, kT=1e-5,
+                 fluid_counterforce=1)
+    f0 = W.random_populations(p, 11)
+    X = (5.5, 5.5, 11.5)
+    sim, orc, err = _run(flbm, oracle_mod, p, f0, X, (0.002, -0.001, 0.01), 80)
+    assert err < RTOL_F, f"max rel err {err:.3e}"
+    pg, po = sim.particle(), orc.particle()
+    assert np.max(np.abs(pg["V"] - po["V"])) <= 1e-4 * np.max(np.abs(po["V"]))
+    assert pg["nfluid"] == po["nfluid"]
