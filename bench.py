@@ -234,7 +234,7 @@ def ensemble_bench(binding, W, steps: int = 100) -> dict:
     return {"workload": "ensemble_128_replicas_L16-48_R2.5-6_kT1e-6-1e-4", "replicas": len(plist), "nodes": nodes,
             "steps": steps, "ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6, "gpu_launches": launches,
             "config": cfg, "one_at_a_time": {"ms_per_step": ms1, "mlups": nodes / (ms1 * 1e-3) / 1e6,
-                                             "launches_per_step": 9 * len(plist)},
+                                             "launches_per_step": 6 * len(plist)},
             "speedup": ms1 / ms}
 
 

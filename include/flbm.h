@@ -159,14 +159,15 @@ int flbm_set_particle(flbm_t* h, const double X[3], const double V[3], const dou
  * (may be NULL). Synchronises before returning. */
 int flbm_run_host(flbm_t* h, const float* host_f_in, int64_t nsteps, float* host_f_out, flbm_particle* traj);
 
-/* Kernel classes of one step, in launch order (k_virtual runs only with a particle). */
+/* Kernel classes of one step, in launch order. */
 enum {
     FLBM_K_DENSITY = 0,  /* densities of fluid nodes (Eq. (density)) */
-    FLBM_K_VIRTUAL = 1,  /* virtual wetting layer on particle surface nodes */
-    FLBM_K_SHELL = 2,    /* periodic copies and neutral wall ghosts of the density field */
-    FLBM_K_COLLIDE = 3,  /* force, MRT collision, noise, streaming, bounce-back, exchange */
-    FLBM_K_PARTICLE = 4, /* leap-frog update, cover/uncover, mass correction */
-    FLBM_NKERNELS = 5
+    FLBM_K_SHELL = 1,    /* periodic copies and neutral wall ghosts of the density field, and the
+                            virtual wetting layer on particle surface nodes (one launch) */
+    FLBM_K_COLLIDE = 2,  /* force, MRT collision, noise, streaming, bounce-back, exchange; with a
+                            particle also its leap-frog update (last block of the near-particle launch) */
+    FLBM_K_PARTICLE = 3, /* next-position particle nodes, cover/uncover, mass correction, step count */
+    FLBM_NKERNELS = 4
 };
 
 /* Same as flbm_step, and measures the device time of each kernel class with

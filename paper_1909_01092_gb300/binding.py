@@ -29,7 +29,7 @@ EXPORTS = (
     "flbm_ensemble_particles", "flbm_ensemble_read_fields", "flbm_ensemble_observables", "flbm_ensemble_nodes",
     "flbm_ensemble_last_launch_count", "flbm_ensemble_last_error", "flbm_ensemble_destroy",
 )
-NKERNELS = 5
+NKERNELS = 4
 
 
 class AdjResult(ctypes.Structure):

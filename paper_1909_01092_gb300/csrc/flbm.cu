@@ -59,8 +59,8 @@ void record(flbm_sim* h, cudaEvent_t* ev, int k)
     if (ev) cudaEventRecord(ev[k], h->stream);
 }
 
-// Densities, virtual layer and psi shell for the current state. With ev,
-// events ev[0..3] bracket the three kernels.
+// Densities, then the psi shell and the virtual layer (one launch), for the
+// current state. With ev, events ev[0..2] bracket the two kernels.
 int launch_psi(flbm_sim* h, const float* f, cudaEvent_t* ev = nullptr)
 {
     const KParams& k = h->kp;
@@ -68,21 +68,15 @@ int launch_psi(flbm_sim* h, const float* f, cudaEvent_t* ev = nullptr)
     k_density<<<h->grid, h->block, 0, h->stream>>>(f, h->psi, h->st, h->masks, k);
     if (int rc = launch_check(h, "k_density")) return rc;
     record(h, ev, 1);
-    if (k.has_particle) {
-        const int nb = (k.B * k.B * k.B + kThreads - 1) / kThreads;
-        k_virtual<<<nb, kThreads, 0, h->stream>>>(h->psi, h->st, h->masks, k);
-        if (int rc = launch_check(h, "k_virtual")) return rc;
-    }
+    const int nbs = (int)((shell_count(k) + kThreads - 1) / kThreads);
+    const int nbv = k.has_particle ? (k.B * k.B * k.B + kThreads - 1) / kThreads : 0;
+    k_shell_virtual<<<nbs + nbv, kThreads, 0, h->stream>>>(h->psi, h->st, h->masks, k, nbs);
+    if (int rc = launch_check(h, "k_shell_virtual")) return rc;
     record(h, ev, 2);
-    const long long nshell = 2LL * k.px * k.py + 2LL * k.px * k.lz + 2LL * k.ly * k.lz;
-    const long long nb = (nshell + kThreads - 1) / kThreads;
-    k_shell<<<(unsigned)nb, kThreads, 0, h->stream>>>(h->psi, h->st, h->masks, k);
-    if (int rc = launch_check(h, "k_shell")) return rc;
-    record(h, ev, 3);
     return FLBM_OK;
 }
 
-// One time step. With ev, events ev[0..5] bracket its five kernel classes.
+// One time step. With ev, events ev[0..4] bracket its four kernel classes.
 int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
 {
     const KParams& k = h->kp;
@@ -107,18 +101,18 @@ int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
     else if (k.tau1) FLBM_COLLIDE(false, true);
     else FLBM_COLLIDE(false, false);
 #undef FLBM_COLLIDE
-    record(h, ev, 4);
+    record(h, ev, 3);
     if (part) {
-        k_update<<<1, 256, 0, h->stream>>>(h->st, h->partials, k);
-        if (int rc = launch_check(h, "k_update")) return rc;
+        // The particle update ran in the near kernel's last block.
         k_mark_next<<<h->box_blocks, 256, 0, h->stream>>>(h->st, h->masks, h->box_counts, k);
         if (int rc = launch_check(h, "k_mark_next")) return rc;
-        k_cover<<<h->box_blocks, 256, 0, h->stream>>>(fout, h->st, h->masks, h->box_parts, k);
+        k_cover<<<h->box_blocks, 256, 0, h->stream>>>(fout, h->st, h->masks, h->box_parts, h->box_counts, k);
         if (int rc = launch_check(h, "k_cover")) return rc;
+    } else {
+        k_finish<<<1, 256, 0, h->stream>>>(h->st, h->box_counts, h->box_parts, h->box_blocks, k);
+        if (int rc = launch_check(h, "k_finish")) return rc;
     }
-    k_finish<<<1, 256, 0, h->stream>>>(h->st, h->box_counts, h->box_parts, h->box_blocks, k);
-    if (int rc = launch_check(h, "k_finish")) return rc;
-    record(h, ev, 5);
+    record(h, ev, 4);
     h->cur = 1 - h->cur;
     return FLBM_OK;
 }
@@ -483,7 +477,7 @@ int flbm_run_host(flbm_t* h, const float* host_f_in, int64_t nsteps, float* host
 int flbm_step_timed(flbm_t* h, int64_t nsteps, double* ms)
 {
     if (!h || nsteps < 0 || !ms) return fail(h, FLBM_E_INVAL, "invalid argument");
-    const size_t need = (size_t)6 * (size_t)nsteps;
+    const size_t need = (size_t)(FLBM_NKERNELS + 1) * (size_t)nsteps;
     while (h->events.size() < need) {
         cudaEvent_t e;
         CK(h, cudaEventCreate(&e));
@@ -491,11 +485,11 @@ int flbm_step_timed(flbm_t* h, int64_t nsteps, double* ms)
     }
     h->launches = 0;
     for (int64_t s = 0; s < nsteps; ++s)
-        if (int rc = launch_step(h, h->events.data() + 6 * s)) return rc;
+        if (int rc = launch_step(h, h->events.data() + (FLBM_NKERNELS + 1) * s)) return rc;
     CK(h, cudaStreamSynchronize(h->stream));
     for (int k = 0; k < FLBM_NKERNELS; ++k) ms[k] = 0.0;
     for (int64_t s = 0; s < nsteps; ++s) {
-        cudaEvent_t* ev = h->events.data() + 6 * s;
+        cudaEvent_t* ev = h->events.data() + (FLBM_NKERNELS + 1) * s;
         for (int k = 0; k < FLBM_NKERNELS; ++k) {
             float t = 0.0f;
             CK(h, cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
@@ -507,7 +501,7 @@ int flbm_step_timed(flbm_t* h, int64_t nsteps, double* ms)
 
 const char* flbm_kernel_name(int k)
 {
-    static const char* names[FLBM_NKERNELS] = {"k_density", "k_virtual", "k_shell", "k_collide", "k_particle"};
+    static const char* names[FLBM_NKERNELS] = {"k_density", "k_shell_virtual", "k_collide", "k_particle"};
     return (k >= 0 && k < FLBM_NKERNELS) ? names[k] : "";
 }
 

@@ -202,6 +202,8 @@ struct DevState {
     int box0[3];           // origin of the particle box (periodic axes in [0, L))
     int box_next[3];       // origin at the position after this step's update
     int err;
+    unsigned near_done;    // blocks of the near-collide launch done this step (last one updates)
+    unsigned cover_done;   // blocks of the cover launch done this step (last one finishes)
 };
 
 constexpr int kThreadsStep = 256;
@@ -296,6 +298,28 @@ __device__ __forceinline__ void block_sum8(double v[8], double* s_red, double* s
         s_out[tid] = a;
     }
     __syncthreads();
+}
+
+// True in the block that is the last of `total` blocks to pass this point
+// (counted in *counter, which that block resets to 0). Every thread of the
+// block must call it; before it, each block's global writes are made visible
+// device-wide, so the last block may read what all the others wrote (with
+// loads that bypass L1). There is no waiting: the other blocks just finish.
+__device__ __forceinline__ bool last_block(unsigned* counter, unsigned total)
+{
+    __shared__ int s_last;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned t = atomicAdd(counter, 1u);
+        s_last = (t + 1u == total) ? 1 : 0;
+        if (s_last) *counter = 0u;
+    }
+    __syncthreads();
+    const bool last = s_last != 0;
+    if (last) __threadfence();
+    return last;
 }
 
 }  // namespace flbm

@@ -8,10 +8,11 @@
 // stages the descriptor of its current replica (kernel parameters and device
 // pointers) in shared memory and runs the same device bodies as the
 // single-simulation kernels, so each replica computes exactly what
-// flbm_create/flbm_step would. The step sequence (densities, virtual layer,
-// density shell, collide-stream of bulk and near tiles, particle update,
-// next-position masks, cover/uncover, bookkeeping) is captured into a CUDA
-// graph of two steps when the stream allows capture.
+// flbm_create/flbm_step would. The step sequence (densities; density shell
+// with the virtual layer; collide-stream of bulk and near tiles, the near
+// launch ending with each replica's particle update; next-position masks;
+// cover/uncover ending with each replica's bookkeeping) is captured into a
+// CUDA graph of two steps when the stream allows capture.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -91,24 +92,19 @@ static __global__ void __launch_bounds__(256) kb_density(const RepDesc* __restri
     FLBM_END_ITEMS
 }
 
-static __global__ void __launch_bounds__(256) kb_virtual(const RepDesc* __restrict__ reps,
-                                                         const int2* __restrict__ items, int nitems)
-{
-    FLBM_FOR_ITEMS
-    virtual_node(it.y * 256 + threadIdx.x, sR.psi, sR.st, sR.masks, P);
-    FLBM_END_ITEMS
-}
-
+// Shell blocks of the replica first, then the blocks of its particle box.
 static __global__ void __launch_bounds__(256) kb_shell(const RepDesc* __restrict__ reps,
                                                        const int2* __restrict__ items, int nitems)
 {
     FLBM_FOR_ITEMS
-    shell_node(it.y * 256LL + threadIdx.x, sR.psi, sR.st, sR.masks, P);
+    const int nbs = (int)((shell_count(P) + 255) / 256);
+    if (it.y < nbs)
+        shell_node(it.y * 256LL + threadIdx.x, sR.psi, sR.st, sR.masks, P);
+    else
+        virtual_node((it.y - nbs) * 256 + threadIdx.x, sR.psi, sR.st, sR.masks, P);
     FLBM_END_ITEMS
 }
 
-// Reading the parameters from shared memory costs registers: three blocks
-// per SM keep the bulk kernel free of spills, two the near kernel.
 template <bool NOISE, bool TAU1>
 static __global__ void __launch_bounds__(256, 3)
     kb_bulk(const RepDesc* __restrict__ reps, const int2* __restrict__ items, int nitems, int par)
@@ -132,15 +128,6 @@ static __global__ void __launch_bounds__(256, 2)
     FLBM_END_ITEMS
 }
 
-static __global__ void __launch_bounds__(256) kb_update(const RepDesc* __restrict__ reps,
-                                                        const int2* __restrict__ items, int nitems)
-{
-    FLBM_FOR_ITEMS
-    update_particle(sR.st, sR.partials, P);
-    __syncthreads();
-    FLBM_END_ITEMS
-}
-
 static __global__ void __launch_bounds__(256) kb_mark_next(const RepDesc* __restrict__ reps,
                                                            const int2* __restrict__ items, int nitems)
 {
@@ -153,7 +140,7 @@ static __global__ void __launch_bounds__(256) kb_cover(const RepDesc* __restrict
                                                        const int2* __restrict__ items, int nitems, int par)
 {
     FLBM_FOR_ITEMS
-    cover_block(it.y, sR.f[1 - par], sR.st, sR.masks, sR.box_parts, P);
+    cover_then_finish(it.y, sR.f[1 - par], sR.st, sR.masks, sR.box_parts, sR.box_counts, P);
     FLBM_END_ITEMS
 }
 
@@ -173,12 +160,10 @@ static __global__ void __launch_bounds__(256) kb_finish(const RepDesc* __restric
 // kernel variant (noise on/off x all relaxation times 1 or not).
 enum WorkKind {
     W_DENSITY = 0,
-    W_VIRTUAL,
-    W_SHELL,
+    W_SHELL,           // shell and virtual layer
     W_BULK,            // + variant (4 lists)
     W_NEAR = W_BULK + 4,  // + variant (4 lists)
-    W_UPDATE = W_NEAR + 4,
-    W_MARK,
+    W_MARK = W_NEAR + 4,
     W_COVER,
     W_FINISH,
     W_COUNT
@@ -242,13 +227,11 @@ long long blocks_of(const KParams& k, int w)
 {
     const bool part = k.has_particle != 0;
     if (w == W_DENSITY) return tile_count(k);
-    if (w == W_VIRTUAL) return part ? box_block_count(k) : 0;
-    if (w == W_SHELL) return (shell_count(k) + 255) / 256;
+    if (w == W_SHELL) return (shell_count(k) + 255) / 256 + (part ? box_block_count(k) : 0);
     if (w >= W_BULK && w < W_BULK + 4) return variant(k) == w - W_BULK ? tile_count(k) : 0;
     if (w >= W_NEAR && w < W_NEAR + 4) return (part && variant(k) == w - W_NEAR) ? cand_count(k) : 0;
-    if (w == W_UPDATE) return part ? 1 : 0;
     if (w == W_MARK || w == W_COVER) return part ? box_block_count(k) : 0;
-    return 1;  // W_FINISH
+    return part ? 0 : 1;  // W_FINISH: with a particle the cover launch finishes the step
 }
 
 void destroy_graphs(flbm_ens* e)
@@ -404,7 +387,6 @@ int ens_step(flbm_ens* e)
 {
     const int par = e->cur;
     if (int rc = launch_list(e, W_DENSITY, kb_density, "kb_density", par)) return rc;
-    if (int rc = launch_list(e, W_VIRTUAL, kb_virtual, "kb_virtual")) return rc;
     if (int rc = launch_list(e, W_SHELL, kb_shell, "kb_shell")) return rc;
     if (int rc = launch_list(e, W_BULK + 0, kb_bulk<false, false>, "kb_bulk", par)) return rc;
     if (int rc = launch_list(e, W_BULK + 1, kb_bulk<false, true>, "kb_bulk", par)) return rc;
@@ -414,7 +396,6 @@ int ens_step(flbm_ens* e)
     if (int rc = launch_list(e, W_NEAR + 1, kb_near<false, true>, "kb_near", par)) return rc;
     if (int rc = launch_list(e, W_NEAR + 2, kb_near<true, false>, "kb_near", par)) return rc;
     if (int rc = launch_list(e, W_NEAR + 3, kb_near<true, true>, "kb_near", par)) return rc;
-    if (int rc = launch_list(e, W_UPDATE, kb_update, "kb_update")) return rc;
     if (int rc = launch_list(e, W_MARK, kb_mark_next, "kb_mark_next")) return rc;
     if (int rc = launch_list(e, W_COVER, kb_cover, "kb_cover", par)) return rc;
     if (int rc = launch_list(e, W_FINISH, kb_finish, "kb_finish")) return rc;

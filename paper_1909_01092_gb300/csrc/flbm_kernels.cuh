@@ -1,15 +1,18 @@
 // Kernels of one FLBM time step (arXiv:1909.01092, Section 2 and Section 3).
 //
 // Per step, on one stream:
-//   k_density  : rho_l = sum_i f_li on fluid nodes (Eq. (density)) -> psi interior
-//   k_virtual  : virtual fluid layer on particle surface nodes (Section 2)
-//   k_shell    : psi shell: periodic copies and neutral wall ghosts (Section 3)
-//   k_collide  : Shan-Chen force (Eq. (sc-force)), MRT collision with source and
-//                thermal noise, push-streaming with halfway wall bounce-back and
-//                the moving link rule at the particle, momentum exchange and
-//                Shan-Chen reaction reduced per tile (Eq. (lbe))
-//   k_particle : sum of tile partials, leap-frog Newton-Euler update,
-//                cover/uncover, mass-correction ledger (Section 2)
+//   k_density       : rho_l = sum_i f_li on fluid nodes (Eq. (density)) -> psi interior
+//   k_shell_virtual : psi shell (periodic copies, neutral wall ghosts, Section 3)
+//                     and the virtual fluid layer on particle surface nodes (Section 2)
+//   k_collide_bulk / k_collide_near (flbm_step.cuh): Shan-Chen force (Eq. (sc-force)),
+//                     MRT collision with source and thermal noise, push-streaming
+//                     with halfway wall bounce-back and the moving link rule at
+//                     the particle, momentum exchange and Shan-Chen reaction
+//                     reduced per tile (Eq. (lbe)); the near launch's last block
+//                     advances the particle (leap-frog)
+//   k_mark_next, k_cover : particle nodes at the new position, cover/uncover,
+//                     mass-correction ledger; the cover launch's last block
+//                     finishes the step (k_finish without a particle)
 #pragma once
 
 #include "flbm_device.cuh"
@@ -79,22 +82,12 @@ static __global__ void __launch_bounds__(kThreads) k_density(const float* __rest
 // the mean density of those neighbours, +delta_rho for A and -delta_rho for
 // B, clipped at 0. One thread per node of the particle box.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void virtual_node(int t, float* __restrict__ psi, const DevState* __restrict__ st,
-                                             const uint8_t* __restrict__ masks, const KParams& P)
+// Virtual-layer densities of particle node c (lattice coordinates, in range).
+__device__ __forceinline__ void virtual_value(const int c[3], const float* __restrict__ psi, const int o[3],
+                                              const uint8_t* __restrict__ mask, const KParams& P, float& va,
+                                              float& vb)
 {
-    const int B = P.B;
-    if (t >= B * B * B) return;
-    const uint8_t* mask = masks + (size_t)st->cur * B * B * B;
-    if (!mask[t]) return;
-    const int o[3] = {st->box0[0], st->box0[1], st->box0[2]};
-    const int d[3] = {t % B, (t / B) % B, t / (B * B)};
     const int L[3] = {P.lx, P.ly, P.lz};
-    int c[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        c[a] = o[a] + d[a];
-        if (!P.wall[a] && c[a] >= L[a]) c[a] -= L[a];
-    }
     float sa = 0.0f, sb = 0.0f;
     int cnt = 0;
 #pragma unroll
@@ -114,12 +107,33 @@ __device__ __forceinline__ void virtual_node(int t, float* __restrict__ psi, con
         sb += psi[P.padn + pi];
         ++cnt;
     }
-    float va = 0.0f, vb = 0.0f;
+    va = 0.0f;
+    vb = 0.0f;
     if (cnt) {
         const float inv = 1.0f / (float)cnt;
         va = fmaxf(sa * inv + P.drho, 0.0f);
         vb = fmaxf(sb * inv - P.drho, 0.0f);
     }
+}
+
+__device__ __forceinline__ void virtual_node(int t, float* __restrict__ psi, const DevState* __restrict__ st,
+                                             const uint8_t* __restrict__ masks, const KParams& P)
+{
+    const int B = P.B;
+    if (t >= B * B * B) return;
+    const uint8_t* mask = masks + (size_t)st->cur * B * B * B;
+    if (!mask[t]) return;
+    const int o[3] = {st->box0[0], st->box0[1], st->box0[2]};
+    const int d[3] = {t % B, (t / B) % B, t / (B * B)};
+    const int L[3] = {P.lx, P.ly, P.lz};
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        c[a] = o[a] + d[a];
+        if (!P.wall[a] && c[a] >= L[a]) c[a] -= L[a];
+    }
+    float va, vb;
+    virtual_value(c, psi, o, mask, P, va, vb);
     const long long q = pad_index(c[0], c[1], c[2], P);
     psi[q] = va;
     psi[P.padn + q] = vb;
@@ -182,14 +196,24 @@ __device__ __forceinline__ void shell_node(long long t, float* __restrict__ psi,
         }
     }
     const long long dst = (long long)(p[0] + 1) + (long long)P.px * ((p[1] + 1) + (long long)P.py * (p[2] + 1));
+    const int o[3] = {st->box0[0], st->box0[1], st->box0[2]};
+    const uint8_t* mask = masks + (size_t)st->cur * P.B * P.B * P.B;
     if (!ghost) {
+        // Periodic copy. A particle node's value is its virtual-layer value,
+        // computed here as virtual_node does, so that this kernel need not
+        // wait for it.
+        if (P.has_particle && is_solid(q[0], q[1], q[2], o, mask, P)) {
+            float va, vb;
+            virtual_value(q, psi, o, mask, P, va, vb);
+            psi[dst] = va;
+            psi[P.padn + dst] = vb;
+            return;
+        }
         const long long src = pad_index(q[0], q[1], q[2], P);
         psi[dst] = psi[src];
         psi[P.padn + dst] = psi[P.padn + src];
         return;
     }
-    const int o[3] = {st->box0[0], st->box0[1], st->box0[2]};
-    const uint8_t* mask = masks + (size_t)st->cur * P.B * P.B * P.B;
     float sa = 0.0f, sb = 0.0f;
     int cnt = 0;
 #pragma unroll
@@ -219,6 +243,19 @@ static __global__ void __launch_bounds__(kThreads) k_shell(float* __restrict__ p
                                                            const uint8_t* __restrict__ masks, KParams P)
 {
     shell_node(blockIdx.x * (long long)blockDim.x + threadIdx.x, psi, st, masks, P);
+}
+
+// Shell and virtual layer in one launch: the first nshell_blocks blocks run
+// the shell, the rest the particle box (no thread reads what another writes).
+static __global__ void __launch_bounds__(kThreads) k_shell_virtual(float* __restrict__ psi,
+                                                                   const DevState* __restrict__ st,
+                                                                   const uint8_t* __restrict__ masks, KParams P,
+                                                                   int nshell_blocks)
+{
+    if ((int)blockIdx.x < nshell_blocks)
+        shell_node(blockIdx.x * (long long)blockDim.x + threadIdx.x, psi, st, masks, P);
+    else
+        virtual_node((blockIdx.x - nshell_blocks) * blockDim.x + threadIdx.x, psi, st, masks, P);
 }
 
 }  // namespace flbm

@@ -9,8 +9,11 @@
 //                 k_collide_near runs them over a fixed grid of candidates
 //                 around the box and reduces force, torque and mass ledger.
 // Both kernels apply the same tile_near() test, so every tile runs exactly once.
-// The particle update then runs as four small kernels (update, mark, cover,
-// finish) spread over the particle box instead of one serial block.
+// The particle update runs in the last block of the near launch (after every
+// candidate's partials are written); the next-position masks and the
+// cover/uncover pass run over the particle box, and the last block of the
+// cover launch does the step's bookkeeping. "Last block" is an atomic ticket
+// per launch: no block waits for another.
 #pragma once
 
 #include "flbm_device.cuh"
@@ -44,11 +47,13 @@ __device__ __forceinline__ void philox_rk(uint32_t& x0, uint32_t& x1, uint32_t& 
 __device__ __forceinline__ void box_muller(uint32_t w1, uint32_t w2, float& z0, float& z1)
 {
     const float u1 = uniform_open(w1);
-    const float u2 = uniform_open(w2);
     const float e = -1.38629436112f * __log2f(u1);  // -2 ln u1 > 0
     const float r = e * rsqrtf(e);
+    // 2 pi (u2 - 1/2) with u2 = ((w2 >> 9) + 1/2) 2^-23, as one multiply-add.
+    constexpr float kA = (float)(6.283185307179586 / 8388608.0);
+    constexpr float kB = (float)(6.283185307179586 * (0.5 / 8388608.0 - 0.5));
     float s, c;
-    __sincosf(6.28318530718f * (u2 - 0.5f), &s, &c);
+    __sincosf(__fmaf_rn((float)(w2 >> 9), kA, kB), &s, &c);
     z0 = -r * c;
     z1 = -r * s;
 }
@@ -344,7 +349,7 @@ __device__ __forceinline__ int candidate_tile(int c, int o, int T, int gt, int L
 // Candidate (cx, cy, cz) of the grid around the particle box; thread (tx, ty)
 // of the tile, tid = tx + TX ty. Every thread of the block must call this.
 template <bool NOISE, bool TAU1>
-__device__ __forceinline__ void near_tile(int cx, int cy, int cz, int tx, int ty, int tid,
+__device__ __forceinline__ void near_tile_work(int cx, int cy, int cz, int tx, int ty, int tid,
                                           const float* __restrict__ fin, float* __restrict__ fout,
                                           const float* __restrict__ psi, const DevState* __restrict__ st,
                                           const uint8_t* __restrict__ masks, double* __restrict__ partials,
@@ -398,10 +403,28 @@ __device__ __forceinline__ void near_tile(int cx, int cy, int cz, int tx, int ty
     __syncthreads();  // s_out is reused by the next tile of a persistent block
 }
 
+__device__ __forceinline__ void update_particle(DevState* __restrict__ st, const double* __restrict__ partials,
+                                                const KParams& P);
+
+// A near tile, then, in the block that finishes the launch's last candidate,
+// the particle update of this step (sum of all candidates' partials in fixed
+// order, leap-frog).
+template <bool NOISE, bool TAU1>
+__device__ __forceinline__ void near_tile(int cx, int cy, int cz, int tx, int ty, int tid,
+                                          const float* __restrict__ fin, float* __restrict__ fout,
+                                          const float* __restrict__ psi, DevState* __restrict__ st,
+                                          const uint8_t* __restrict__ masks, double* __restrict__ partials,
+                                          const KParams& P)
+{
+    near_tile_work<NOISE, TAU1>(cx, cy, cz, tx, ty, tid, fin, fout, psi, st, masks, partials, P);
+    if (last_block(&st->near_done, (unsigned)(P.ncx * P.ncy * P.ncz))) update_particle(st, partials, P);
+    __syncthreads();
+}
+
 template <bool NOISE, bool TAU1>
 static __global__ void __launch_bounds__(kThreadsStep, TAU1 ? 3 : 2)
     k_collide_near(const float* __restrict__ fin, float* __restrict__ fout, const float* __restrict__ psi,
-                   const DevState* __restrict__ st, const uint8_t* __restrict__ masks,
+                   DevState* __restrict__ st, const uint8_t* __restrict__ masks,
                    double* __restrict__ partials, KParams P)
 {
     near_tile<NOISE, TAU1>(blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y,
@@ -453,12 +476,14 @@ __device__ __forceinline__ void update_particle(DevState* __restrict__ st, const
     __shared__ double s_red[(256 / 32) * 8];
     __shared__ double s_out[8];
     const long long ncand = (long long)P.ncx * P.ncy * P.ncz;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nthr = blockDim.x * blockDim.y;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (long long c = threadIdx.x; c < ncand; c += blockDim.x)
+    for (long long c = tid; c < ncand; c += nthr)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] += partials[c * 8 + k];
+        for (int k = 0; k < 8; ++k) acc[k] += __ldcg(partials + c * 8 + k);
     block_sum8<256>(acc, s_red, s_out);
-    if (threadIdx.x != 0) return;
+    if (tid != 0) return;
     const int L[3] = {P.lx, P.ly, P.lz};
     for (int a = 0; a < 3; ++a) {
         st->F[a] = s_out[a] + st->Ppend[a];
@@ -628,11 +653,26 @@ __device__ __forceinline__ void cover_block(int blk, float* __restrict__ f, cons
     __syncthreads();
 }
 
-static __global__ void __launch_bounds__(256) k_cover(float* __restrict__ f, const DevState* __restrict__ st,
-                                                      const uint8_t* __restrict__ masks, double* __restrict__ parts,
-                                                      KParams P)
+__device__ __forceinline__ void finish_step(DevState* __restrict__ st, const int* __restrict__ counts,
+                                            const double* __restrict__ parts, int nblocks, const KParams& P);
+
+// A block of the cover/uncover pass, then, in the launch's last block, the
+// step's bookkeeping (finish_step).
+__device__ __forceinline__ void cover_then_finish(int blk, float* __restrict__ f, DevState* __restrict__ st,
+                                                  const uint8_t* __restrict__ masks, double* __restrict__ parts,
+                                                  const int* __restrict__ counts, const KParams& P)
 {
-    cover_block(blockIdx.x, f, st, masks, parts, P);
+    cover_block(blk, f, st, masks, parts, P);
+    const int nb = (P.B * P.B * P.B + 255) / 256;
+    if (last_block(&st->cover_done, (unsigned)nb)) finish_step(st, counts, parts, nb, P);
+    __syncthreads();
+}
+
+static __global__ void __launch_bounds__(256) k_cover(float* __restrict__ f, DevState* __restrict__ st,
+                                                      const uint8_t* __restrict__ masks, double* __restrict__ parts,
+                                                      const int* __restrict__ counts, KParams P)
+{
+    cover_then_finish(blockIdx.x, f, st, masks, parts, counts, P);
 }
 
 // (4) Bookkeeping for the next step: pending impulses, fluid count, mass
@@ -655,8 +695,8 @@ __device__ __forceinline__ void finish_step(DevState* __restrict__ st, const int
     long long cnt = 0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] += parts[b * 8 + k];
-        cnt += counts[b];
+        for (int k = 0; k < 8; ++k) acc[k] += __ldcg(parts + b * 8 + k);
+        cnt += __ldcg(counts + b);
     }
     s_c[threadIdx.x] = cnt;
     block_sum8<256>(acc, s_red, s_out);

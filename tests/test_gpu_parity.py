@@ -33,10 +33,12 @@ def flbm():
 
 
 def _launches_per_step(p):
-    """Kernels of one step: densities, (virtual layer,) density shell, the
-    collide-stream pass of the tiles away from the particle, (the
-    near-particle collide and three particle kernels,) the finish kernel."""
-    return 9 if p["radius"] > 0 else 4
+    """Kernels of one step: densities, density shell with the virtual layer,
+    the collide-stream pass of the tiles away from the particle, then either
+    the near-particle collide (ending with the particle update), the
+    next-position masks and cover/uncover (ending with the bookkeeping), or
+    the finish kernel."""
+    return 6 if p["radius"] > 0 else 4
 
 
 def _fluid_mask(orc):
