@@ -37,6 +37,15 @@ WORKLOAD = "channel_128x128x512_kT1e-5_R12"
 STEP_BYTES_PER_NODE = 2 * 19 * 4 * 2
 COLLIDE_BYTES_PER_NODE = STEP_BYTES_PER_NODE + 2 * 4
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes of the collide class (bulk + near launches) per step of the
+# 128x128x512 channel, from an ncu capture of the same kernels at 128x128x128
+# scaled by bulk nodes (profiles/k_collide_bulk_channel_128x128x128.md):
+# 290 B per bulk node x 8,331,264 bulk nodes + 9.9 MB for the near tiles.
+COLLIDE_TRAFFIC_BYTES = 290.1 * 8331264 + 9.9e6
+# Thread instructions per node of the noisy bulk collide kernel (same capture:
+# 119.3 M warp instructions over 2,039,808 nodes).
+COLLIDE_INST_PER_NODE = 119.3e6 * 32 / 2039808
+SMS, SCHEDULERS_PER_SM = 152, 4
 
 
 def parse():
@@ -140,6 +149,18 @@ def dist_init():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def alu_bound(nodes: int, coll_ms: float, ck: dict) -> dict:
+    """Secondary bound of the noisy collide: the issue rate. Instructions per
+    node from ncu, over the CUDA-event time of the collide class, against one
+    warp instruction per scheduler per clock at the median SM clock sampled
+    during the run (the maximum clock if none was sampled)."""
+    mhz = (ck or {}).get("sm_mhz") or (ck or {}).get("sm_max_mhz") or 2070.0
+    peak = SMS * SCHEDULERS_PER_SM * mhz * 1e6 / 1e9  # G warp instructions / s
+    achieved = COLLIDE_INST_PER_NODE / 32 * nodes / (coll_ms * 1e-3) / 1e9
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "G warp instr/s",
+            "frac": achieved / peak, "inst_per_node": COLLIDE_INST_PER_NODE, "sm_mhz": mhz}
 
 
 def rank_workload(W, rank: int, lz: int = 512) -> dict:
@@ -363,10 +384,12 @@ def run_ours(args):
     coll_ms = kms["k_collide"] / args.steps
     achieved = COLLIDE_BYTES_PER_NODE * nodes / (coll_ms * 1e-3) / 1e9
     step_gbs = STEP_BYTES_PER_NODE * nodes / (ms / args.steps * 1e-3) / 1e9
+    traffic = COLLIDE_TRAFFIC_BYTES / 1e9 if args.lz == 512 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_collide", "peak_source": f"{src} hbm_gbs (copy)",
+                "traffic": traffic, "traffic_unit": "GB per step (ncu DRAM read + write, scaled)", "kernel": "k_collide", "peak_source": f"{src} hbm_gbs (copy)",
                 "bytes_per_node": COLLIDE_BYTES_PER_NODE,
                 "step": {"achieved": step_gbs, "frac": step_gbs / peak, "bytes_per_node": STEP_BYTES_PER_NODE},
+                "alu": alu_bound(nodes, coll_ms, ck),
                 "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()}}
 
     cpu = None
