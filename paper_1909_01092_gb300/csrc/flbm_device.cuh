@@ -302,14 +302,16 @@ __device__ __forceinline__ void block_sum8(double v[8], double* s_red, double* s
 
 // True in the block that is the last of `total` blocks to pass this point
 // (counted in *counter, which that block resets to 0). Every thread of the
-// block must call it; before it, each block's global writes are made visible
-// device-wide, so the last block may read what all the others wrote (with
-// loads that bypass L1). There is no waiting: the other blocks just finish.
-__device__ __forceinline__ bool last_block(unsigned* counter, unsigned total)
+// block must call it. Threads that wrote what the last block will read pass
+// wrote = true: their writes are made visible device-wide before the block
+// takes its ticket, so the last block may read what all the others wrote
+// (with loads that bypass L1). There is no waiting: the other blocks just
+// finish.
+__device__ __forceinline__ bool last_block(unsigned* counter, unsigned total, bool wrote)
 {
     __shared__ int s_last;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    __threadfence();
+    if (wrote) __threadfence();
     __syncthreads();
     if (tid == 0) {
         const unsigned t = atomicAdd(counter, 1u);

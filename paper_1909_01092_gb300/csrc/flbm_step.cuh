@@ -201,6 +201,36 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, co
 #pragma unroll
         for (int k = 0; k < 19; ++k) m[k] *= 1.0f / bnorm(k);
     };
+    relax(ma, rhoA, FA, st->delta_f[0]);
+    relax(mb, rhoB, FB, st->delta_f[1]);
+
+    if (NOISE) {
+        // 33 normals from 9 Philox blocks with counter (step, node, block, 0):
+        // A modes 4..18, B modes 4..18, interdiffusion J_x, J_y, J_z.
+        const float sA = sqrtf(3.0f * P.kT * fmaxf(rhoA, 0.0f));
+        const float sB = sqrtf(3.0f * P.kT * fmaxf(rhoB, 0.0f));
+        const float sJ = 3.0f * P.nz_j * sqrtf(P.kT * fmaxf(rhoA, 0.0f) * fmaxf(rhoB, 0.0f) * fmaxf(irt, 0.0f));
+        const uint32_t stp = st->step_u32;
+#pragma unroll
+        for (int blk = 0; blk < 9; ++blk) {
+            uint32_t r0 = stp, r1 = n, r2 = (uint32_t)blk, r3 = 0u;
+            philox_rk(r0, r1, r2, r3, P);
+            float zn[4];
+            box_muller(r0, r1, zn[0], zn[1]);
+            box_muller(r2, r3, zn[2], zn[3]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int idx = 4 * blk + q;
+                if (idx < 15) ma[4 + idx] += sA * P.nz_mode[4 + idx] * zn[q];
+                else if (idx < 30) mb[4 + idx - 15] += sB * P.nz_mode[4 + idx - 15] * zn[q];
+                else if (idx < 33) {
+                    ma[1 + idx - 30] += sJ * zn[q];
+                    mb[1 + idx - 30] -= sJ * zn[q];
+                }
+            }
+        }
+    }
+
     // Destination offsets along each axis (periodic wrap), and wall flags.
     const int L[3] = {P.lx, P.ly, P.lz};
     const int crd[3] = {x, y, z};
@@ -221,11 +251,13 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, co
         }
     }
 
-    // Back-transform and push component l (Eq. (lbe) streaming; halfway
+    // Back-transform and push each component (Eq. (lbe) streaming; halfway
     // bounce-back at walls; moving link rule at the particle).
-    auto store = [&](int l, const float* m, float rl) {
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
         float fo[19];
-        from_modes(m, fo);
+        from_modes(l == 0 ? ma : mb, fo);
+        const float rl = l == 0 ? rhoA : rhoB;
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             const int cx = cxv(i), cy = cyv(i), cz = czv(i);
@@ -255,73 +287,6 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, co
             const uint32_t push_idx = n + (uint32_t)off + P.dirN[19 * l + i];
             fout[wall ? back_idx : push_idx] = fo[i];
         }
-    };
-
-    if (!NOISE) {
-        relax(ma, rhoA, FA, st->delta_f[0]);
-        store(0, ma, rhoA);
-        relax(mb, rhoB, FB, st->delta_f[1]);
-        store(1, mb, rhoB);
-    } else {
-        // 33 normals from 9 Philox blocks with counter (step, node, block, 0), in
-        // the order A modes 4..18 (normals 0..14), B modes 4..18 (15..29),
-        // interdiffusion J_x, J_y, J_z (30..32). Component A is relaxed, given
-        // its noise and stored before B's modes exist (fewer live registers):
-        // blocks 7 and 8 first (B modes 17, 18 and J), then 0..3 (A, and B mode
-        // 4), then 4..6 (B modes 5..16).
-        const float sA = sqrtf(3.0f * P.kT * fmaxf(rhoA, 0.0f));
-        const float sB = sqrtf(3.0f * P.kT * fmaxf(rhoB, 0.0f));
-        const float sJ = 3.0f * P.nz_j * sqrtf(P.kT * fmaxf(rhoA, 0.0f) * fmaxf(rhoB, 0.0f) * fmaxf(irt, 0.0f));
-        const uint32_t stp = st->step_u32;
-        auto normals = [&](int blk, float zn[4], bool second_pair) {
-            uint32_t r0 = stp, r1 = n, r2 = (uint32_t)blk, r3 = 0u;
-            philox_rk(r0, r1, r2, r3, P);
-            box_muller(r0, r1, zn[0], zn[1]);
-            if (second_pair) box_muller(r2, r3, zn[2], zn[3]);
-        };
-        float zb17, zb18, zj[3], zb4;
-        {
-            float zn[4];
-            normals(7, zn, true);
-            zb17 = zn[0];
-            zb18 = zn[1];
-            zj[0] = zn[2];
-            zj[1] = zn[3];
-            normals(8, zn, false);
-            zj[2] = zn[0];
-        }
-        relax(ma, rhoA, FA, st->delta_f[0]);
-#pragma unroll
-        for (int blk = 0; blk < 4; ++blk) {
-            float zn[4];
-            normals(blk, zn, true);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int idx = 4 * blk + q;
-                if (idx < 15) ma[4 + idx] += sA * P.nz_mode[4 + idx] * zn[q];
-                else zb4 = zn[q];
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ma[1 + a] += sJ * zj[a];
-        store(0, ma, rhoA);
-        relax(mb, rhoB, FB, st->delta_f[1]);
-        mb[4] += sB * P.nz_mode[4] * zb4;
-#pragma unroll
-        for (int blk = 4; blk < 7; ++blk) {
-            float zn[4];
-            normals(blk, zn, true);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int idx = 4 * blk + q;  // 16..27: B modes 5..16
-                mb[4 + idx - 15] += sB * P.nz_mode[4 + idx - 15] * zn[q];
-            }
-        }
-        mb[17] += sB * P.nz_mode[17] * zb17;
-        mb[18] += sB * P.nz_mode[18] * zb18;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) mb[1 + a] -= sJ * zj[a];
-        store(1, mb, rhoB);
     }
     if (PARTICLE && solid_nb) {
         const double F[3] = {lk.F[0], lk.F[1], lk.F[2]};
@@ -452,7 +417,8 @@ __device__ __forceinline__ void near_tile(int cx, int cy, int cz, int tx, int ty
                                           const KParams& P)
 {
     near_tile_work<NOISE, TAU1>(cx, cy, cz, tx, ty, tid, fin, fout, psi, st, masks, partials, P);
-    if (last_block(&st->near_done, (unsigned)(P.ncx * P.ncy * P.ncz))) update_particle(st, partials, P);
+    if (last_block(&st->near_done, (unsigned)(P.ncx * P.ncy * P.ncz), tid < 8))  // tid < 8 wrote partials
+        update_particle(st, partials, P);
     __syncthreads();
 }
 
@@ -699,7 +665,8 @@ __device__ __forceinline__ void cover_then_finish(int blk, float* __restrict__ f
 {
     cover_block(blk, f, st, masks, parts, P);
     const int nb = (P.B * P.B * P.B + 255) / 256;
-    if (last_block(&st->cover_done, (unsigned)nb)) finish_step(st, counts, parts, nb, P);
+    if (last_block(&st->cover_done, (unsigned)nb, threadIdx.x < 8))  // threads 0..7 wrote parts
+        finish_step(st, counts, parts, nb, P);
     __syncthreads();
 }
 
