@@ -518,3 +518,113 @@ def test_sphere_comoving_with_uniform_flow_is_invisible(oracle_mod):
     keep = ~(solid0 | o.fields()["solid"])
     for l in range(2):
         assert np.allclose(g[l][:, keep], f[l][:, keep], rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Brute force on a 4^3 box
+# ---------------------------------------------------------------------------
+def test_full_step_on_a_4cubed_box_equals_population_space_bgk(oracle_mod):
+    """Three noise-free steps of a periodic 4x4x4 two-component box with the
+    Shan-Chen force, against a brute-force numpy step written in population
+    space: with every relaxation time 1 the MRT collision is BGK with tau = 1,
+    f* = f_eq(rho_l, u) + S_l / 2 with Guo's source
+    S_li = w_i [3 (c_i - u) . F_l + 9 (c_i . u)(c_i . F_l)], u = v^(H), and
+    streaming is a periodic shift of each direction by c_i."""
+    p = W.params(lx=4, ly=4, lz=4, wall=(0, 0, 0), G=1.2, kT=0.0)
+    f = W.random_populations(p, 44, amp=0.1, vel=0.05)
+    o = oracle_mod.Oracle(p)
+    o.set_f(f)
+    o.step(3)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    G = p["G"]
+
+    def shifted(a, c):  # a(x + c) on the periodic box, arrays indexed [z, y, x]
+        return np.roll(a, shift=(-int(c[2]), -int(c[1]), -int(c[0])), axis=(0, 1, 2))
+
+    for _ in range(3):
+        rho = f.sum(axis=1)                                    # (2, z, y, x)
+        j = np.einsum("lizyx,ia->lazyx", f, C)                 # (2, 3, z, y, x)
+        gsum = np.zeros_like(j)                                # sum_i w_i psi_other(x + c_i) c_i
+        for i in range(1, 19):
+            for l in range(2):
+                gsum[l] += w[i] * shifted(rho[1 - l], C[i])[None] * C[i][:, None, None, None]
+        F = -G * rho[:, None] * gsum
+        u = (j.sum(axis=0) + 0.5 * F.sum(axis=0)) / rho.sum(axis=0)
+        cu = np.einsum("ia,azyx->izyx", C, u)
+        uu = (u * u).sum(axis=0)
+        new = np.empty_like(f)
+        for l in range(2):
+            feq = w[:, None, None, None] * rho[l][None] * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * uu[None])
+            cF = np.einsum("ia,azyx->izyx", C, F[l])
+            uF = (u * F[l]).sum(axis=0)
+            S = w[:, None, None, None] * (3 * (cF - uF[None]) + 9 * cu * cF)
+            fs = feq + 0.5 * S
+            for i in range(19):
+                new[l, i] = shifted(fs[i], -C[i])  # f(x + c_i) <- f*(x)
+        f = new
+    assert np.allclose(o.get_f(), f, rtol=1e-13, atol=1e-16)
+
+
+# ---------------------------------------------------------------------------
+# Particle hydrodynamics and fluctuations
+# ---------------------------------------------------------------------------
+def _hasimoto_K(R, L):
+    """Drag factor of a simple cubic array of spheres (Hasimoto 1959):
+    F = 6 pi eta R U K, 1/K = 1 - 1.7601 c^(1/3) + c - 1.5593 c^2, c the
+    volume fraction."""
+    c = 4 / 3 * math.pi * R ** 3 / L ** 3
+    return 1 / (1 - 1.7601 * c ** (1 / 3) + c - 1.5593 * c ** 2)
+
+
+def test_settling_drag_of_a_sphere_in_a_periodic_box(oracle_mod):
+    """Noise-free sphere (R = 2.5) driven through a periodic 16^3 box, with the
+    counterforce on the fluid so that the system reaches a steady state.
+    The steady velocity relative to the fluid, read through Stokes' law with
+    Hasimoto's periodic-array correction and eta = rho nu = rho_tot / 6 (tau = 1),
+    gives the sphere's hydrodynamic radius: it must lie within half a lattice
+    spacing below and a full spacing above the nominal radius (bounce-back
+    spheres are known to act slightly smaller or larger than R)."""
+    R, L = 2.5, 16
+    p = W.params(lx=L, ly=L, lz=L, wall=(0, 0, 0), radius=R, rho_p_ratio=1.5, g=4e-4, kT=0.0, init_pert=0.0,
+                 G=0.0, fluid_counterforce=1)
+    o = oracle_mod.Oracle(p)
+    o.step(600)
+    us, uf = [], []
+    for _ in range(40):
+        o.step(10)
+        pa, ob = o.particle(), o.observables()
+        us.append(pa["V"][2])
+        uf.append(ob["momentum"][2] / ob["mass"].sum())
+    U = float(np.mean(us) - np.mean(uf))
+    eta = (p["rho_a0"] + p["rho_b0"]) / 6
+    F = o.particle()["Fp"]
+    Rh = R
+    for _ in range(60):
+        Rh = F / (6 * math.pi * eta * U * _hasimoto_K(Rh, L))
+    assert U > 0
+    assert R - 0.5 <= Rh <= R + 1.0, f"hydrodynamic radius {Rh:.3f} for R = {R}"
+    assert np.std(us) < 0.05 * abs(np.mean(us))  # steady
+
+
+def test_particle_velocity_equipartition(oracle_mod):
+    """A heavy sphere (rho_p = 5 rho, R = 2.5) in a fluctuating 12^3 channel
+    without driving: its velocity variance per axis is kT / m_p (the paper's
+    Langevin picture, Section 3). For light spheres the explicit time stepping
+    of the coupling biases the leap-frog velocities (about +30 % for the
+    half-step velocity, -10 % for the step average at rho_p = 1.5 rho); with a
+    long particle relaxation time both estimates must be within 15 %."""
+    p = W.params(lx=12, ly=12, lz=12, wall=(1, 1, 0), radius=2.5, rho_p_ratio=5.0, g=0.0, kT=1e-4, init_pert=0.0,
+                 G=0.0)
+    o = oracle_mod.Oracle(p)
+    o.step(300)
+    v, va = [], []
+    for _ in range(3000):
+        o.step(1)
+        pa = o.particle()
+        v.append(pa["V"].copy())
+        va.append(pa["Vavg"].copy())
+    s = p["kT"] / o.particle()["mp"]
+    rv = float(np.mean(np.var(v, axis=0)) / s)
+    ra = float(np.mean(np.var(va, axis=0)) / s)
+    assert 0.85 <= rv <= 1.15, rv
+    assert 0.85 <= ra <= 1.15, ra
