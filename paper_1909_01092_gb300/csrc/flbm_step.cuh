@@ -43,17 +43,25 @@ __device__ __forceinline__ void philox_rk(uint32_t& x0, uint32_t& x1, uint32_t& 
 // Box-Muller pair from two Philox words with the hardware approximations of
 // log2, rsqrt, sin and cos: z0 = r cos(2 pi u2), z1 = r sin(2 pi u2) with
 // r = sqrt(-2 ln u1); the angle is taken as 2 pi (u2 - 1/2) in (-pi, pi),
-// where the approximations are accurate, and the signs flipped back.
+// where the approximations are accurate, and the signs flipped back. The
+// flush-to-zero forms are used: their inputs and results here (u1 >= 2^-24,
+// |angle| >= 2^-22, -2 ln u1 of about 2^-23 at least) lie far above the
+// subnormal range, where both forms agree, and they skip the rescaling of
+// subnormal inputs.
 __device__ __forceinline__ void box_muller(uint32_t w1, uint32_t w2, float& z0, float& z1)
 {
     const float u1 = uniform_open(w1);
-    const float e = -1.38629436112f * __log2f(u1);  // -2 ln u1 > 0
-    const float r = e * rsqrtf(e);
+    float lg, rs, s, c;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(u1));
+    const float e = -1.38629436112f * lg;  // -2 ln u1 > 0
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(e));
+    const float r = e * rs;
     // 2 pi (u2 - 1/2) with u2 = ((w2 >> 9) + 1/2) 2^-23, as one multiply-add.
     constexpr float kA = (float)(6.283185307179586 / 8388608.0);
     constexpr float kB = (float)(6.283185307179586 * (0.5 / 8388608.0 - 0.5));
-    float s, c;
-    __sincosf(__fmaf_rn((float)(w2 >> 9), kA, kB), &s, &c);
+    const float ang = __fmaf_rn((float)(w2 >> 9), kA, kB);
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(ang));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(ang));
     z0 = -r * c;
     z1 = -r * s;
 }
