@@ -131,12 +131,13 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
  * FLBM_E_CUDA (launch failure). */
 int flbm_step(flbm_t* h, int64_t nsteps);
 
-/* Copy the particle record to host memory `out`; synchronises the stream. */
+/* Copy the particle record to host memory `out`; synchronises the stream.
+ * FLBM_E_TIMEOUT if a bounded device-side wait of an earlier step gave up. */
 int flbm_particle_state(flbm_t* h, flbm_particle* out);
 
 /* Reduce the observables of the current state (FP64) into `out`;
  * synchronises the stream. Returns FLBM_E_NONFINITE if any fluid population
- * is not finite (out is still filled). */
+ * is not finite (out is still filled), FLBM_E_TIMEOUT as flbm_particle_state. */
 int flbm_observables(flbm_t* h, flbm_obs* out);
 
 /* Copy the current populations to host_f (2*19*N float32, layout above) and,
@@ -210,6 +211,20 @@ int flbm_restore(flbm_t* h, const char* path);
  * FLBM_E_UNSUPPORTED then. enable = 0 returns to plain launches.
  * Errors: FLBM_E_INVAL, FLBM_E_UNSUPPORTED, FLBM_E_CUDA (capture failed). */
 int flbm_use_graphs(flbm_t* h, int enable);
+
+/* Bulk collide-stream with its inputs staged by the Tensor Memory Accelerator
+ * (same node update, Section 2, Eq. (lbe)): a persistent grid copies each
+ * tile's 38 x 256 populations and its padded density stencil into shared
+ * memory with tensor copies, double-buffered, while the previous tile is
+ * computed. Available when the lattice allows it (lx % 4 == 0 and
+ * lx >= 32); off by default, since the kernel that reads global memory
+ * directly keeps twice as many warps resident and runs this issue-bound
+ * update faster. Both give identical results. Captured step graphs are dropped on
+ * a change (the stream is synchronised). A bounded wait in this kernel that
+ * gives up makes flbm_particle_state and flbm_observables return
+ * FLBM_E_TIMEOUT. Errors: FLBM_E_INVAL, FLBM_E_UNSUPPORTED (enable = 1 on a
+ * lattice that does not allow it), FLBM_E_CUDA. */
+int flbm_use_tma(flbm_t* h, int enable);
 
 /* Observables of a population field, allocating nothing.
  *

@@ -1,6 +1,8 @@
 // C-ABI of the FLBM step library (declared in include/flbm.h): handle
 // management, validation, launch sequence of one time step, and the host
 // copies. All compute runs in the kernels of flbm_kernels.cuh.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -13,6 +15,7 @@
 
 #include "flbm.h"
 #include "flbm_sim.cuh"
+#include "flbm_tma.cuh"
 
 using namespace flbm;
 
@@ -59,6 +62,74 @@ void record(flbm_sim* h, cudaEvent_t* ev, int k)
     if (ev) cudaEventRecord(ev[k], h->stream);
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once (no link to libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor maps and launch shape of k_collide_bulk_tma. The populations of one
+// copy are a 4-D float tensor (lx, ly, lz, 38) and the padded densities one of
+// (px, py, pz, 2); both need rows of a multiple of 16 bytes (lx % 4 == 0,
+// px is rounded up) and the 32 x 8 tile. Otherwise, or if the driver refuses
+// a map, the kernel is unavailable. It is off by default: holding two stages
+// of 256 nodes in shared memory leaves room for two blocks (16 warps) per
+// SM, and the direct kernel with 32 resident warps runs the issue-bound
+// update faster.
+void setup_tma(flbm_sim* h)
+{
+    const KParams& k = h->kp;
+    h->tma_ok = h->tma = false;
+    if (k.lx % 4 != 0 || k.tx != kTmaTX || k.ty != kTmaTY || k.px % 4 != 0) return;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return;
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    for (int c = 0; c < 2; ++c) {
+        const cuuint64_t dims[4] = {(cuuint64_t)k.lx, (cuuint64_t)k.ly, (cuuint64_t)k.lz, 38};
+        const cuuint64_t strides[3] = {(cuuint64_t)k.lx * 4, (cuuint64_t)k.lx * k.ly * 4, (cuuint64_t)k.N * 4};
+        const cuuint32_t box[4] = {kTmaTX, kTmaTY, 1, 38};
+        if (enc(&h->tm_f[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->fbuf[c], dims, strides, box, one,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return;
+    }
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)k.px, (cuuint64_t)k.py, (cuuint64_t)k.pz, 2};
+        const cuuint64_t strides[3] = {(cuuint64_t)k.px * 4, (cuuint64_t)k.px * k.py * 4, (cuuint64_t)k.padn * 4};
+        const cuuint32_t box[4] = {kTmaPX, kTmaPY, 3, 2};
+        if (enc(&h->tm_psi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->psi, dims, strides, box, one,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return;
+    void (*kern[4])(const CUtensorMap, const CUtensorMap, float*, DevState*, KParams) = {
+        k_collide_bulk_tma<false, false>, k_collide_bulk_tma<false, true>, k_collide_bulk_tma<true, false>,
+        k_collide_bulk_tma<true, true>};
+    for (auto* f : kern)
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmemBytes) != cudaSuccess)
+            return;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[3], kThreadsStep, kTmaSmemBytes) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return;
+    h->tma_grid = (int)std::min<long long>(h->ntiles, (long long)sms * per_sm);
+    h->tma_ok = true;  // available; flbm_use_tma switches it on
+}
+
 // Densities, then the psi shell and the virtual layer (one launch), for the
 // current state. With ev, events ev[0..2] bracket the two kernels.
 int launch_psi(flbm_sim* h, const float* f, cudaEvent_t* ev = nullptr)
@@ -88,8 +159,14 @@ int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
     const dim3 gnear(k.ncx, k.ncy, k.ncz);
 #define FLBM_COLLIDE(NZ, T1)                                                                                  \
     do {                                                                                                      \
-        k_collide_bulk<NZ, T1><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, k);             \
-        if (int rc = launch_check(h, "k_collide_bulk")) return rc;                                            \
+        if (h->tma) {                                                                                         \
+            k_collide_bulk_tma<NZ, T1><<<h->tma_grid, h->block, kTmaSmemBytes, h->stream>>>(                   \
+                h->tm_f[h->cur], h->tm_psi, fout, h->st, k);                                                  \
+            if (int rc = launch_check(h, "k_collide_bulk_tma")) return rc;                                    \
+        } else {                                                                                              \
+            k_collide_bulk<NZ, T1><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, k);         \
+            if (int rc = launch_check(h, "k_collide_bulk")) return rc;                                        \
+        }                                                                                                     \
         if (part) {                                                                                           \
             k_collide_near<NZ, T1><<<gnear, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks,     \
                                                                       h->partials, k);                        \
@@ -247,6 +324,7 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
         if (launch_check(h, "k_mark")) return bail(FLBM_E_CUDA);
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(FLBM_E_CUDA);
+    setup_tma(h);
     *out = h;
     return FLBM_OK;
 }
@@ -265,6 +343,24 @@ int flbm_step(flbm_t* h, int64_t nsteps)
     }
     for (; s < nsteps; ++s)
         if (int rc = launch_step(h)) return rc;
+    return FLBM_OK;
+}
+
+int flbm_use_tma(flbm_t* h, int enable)
+{
+    if (!h || (enable != 0 && enable != 1)) return fail(h, FLBM_E_INVAL, "invalid argument");
+    if (enable && !h->tma_ok)
+        return fail(h, FLBM_E_UNSUPPORTED, "TMA-staged collide needs lx % 4 == 0 and lx >= 32");
+    if (h->tma != (enable != 0)) {
+        // Captured graphs hold the other bulk kernel.
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (int c = 0; c < 2; ++c)
+            if (h->graph[c]) {
+                cudaGraphExecDestroy(h->graph[c]);
+                h->graph[c] = nullptr;
+            }
+    }
+    h->tma = enable != 0;
     return FLBM_OK;
 }
 
@@ -351,6 +447,7 @@ int flbm_particle_state(flbm_t* h, flbm_particle* out)
     DevState s;
     CK(h, cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    if (s.err) return fail(h, FLBM_E_TIMEOUT, "a bounded device-side wait gave up");
     return copy_particle(s, out);
 }
 
@@ -368,6 +465,7 @@ int flbm_observables(flbm_t* h, flbm_obs* out)
     CK(h, cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     fill_obs(v, s, out);
+    if (s.err) return fail(h, FLBM_E_TIMEOUT, "a bounded device-side wait gave up");
     return out->nonfinite ? fail(h, FLBM_E_NONFINITE, "non-finite populations") : FLBM_OK;
 }
 

@@ -757,17 +757,18 @@ static __global__ void __launch_bounds__(kT) ka_lpsi_shell(const aux_t* __restri
                                                            const uint8_t* __restrict__ mk0, KParams P)
 {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long nzf = 2LL * P.px * P.py, nyf = 2LL * P.px * P.lz, nxf = 2LL * P.ly * P.lz;
+    const long long pw = P.lx + 2;  // padded row length (the row stride P.px may be larger)
+    const long long nzf = 2LL * pw * P.py, nyf = 2LL * pw * P.lz, nxf = 2LL * P.ly * P.lz;
     int p[3];
     if (t < nzf) {
-        const long long r = t % ((long long)P.px * P.py);
-        p[0] = (int)(r % P.px) - 1;
-        p[1] = (int)(r / P.px) - 1;
+        const long long r = t % (pw * P.py);
+        p[0] = (int)(r % pw) - 1;
+        p[1] = (int)(r / pw) - 1;
         p[2] = (t < nzf / 2) ? -1 : P.lz;
     } else if (t < nzf + nyf) {
-        const long long u = t - nzf, r = u % ((long long)P.px * P.lz);
-        p[0] = (int)(r % P.px) - 1;
-        p[2] = (int)(r / P.px);
+        const long long u = t - nzf, r = u % (pw * P.lz);
+        p[0] = (int)(r % pw) - 1;
+        p[2] = (int)(r / pw);
         p[1] = (u < nyf / 2) ? -1 : P.ly;
     } else if (t < nzf + nyf + nxf) {
         const long long u = t - nzf - nyf, r = u % ((long long)P.ly * P.lz);

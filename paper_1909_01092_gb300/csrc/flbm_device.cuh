@@ -161,7 +161,7 @@ __device__ __forceinline__ float uniform_open(uint32_t x)
 struct KParams {
     int lx, ly, lz;
     int wall[3];
-    int px, py, pz;        // padded psi dimensions lx+2, ly+2, lz+2
+    int px, py, pz;        // padded psi row stride (lx + 2 rounded up to 4) and dimensions ly + 2, lz + 2
     long long N;           // lx*ly*lz
     long long padn;        // px*py*pz
     int tx, ty;            // tile (block) shape in x, y; one z-plane per block

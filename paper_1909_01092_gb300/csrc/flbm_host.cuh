@@ -74,7 +74,8 @@ inline void make_kparams(const flbm_params& p, int tile_policy, KParams& k)
     std::memset(&k, 0, sizeof(k));
     k.lx = p.lx; k.ly = p.ly; k.lz = p.lz;
     k.wall[0] = p.wall_x; k.wall[1] = p.wall_y; k.wall[2] = p.wall_z;
-    k.px = p.lx + 2; k.py = p.ly + 2; k.pz = p.lz + 2;
+    k.px = (p.lx + 2 + 3) / 4 * 4;  // row stride: lx + 2 nodes, rounded up to 16 bytes
+    k.py = p.ly + 2; k.pz = p.lz + 2;
     k.N = (long long)p.lx * p.ly * p.lz;
     k.padn = (long long)k.px * k.py * k.pz;
     k.tx = tile_width(p.lx, tile_policy);

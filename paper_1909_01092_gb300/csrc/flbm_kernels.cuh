@@ -146,10 +146,12 @@ static __global__ void __launch_bounds__(kThreads) k_virtual(float* __restrict__
 }
 
 // Shell nodes of the padded psi field: z faces (full padded planes), y faces
-// (interior z), x faces (interior y and z).
+// (interior z), x faces (interior y and z). A padded row holds lx + 2 nodes;
+// its stride P.px may be larger (rounded up to 16 bytes).
 __host__ __device__ __forceinline__ long long shell_count(const KParams& P)
 {
-    return 2LL * P.px * P.py + 2LL * P.px * P.lz + 2LL * P.ly * P.lz;
+    const long long pw = P.lx + 2;
+    return 2LL * pw * P.py + 2LL * pw * P.lz + 2LL * P.ly * P.lz;
 }
 
 // ---------------------------------------------------------------------------
@@ -160,20 +162,21 @@ __host__ __device__ __forceinline__ long long shell_count(const KParams& P)
 __device__ __forceinline__ void shell_node(long long t, float* __restrict__ psi, const DevState* __restrict__ st,
                                            const uint8_t* __restrict__ masks, const KParams& P)
 {
-    const long long nzf = 2LL * P.px * P.py;        // z faces, full padded planes
-    const long long nyf = 2LL * P.px * P.lz;        // y faces, interior z
+    const long long pw = P.lx + 2;                  // padded row length
+    const long long nzf = 2LL * pw * P.py;          // z faces, full padded planes
+    const long long nyf = 2LL * pw * P.lz;          // y faces, interior z
     const long long nxf = 2LL * P.ly * P.lz;        // x faces, interior y, z
     int p[3];
     if (t < nzf) {
-        const long long r = t % (P.px * P.py);
-        p[0] = (int)(r % P.px) - 1;
-        p[1] = (int)(r / P.px) - 1;
+        const long long r = t % (pw * P.py);
+        p[0] = (int)(r % pw) - 1;
+        p[1] = (int)(r / pw) - 1;
         p[2] = (t < nzf / 2) ? -1 : P.lz;
     } else if (t < nzf + nyf) {
         const long long u = t - nzf;
-        const long long r = u % ((long long)P.px * P.lz);
-        p[0] = (int)(r % P.px) - 1;
-        p[2] = (int)(r / P.px);
+        const long long r = u % (pw * P.lz);
+        p[0] = (int)(r % pw) - 1;
+        p[2] = (int)(r / pw);
         p[1] = (u < nyf / 2) ? -1 : P.ly;
     } else if (t < nzf + nyf + nxf) {
         const long long u = t - nzf - nyf;

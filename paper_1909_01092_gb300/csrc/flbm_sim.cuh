@@ -2,6 +2,7 @@
 // translation units of the library (single simulation and adjoint).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -39,6 +40,14 @@ struct flbm_sim {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two steps starting from cur = 0 / 1
     int64_t graph_launches[2] = {0, 0};            // kernels in each graph
     dim3 grid, block;
+    // Bulk collide with TMA-staged inputs (k_collide_bulk_tma): tensor maps of
+    // the two population copies and of the padded densities; tma_ok when the
+    // lattice allows it, tma when it is in use; persistent grid size.
+    CUtensorMap tm_f[2];
+    CUtensorMap tm_psi;
+    bool tma_ok = false;
+    bool tma = false;
+    int tma_grid = 0;
     long long ntiles = 0;
     int64_t launches = 0;
     std::string err;

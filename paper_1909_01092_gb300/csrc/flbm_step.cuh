@@ -97,17 +97,37 @@ __device__ __forceinline__ void moments(const float f[19], float& rho, float j[3
     j[2] = (f[5] - f[6]) + d11 - d13 + d15 - d17;
 }
 
+// Where collide_core reads a node's inputs: f(q) is population q = 19 l + i
+// of the node, psa(i) / psb(i) the densities rho_A / rho_B of neighbour
+// x + c_i in the padded psi field.
+struct GlobalInputs {
+    const float* __restrict__ fin;  // current populations; (l, i) of node m at m + P.dirN[19 l + i]
+    const float* __restrict__ pA;   // psi_A at the node (padded field); psi_B at pA + padn
+    uint32_t n;
+    long long padn;
+    int sy, sz;                      // padded row and plane strides
+    __device__ __forceinline__ GlobalInputs(const float* f, const float* psi, int x, int y, int z, uint32_t node,
+                                            const KParams& P)
+        : fin(f), pA(psi + pad_index(x, y, z, P)), n(node), padn(P.padn), sy(P.px), sz(P.px * P.py)
+    {
+    }
+    __device__ __forceinline__ float f(int q, const KParams& P) const { return __ldg(fin + (n + P.dirN[q])); }
+    __device__ __forceinline__ int off(int i) const { return cxv(i) + sy * cyv(i) + sz * czv(i); }
+    __device__ __forceinline__ float psa(int i) const { return __ldg(pA + off(i)); }
+    __device__ __forceinline__ float psb(int i) const { return __ldg(pA + padn + off(i)); }
+};
+
 // Collision and push-streaming of one fluid node (Eq. (lbe)). With PARTICLE,
 // solid_nb marks the directions whose neighbour is a particle node; their
 // links take the moving rule and feed acc = (F[3], T[3], ledger[2]). TAU1:
 // every relaxation time is 1, so the post-collision modes depend on the
 // input only through rho_l and j_l, and the ghost modes carry noise only.
-// Population (l, i) of node m lives at index m + P.dirN[19 l + i] (32-bit).
-template <bool NOISE, bool PARTICLE, bool TAU1>
-__device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, const float* __restrict__ fin,
-                                             float* __restrict__ fout, const float* __restrict__ psi,
-                                             const DevState* __restrict__ st, const KParams& P, uint32_t solid_nb,
-                                             double* acc)
+// The inputs come from `in` (global memory or a shared-memory tile); the
+// outputs are pushed to fout, population (l, i) of node m at m + P.dirN[19 l + i].
+template <bool NOISE, bool PARTICLE, bool TAU1, class In>
+__device__ __forceinline__ void collide_core(int x, int y, int z, uint32_t n, const In& in,
+                                             float* __restrict__ fout, const DevState* __restrict__ st,
+                                             const KParams& P, uint32_t solid_nb, double* acc)
 {
     float ma[19], mb[19];
     float rhoA, rhoB;
@@ -115,8 +135,8 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, co
         float fa[19], fb[19];
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            fa[i] = __ldg(fin + (n + P.dirN[i]));
-            fb[i] = __ldg(fin + (n + P.dirN[19 + i]));
+            fa[i] = in.f(i, P);
+            fb[i] = in.f(19 + i, P);
         }
         if (TAU1) {
             moments(fa, ma[0], ma + 1);
@@ -147,14 +167,10 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, co
     // Shan-Chen force, Eq. (sc-force), omega_i = w_i, psi = rho.
     float ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
     {
-        const float* pA = psi + pad_index(x, y, z, P);
-        const float* pB = pA + P.padn;
-        const int sy = P.px, sz = P.px * P.py;
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
-            const int off = cxv(i) + sy * cyv(i) + sz * czv(i);
-            const float pa = __ldg(pA + off);
-            const float pb = __ldg(pB + off);
+            const float pa = in.psa(i);
+            const float pb = in.psb(i);
             const float w = wv(i);
             if (cxv(i)) { ga[0] += (cxv(i) * w) * pb; gb[0] += (cxv(i) * w) * pa; }
             if (cyv(i)) { ga[1] += (cyv(i) * w) * pb; gb[1] += (cyv(i) * w) * pa; }
@@ -305,6 +321,17 @@ __device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, co
         acc[6] += lk.led[0];
         acc[7] += lk.led[1];
     }
+}
+
+// collide_core with its inputs read from global memory.
+template <bool NOISE, bool PARTICLE, bool TAU1>
+__device__ __forceinline__ void collide_node(int x, int y, int z, uint32_t n, const float* __restrict__ fin,
+                                             float* __restrict__ fout, const float* __restrict__ psi,
+                                             const DevState* __restrict__ st, const KParams& P, uint32_t solid_nb,
+                                             double* acc)
+{
+    const GlobalInputs in(fin, psi, x, y, z, n, P);
+    collide_core<NOISE, PARTICLE, TAU1>(x, y, z, n, in, fout, st, P, solid_nb, acc);
 }
 
 // ---------------------------------------------------------------------------
