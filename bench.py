@@ -40,11 +40,11 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes of the collide class (bulk + near launches) per step of the
 # 128x128x512 channel, from an ncu capture of the same kernels at 128x128x128
 # scaled by bulk nodes (profiles/k_collide_bulk_channel_128x128x128.md):
-# 290 B per bulk node x 8,331,264 bulk nodes + 9.9 MB for the near tiles.
-COLLIDE_TRAFFIC_BYTES = 290.1 * 8331264 + 9.9e6
+# 289.6 B per bulk node x 8,331,264 bulk nodes + 9.9 MB for the near tiles.
+COLLIDE_TRAFFIC_BYTES = (329398784 + 261222912) / 2039808 * 8331264 + 9.9e6
 # Thread instructions per node of the noisy bulk collide kernel (same capture:
-# 119.3 M warp instructions over 2,039,808 nodes).
-COLLIDE_INST_PER_NODE = 119.3e6 * 32 / 2039808
+# 107.6 M warp instructions over 2,039,808 nodes).
+COLLIDE_INST_PER_NODE = 107604480 * 32 / 2039808
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 
