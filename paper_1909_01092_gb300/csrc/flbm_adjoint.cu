@@ -70,10 +70,50 @@ struct AdjState {
 #ifndef FLBM_ADJ_AUX
 #define FLBM_ADJ_AUX double
 #endif
-using lam_t = double;
 using aux_t = FLBM_ADJ_AUX;
 
+// The (a_l, b_l) fields are stored as two floats, v = hi + lo with
+// lo = fl(v - hi): 48 significant bits. A node reads its own values as FP64
+// (sval) and forms its neighbours' differences in float from the two parts
+// (sdiff; the high parts of close values subtract exactly), so the stencil
+// loop of the node adjoint needs no FP64 arithmetic, which is scarce here.
+struct __align__(8) Split {
+    float hi, lo;
+};
+__device__ __forceinline__ double sval(Split s) { return (double)s.hi + (double)s.lo; }
+__device__ __forceinline__ Split ssplit(double v)
+{
+    const float h = (float)v;
+    return Split{h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ float sdiff(Split a, Split b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+using lam_t = Split;
+
 constexpr int kT = 256;  // threads per block
+
+// Sum of NV <= 8 doubles over the block by the tree of block_sum8 (so each
+// sum is the same), without reducing unused slots; s_out[0..NV) is the result.
+template <int NV>
+__device__ __forceinline__ void block_sum_n(const double v[NV], double* s_red, double* s_out)
+{
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarp = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double a = v[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+        if (lane == 0) s_red[warp * 8 + k] = a;
+    }
+    __syncthreads();
+    if (tid < NV) {
+        double a = 0.0;
+        for (int w = 0; w < nwarp; ++w) a += s_red[w * 8 + tid];
+        s_out[tid] = a;
+    }
+    __syncthreads();
+}
 constexpr int kNodeParts = 12;  // per tile: lX[3], lV[3], lOm[3], dJ/dG, ld[2]
 
 // Periodic-aware neighbour of (x,y,z) along c; false if it leaves through a wall.
@@ -229,7 +269,7 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 static __global__ void __launch_bounds__(kT) ka_cover(lam_t* __restrict__ lam1, const float* __restrict__ tape1,
                                                       const DevState* __restrict__ s0, const uint8_t* __restrict__ mk0,
                                                       const DevState* __restrict__ s1, const uint8_t* __restrict__ mk1,
-                                                      const AdjState* __restrict__ adj, lam_t* __restrict__ uv,
+                                                      const AdjState* __restrict__ adj, double* __restrict__ uv,
                                                       double* __restrict__ parts, KParams P)
 {
     __shared__ double s_red[(kT / 32) * 8];
@@ -260,8 +300,8 @@ static __global__ void __launch_bounds__(kT) ka_cover(lam_t* __restrict__ lam1, 
                 cross3(adj->lL, r, lb);
                 for (int a = 0; a < 3; ++a) lb[a] += adj->lP[a];
                 for (int l = 0; l < 2; ++l) {
-                    lam1[(size_t)l * N + n] = adj->lled[l];
-                    for (int a = 0; a < 3; ++a) lam1[(size_t)(2 + 3 * l + a) * N + n] = lb[a];
+                    lam1[(size_t)l * N + n] = ssplit(adj->lled[l]);
+                    for (int a = 0; a < 3; ++a) lam1[(size_t)(2 + 3 * l + a) * N + n] = ssplit(lb[a]);
                 }
                 for (int a = 0; a < 3; ++a) j[a] = (double)tape1[(2 + a) * N + n] + (double)tape1[(5 + a) * N + n];
                 cross3(j, adj->lL, t3);  // d/dX' of lambda_L . ((c - X') x j) = -(j x lambda_L)
@@ -298,9 +338,9 @@ static __global__ void __launch_bounds__(kT) ka_cover(lam_t* __restrict__ lam1, 
                 const double rsum = rl[0] + rl[1];
                 double lqub = lq[0] * ub[0] + lq[1] * ub[1] + lq[2] * ub[2];
                 for (int l = 0; l < 2; ++l) {
-                    const double al = lam1[(size_t)l * N + n];
+                    const double al = sval(lam1[(size_t)l * N + n]);
                     double bl[3];
-                    for (int a = 0; a < 3; ++a) bl[a] = lam1[(size_t)(2 + 3 * l + a) * N + n];
+                    for (int a = 0; a < 3; ++a) bl[a] = sval(lam1[(size_t)(2 + 3 * l + a) * N + n]);
                     const double lmean = al + bl[0] * ub[0] + bl[1] * ub[1] + bl[2] * ub[2] - lqub - adj->lled[l];
                     if (cnt) uv[(size_t)l * B3 + t] = lmean / cnt;
                     for (int a = 0; a < 3; ++a) lub[a] += rl[l] * bl[a];
@@ -336,7 +376,7 @@ static __global__ void __launch_bounds__(kT) ka_cover(lam_t* __restrict__ lam1, 
 static __global__ void __launch_bounds__(kT) ka_cover_mean(lam_t* __restrict__ lam1, const DevState* __restrict__ s0,
                                                            const uint8_t* __restrict__ mk0,
                                                            const DevState* __restrict__ s1,
-                                                           const uint8_t* __restrict__ mk1, const lam_t* __restrict__ uv,
+                                                           const uint8_t* __restrict__ mk1, const double* __restrict__ uv,
                                                            KParams P)
 {
     const int B = P.B, G = B + 2, B3 = B * B * B;
@@ -357,7 +397,7 @@ static __global__ void __launch_bounds__(kT) ka_cover_mean(lam_t* __restrict__ l
         }
     }
     if (is_solid(m[0], m[1], m[2], o0, m0, P) || is_solid(m[0], m[1], m[2], o1, m1, P)) return;
-    lam_t add[2] = {0.0, 0.0};
+    double add[2] = {0.0, 0.0};
     for (int jd = 1; jd < 19; ++jd) {
         int c[3];
         if (!nbr(m[0], m[1], m[2], cxv(jd), cyv(jd), czv(jd), P, c)) continue;
@@ -369,8 +409,8 @@ static __global__ void __launch_bounds__(kT) ka_cover_mean(lam_t* __restrict__ l
     }
     if (add[0] != 0.0 || add[1] != 0.0) {
         const uint32_t n = lin(m[0], m[1], m[2], P);
-        lam1[n] += add[0];
-        lam1[P.N + n] += add[1];
+        lam1[n] = ssplit(sval(lam1[n]) + add[0]);
+        lam1[P.N + n] = ssplit(sval(lam1[P.N + n]) + add[1]);
     }
 }
 
@@ -436,7 +476,7 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
         const uint8_t* m0 = cur_mask(s0, mk0, P);
         const uint32_t n = lin(x, y, z, P);
         if (PARTICLE && solid_at(x, y, z, s0, m0, P)) {
-            for (int k = 0; k < 8; ++k) lam0[k * N + n] = 0.0;
+            for (int k = 0; k < 8; ++k) lam0[k * N + n] = Split{0.0f, 0.0f};
             for (int k = 0; k < 6; ++k) lg[k * N + n] = 0.0f;
         } else {
             float rho[2], j[2][3], g[2][3];
@@ -495,8 +535,11 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
             float lm[2][10];               // mode adjoint of the neighbour differences
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
-                axd[l] = lam1[(size_t)l * N + n];
-                for (int a = 0; a < 3; ++a) bxd[l][a] = lam1[(size_t)(2 + 3 * l + a) * N + n];
+                const Split as = lam1[(size_t)l * N + n];
+                Split bs[3];
+                for (int a = 0; a < 3; ++a) bs[a] = lam1[(size_t)(2 + 3 * l + a) * N + n];
+                axd[l] = sval(as);
+                for (int a = 0; a < 3; ++a) bxd[l][a] = sval(bs[a]);
                 const double ax = axd[l];
                 const double* bx = bxd[l];
                 float wl[19];
@@ -540,10 +583,10 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                         }
                     } else {
                         const uint32_t q = qidx[i];
-                        dv = (float)(lam1[(size_t)l * N + q] - ax);
-                        if (cx) dv += cx * (float)(lam1[(2 + 3 * l) * N + q] - bx[0]);
-                        if (cy) dv += cy * (float)(lam1[(3 + 3 * l) * N + q] - bx[1]);
-                        if (cz) dv += cz * (float)(lam1[(4 + 3 * l) * N + q] - bx[2]);
+                        dv = sdiff(lam1[(size_t)l * N + q], as);
+                        if (cx) dv += cx * sdiff(lam1[(2 + 3 * l) * N + q], bs[0]);
+                        if (cy) dv += cy * sdiff(lam1[(3 + 3 * l) * N + q], bs[1]);
+                        if (cz) dv += cz * sdiff(lam1[(4 + 3 * l) * N + q], bs[2]);
                     }
                     wl[i] = wv(i) * dv;
                     wsum += wl[i];
@@ -592,9 +635,9 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
             adj_modes_ab<double>(rd, jd, gd, ed, (double)P.G, axd, bxd, lrd, ljd, lgd, lGd);
             acc[9] += lGd + (double)lG;
             for (int l = 0; l < 2; ++l) {
-                lam0[(size_t)l * N + n] = lrd[l] + (double)lrho[l] + lrx[l];
+                lam0[(size_t)l * N + n] = ssplit(lrd[l] + (double)lrho[l] + lrx[l]);
                 for (int a = 0; a < 3; ++a) {
-                    lam0[(size_t)(2 + 3 * l + a) * N + n] = ljd[l][a] + (double)lj[l][a];
+                    lam0[(size_t)(2 + 3 * l + a) * N + n] = ssplit(ljd[l][a] + (double)lj[l][a]);
                     lg[(size_t)(3 * l + a) * N + n] = (aux_t)(lgd[l][a] + (double)lgv[l][a]);
                 }
             }
@@ -611,8 +654,9 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
     } else if (tid < 9) {
         parts[tile * kNodeParts + tid] = 0.0;  // no link terms away from the particle
     }
-    for (int k = 0; k < 8; ++k) v8[k] = k < kNodeParts - 8 ? acc[8 + k] : 0.0;
-    block_sum8<kT>(v8, s_red, s_out);
+    double v4[kNodeParts - 8];
+    for (int k = 0; k < kNodeParts - 8; ++k) v4[k] = acc[8 + k];
+    block_sum_n<kNodeParts - 8>(v4, s_red, s_out);
     if (tid < kNodeParts - 8) parts[tile * kNodeParts + 8 + tid] = s_out[tid];
 }
 
@@ -827,8 +871,8 @@ static __global__ void __launch_bounds__(kT) ka_final(lam_t* __restrict__ lam0, 
         add[1] += lpsi[P.padn + q];
     }
     const uint32_t n = lin(x, y, z, P);
-    lam0[n] += add[0];
-    lam0[P.N + n] += add[1];
+    lam0[n] = ssplit(sval(lam0[n]) + (double)add[0]);
+    lam0[P.N + n] = ssplit(sval(lam0[P.N + n]) + (double)add[1]);
 }
 
 // Per-tile partials -> adjoint of step n's particle state and the gradient
@@ -882,7 +926,7 @@ struct AdjBuffers {
     lam_t* lam[2] = {nullptr, nullptr};
     aux_t* lgf = nullptr;
     aux_t* lpsi = nullptr;
-    lam_t* uv = nullptr;
+    double* uv = nullptr;
     double* parts = nullptr;
     double* parts2 = nullptr;
     double* cparts = nullptr;

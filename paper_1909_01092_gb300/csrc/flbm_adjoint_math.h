@@ -28,10 +28,11 @@ template <class T>
 FLBM_HD void fwd_modes(const T rho[2], const T j[2][3], const T g[2][3], const T ext[3], T G, T ms[2][10])
 {
     const T rt = rho[0] + rho[1];
+    const T irt = T(1) / rt;
     T F[2][3], u[3];
     for (int l = 0; l < 2; ++l)
-        for (int a = 0; a < 3; ++a) F[l][a] = -G * rho[l] * g[l][a] + rho[l] / rt * ext[a];
-    for (int a = 0; a < 3; ++a) u[a] = (j[0][a] + j[1][a] + T(0.5) * (F[0][a] + F[1][a])) / rt;
+        for (int a = 0; a < 3; ++a) F[l][a] = -G * rho[l] * g[l][a] + rho[l] * irt * ext[a];
+    for (int a = 0; a < 3; ++a) u[a] = (j[0][a] + j[1][a] + T(0.5) * (F[0][a] + F[1][a])) * irt;
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     for (int l = 0; l < 2; ++l) {
         const T r = rho[l];
@@ -54,10 +55,11 @@ FLBM_HD void adj_modes(const T rho[2], const T j[2][3], const T g[2][3], const T
                        T lrho[2], T lj[2][3], T lg[2][3], T& lG)
 {
     const T rt = rho[0] + rho[1];
+    const T irt = T(1) / rt;
     T F[2][3], u[3];
     for (int l = 0; l < 2; ++l)
-        for (int a = 0; a < 3; ++a) F[l][a] = -G * rho[l] * g[l][a] + rho[l] / rt * ext[a];
-    for (int a = 0; a < 3; ++a) u[a] = (j[0][a] + j[1][a] + T(0.5) * (F[0][a] + F[1][a])) / rt;
+        for (int a = 0; a < 3; ++a) F[l][a] = -G * rho[l] * g[l][a] + rho[l] * irt * ext[a];
+    for (int a = 0; a < 3; ++a) u[a] = (j[0][a] + j[1][a] + T(0.5) * (F[0][a] + F[1][a])) * irt;
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
 
     // Modes -> (rho_l, u, F_l) with u and F_l held as independent inputs.
@@ -83,16 +85,16 @@ FLBM_HD void adj_modes(const T rho[2], const T j[2][3], const T g[2][3], const T
     T ul = T(0);
     for (int a = 0; a < 3; ++a) ul += lu[a] * u[a];
     for (int l = 0; l < 2; ++l) {
-        lrho[l] -= ul / rt;
+        lrho[l] -= ul * irt;
         for (int a = 0; a < 3; ++a) {
-            lj[l][a] = lu[a] / rt;
-            lF[l][a] += T(0.5) * lu[a] / rt;
+            lj[l][a] = lu[a] * irt;
+            lF[l][a] += T(0.5) * lu[a] * irt;
         }
     }
     // F_l = -G rho_l g_l + (rho_l / rho_t) ext
     T eF[2];
     for (int l = 0; l < 2; ++l) eF[l] = lF[l][0] * ext[0] + lF[l][1] * ext[1] + lF[l][2] * ext[2];
-    const T es = (rho[0] * eF[0] + rho[1] * eF[1]) / (rt * rt);
+    const T es = (rho[0] * eF[0] + rho[1] * eF[1]) * (irt * irt);
     lG = T(0);
     for (int l = 0; l < 2; ++l) {
         T gl = T(0);
@@ -100,7 +102,7 @@ FLBM_HD void adj_modes(const T rho[2], const T j[2][3], const T g[2][3], const T
             gl += g[l][a] * lF[l][a];
             lg[l][a] = -G * rho[l] * lF[l][a];
         }
-        lrho[l] += -G * gl + eF[l] / rt - es;
+        lrho[l] += -G * gl + eF[l] * irt - es;
         lG += -rho[l] * gl;
     }
 }
@@ -113,10 +115,11 @@ FLBM_HD void adj_modes_ab(const T rho[2], const T j[2][3], const T g[2][3], cons
                           const T b[2][3], T lrho[2], T lj[2][3], T lg[2][3], T& lG)
 {
     const T rt = rho[0] + rho[1];
+    const T irt = T(1) / rt;
     T F[2][3], u[3];
     for (int l = 0; l < 2; ++l)
-        for (int c = 0; c < 3; ++c) F[l][c] = -G * rho[l] * g[l][c] + rho[l] / rt * ext[c];
-    for (int c = 0; c < 3; ++c) u[c] = (j[0][c] + j[1][c] + T(0.5) * (F[0][c] + F[1][c])) / rt;
+        for (int c = 0; c < 3; ++c) F[l][c] = -G * rho[l] * g[l][c] + rho[l] * irt * ext[c];
+    for (int c = 0; c < 3; ++c) u[c] = (j[0][c] + j[1][c] + T(0.5) * (F[0][c] + F[1][c])) * irt;
     T lu[3] = {T(0), T(0), T(0)};
     T lF[2][3];
     for (int l = 0; l < 2; ++l) {
@@ -128,15 +131,15 @@ FLBM_HD void adj_modes_ab(const T rho[2], const T j[2][3], const T g[2][3], cons
     }
     const T ul = lu[0] * u[0] + lu[1] * u[1] + lu[2] * u[2];
     for (int l = 0; l < 2; ++l) {
-        lrho[l] -= ul / rt;
+        lrho[l] -= ul * irt;
         for (int c = 0; c < 3; ++c) {
-            lj[l][c] = lu[c] / rt;
-            lF[l][c] += T(0.5) * lu[c] / rt;
+            lj[l][c] = lu[c] * irt;
+            lF[l][c] += T(0.5) * lu[c] * irt;
         }
     }
     T eF[2];
     for (int l = 0; l < 2; ++l) eF[l] = lF[l][0] * ext[0] + lF[l][1] * ext[1] + lF[l][2] * ext[2];
-    const T es = (rho[0] * eF[0] + rho[1] * eF[1]) / (rt * rt);
+    const T es = (rho[0] * eF[0] + rho[1] * eF[1]) * (irt * irt);
     lG = T(0);
     for (int l = 0; l < 2; ++l) {
         T gl = T(0);
@@ -144,7 +147,7 @@ FLBM_HD void adj_modes_ab(const T rho[2], const T j[2][3], const T g[2][3], cons
             gl += g[l][c] * lF[l][c];
             lg[l][c] = -G * rho[l] * lF[l][c];
         }
-        lrho[l] += -G * gl + eF[l] / rt - es;
+        lrho[l] += -G * gl + eF[l] * irt - es;
         lG += -rho[l] * gl;
     }
 }
