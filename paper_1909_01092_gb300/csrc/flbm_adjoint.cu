@@ -62,21 +62,18 @@ struct AdjState {
 // the momentum and stress adjoints, lambda g_l (= -G rho_l lambda F_l, which
 // inherits b_l / 2) for the adjoint of psi. Stored in float32 they cost a
 // weakly coupled gradient (G or delta_rho in a dilute mixture) 1e-3 to 5e-2
-// relative accuracy within tens of steps. So every adjoint field is FP64
-// (lam_t, aux_t) and the large parts enter exactly; only the neighbour
-// differences (a(x+c_i) - a(x)) + c_i . (b(x+c_i) - b(x)) go through the
-// float32 mode projection and collision transpose (adj_modes), the large
-// part through adj_modes_ab in FP64.
-#ifndef FLBM_ADJ_AUX
-#define FLBM_ADJ_AUX double
-#endif
-using aux_t = FLBM_ADJ_AUX;
-
-// The (a_l, b_l) fields are stored as two floats, v = hi + lo with
-// lo = fl(v - hi): 48 significant bits. A node reads its own values as FP64
-// (sval) and forms its neighbours' differences in float from the two parts
-// (sdiff; the high parts of close values subtract exactly), so the stencil
-// loop of the node adjoint needs no FP64 arithmetic, which is scarce here.
+// relative accuracy within tens of steps. So these fields keep 48 significant
+// bits and the large parts enter in FP64; only the neighbour differences
+// (a(x+c_i) - a(x)) + c_i . (b(x+c_i) - b(x)) go through the float32 mode
+// projection and collision transpose (adj_modes), the large part through
+// adj_modes_ab in FP64. The adjoint of psi at particle nodes and wall ghosts
+// (lpsi) is FP64.
+//
+// The 48-bit fields are stored as two floats, v = hi + lo with
+// lo = fl(v - hi). A node reads its own values as FP64 (sval) and forms its
+// neighbours' differences in float from the two parts (sdiff; the high parts
+// of close values subtract exactly), so the stencil loops need no FP64
+// arithmetic, which is scarce on this GPU.
 struct __align__(8) Split {
     float hi, lo;
 };
@@ -87,7 +84,8 @@ __device__ __forceinline__ Split ssplit(double v)
     return Split{h, (float)(v - (double)h)};
 }
 __device__ __forceinline__ float sdiff(Split a, Split b) { return (a.hi - b.hi) + (a.lo - b.lo); }
-using lam_t = Split;
+using lam_t = Split;  // a_l, b_l: 8 per node
+using lg_t = Split;   // lambda g_l: 6 per node
 
 constexpr int kT = 256;  // threads per block
 
@@ -458,7 +456,7 @@ static __global__ void ka_update(AdjState* __restrict__ a, const double* __restr
 template <bool PARTICLE>
 __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty, const float* __restrict__ tape,
                                          const float* __restrict__ psi, const lam_t* __restrict__ lam1,
-                                         lam_t* __restrict__ lam0, aux_t* __restrict__ lg,
+                                         lam_t* __restrict__ lam0, lg_t* __restrict__ lg,
                                          const DevState* __restrict__ s0, const uint8_t* __restrict__ mk0,
                                          const AdjState* __restrict__ adj, double* __restrict__ parts,
                                          const KParams& P)
@@ -477,7 +475,7 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
         const uint32_t n = lin(x, y, z, P);
         if (PARTICLE && solid_at(x, y, z, s0, m0, P)) {
             for (int k = 0; k < 8; ++k) lam0[k * N + n] = Split{0.0f, 0.0f};
-            for (int k = 0; k < 6; ++k) lg[k * N + n] = 0.0f;
+            for (int k = 0; k < 6; ++k) lg[k * N + n] = Split{0.0f, 0.0f};
         } else {
             float rho[2], j[2][3], g[2][3];
             for (int l = 0; l < 2; ++l) {
@@ -638,7 +636,7 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                 lam0[(size_t)l * N + n] = ssplit(lrd[l] + (double)lrho[l] + lrx[l]);
                 for (int a = 0; a < 3; ++a) {
                     lam0[(size_t)(2 + 3 * l + a) * N + n] = ssplit(ljd[l][a] + (double)lj[l][a]);
-                    lg[(size_t)(3 * l + a) * N + n] = (aux_t)(lgd[l][a] + (double)lgv[l][a]);
+                    lg[(size_t)(3 * l + a) * N + n] = ssplit(lgd[l][a] + (double)lgv[l][a]);
                 }
             }
         }
@@ -663,7 +661,7 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
 // Tiles away from the particle (all tiles when there is none).
 static __global__ void __launch_bounds__(kT, 2) ka_node_bulk(const float* __restrict__ tape, const float* __restrict__ psi,
                                                           const lam_t* __restrict__ lam1, lam_t* __restrict__ lam0,
-                                                          aux_t* __restrict__ lg, const DevState* __restrict__ s0,
+                                                          lg_t* __restrict__ lg, const DevState* __restrict__ s0,
                                                           const uint8_t* __restrict__ mk0,
                                                           const AdjState* __restrict__ adj, double* __restrict__ parts,
                                                           KParams P)
@@ -679,7 +677,7 @@ static __global__ void __launch_bounds__(kT, 2) ka_node_bulk(const float* __rest
 // Tiles near the particle: the candidate grid of the forward step.
 static __global__ void __launch_bounds__(kT) ka_node_near(const float* __restrict__ tape, const float* __restrict__ psi,
                                                           const lam_t* __restrict__ lam1, lam_t* __restrict__ lam0,
-                                                          aux_t* __restrict__ lg, const DevState* __restrict__ s0,
+                                                          lg_t* __restrict__ lg, const DevState* __restrict__ s0,
                                                           const uint8_t* __restrict__ mk0,
                                                           const AdjState* __restrict__ adj, double* __restrict__ parts,
                                                           KParams P)
@@ -707,20 +705,81 @@ __device__ __forceinline__ int fluid_count(const int q[3], const DevState* s0, c
 }
 
 // lambda psi_l at padded point p (in range on every periodic axis): the
-// Shan-Chen stencil transposed, g_A reads psi_B and g_B reads psi_A.
-__device__ __forceinline__ void lpsi_gather(const int p[3], const aux_t* __restrict__ lg, const KParams& P, aux_t out[2])
+// Shan-Chen stencil transposed, g_A reads psi_B and g_B reads psi_A. Sources
+// whose lambda g is zero (particle nodes) add nothing and are skipped. The
+// others are taken as float differences from the first of them (r) plus
+// r sum w_i c_i over them in FP64, where sum w_i c_i = (2 n_axis + n_diag) / 36
+// per axis from the integer sums of c_i over the included axis and diagonal
+// directions (zero when every source is included).
+__device__ __forceinline__ void lpsi_gather(const int p[3], const lg_t* __restrict__ lg, const KParams& P,
+                                            double out[2])
 {
     const size_t N = P.N;
-    aux_t la = aux_t(0), lb = aux_t(0);
+    Split r[6];
+    bool have = false;
+    int nc[3] = {0, 0, 0};  // 2 sum c over included axis directions + sum c over diagonal ones
+    float la = 0.0f, lb = 0.0f;
     for (int i = 1; i < 19; ++i) {
         int x[3];
         if (!nbr(p[0], p[1], p[2], -cxv(i), -cyv(i), -czv(i), P, x)) continue;
         // a source outside the domain (p is a ghost and -c_i points further out) is skipped by nbr()
         const uint32_t s = lin(x[0], x[1], x[2], P);
-        const aux_t w = wv(i);
-        const aux_t cx = cxv(i), cy = cyv(i), cz = czv(i);
-        lb += w * (cx * lg[0 * N + s] + cy * lg[1 * N + s] + cz * lg[2 * N + s]);
-        la += w * (cx * lg[3 * N + s] + cy * lg[4 * N + s] + cz * lg[5 * N + s]);
+        Split v[6];
+        bool zero = true;
+        for (int k = 0; k < 6; ++k) {
+            v[k] = lg[k * N + s];
+            zero = zero && v[k].hi == 0.0f && v[k].lo == 0.0f;
+        }
+        if (zero) continue;
+        if (!have) {
+            for (int k = 0; k < 6; ++k) r[k] = v[k];
+            have = true;
+        }
+        const int c[3] = {cxv(i), cyv(i), czv(i)};
+        const int wt = i <= 6 ? 2 : 1;  // w_i in units of 1/36
+        const float w = wv(i);
+        for (int a = 0; a < 3; ++a) {
+            if (!c[a]) continue;
+            nc[a] += wt * c[a];
+            lb += w * c[a] * sdiff(v[a], r[a]);
+            la += w * c[a] * sdiff(v[3 + a], r[3 + a]);
+        }
+    }
+    double da = la, db = lb;
+    if (have)
+        for (int a = 0; a < 3; ++a)
+            if (nc[a]) {
+                db += sval(r[a]) * (nc[a] * (1.0 / 36.0));
+                da += sval(r[3 + a]) * (nc[a] * (1.0 / 36.0));
+            }
+    out[0] = da;
+    out[1] = db;
+}
+
+// lpsi_gather at fluid node n = (x, y, z) whose 18 neighbours are fluid nodes
+// of the domain. Then sum_i w_i c_i = 0 over the sources, so the stencil is
+// taken on the differences from the node's own lambda g_l, in float.
+__device__ __forceinline__ void lpsi_gather_inner(int x, int y, int z, uint32_t n, const lg_t* __restrict__ lg,
+                                                  const KParams& P, double out[2])
+{
+    const size_t N = P.N;
+    Split r[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r[k] = lg[k * N + n];
+    float la = 0.0f, lb = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        int q[3];
+        nbr(x, y, z, -cxv(i), -cyv(i), -czv(i), P, q);  // in the domain: the caller checked
+        const uint32_t s = lin(q[0], q[1], q[2], P);
+        const float w = wv(i);
+        const int cx = cxv(i), cy = cyv(i), cz = czv(i);
+        float tb = 0.0f, ta = 0.0f;
+        if (cx) { tb += cx * sdiff(lg[0 * N + s], r[0]); ta += cx * sdiff(lg[3 * N + s], r[3]); }
+        if (cy) { tb += cy * sdiff(lg[1 * N + s], r[1]); ta += cy * sdiff(lg[4 * N + s], r[4]); }
+        if (cz) { tb += cz * sdiff(lg[2 * N + s], r[2]); ta += cz * sdiff(lg[5 * N + s], r[5]); }
+        lb += w * tb;
+        la += w * ta;
     }
     out[0] = la;
     out[1] = lb;
@@ -733,8 +792,8 @@ __device__ __forceinline__ void lpsi_gather(const int p[3], const aux_t* __restr
 // mu_l = lambda psi_l / cnt where the clip at 0 is inactive, written at the
 // node's place in lpsi; dJ/d delta_rho partial per block.
 // ---------------------------------------------------------------------------
-static __global__ void __launch_bounds__(kT) ka_lpsi(const aux_t* __restrict__ lg, const float* __restrict__ psi,
-                                                     aux_t* __restrict__ lpsi, const DevState* __restrict__ s0,
+static __global__ void __launch_bounds__(kT) ka_lpsi(const lg_t* __restrict__ lg, const float* __restrict__ psi,
+                                                     double* __restrict__ lpsi, const DevState* __restrict__ s0,
                                                      const uint8_t* __restrict__ mk0, const AdjState* __restrict__ adj,
                                                      double* __restrict__ parts2, KParams P)
 {
@@ -753,12 +812,12 @@ static __global__ void __launch_bounds__(kT) ka_lpsi(const aux_t* __restrict__ l
             if (!P.wall[a] && p[a] >= L[a]) p[a] -= L[a];
         }
         const int x = p[0], y = p[1], z = p[2];
-        aux_t lp[2];
+        double lp[2];
         lpsi_gather(p, lg, P, lp);
         const long long pi = pad_index(x, y, z, P);
         {
             const int cnt = fluid_count(p, s0, m0, P);
-            aux_t mu[2] = {aux_t(0), aux_t(0)};
+            double mu[2] = {0.0, 0.0};
             if (cnt) {
                 const float* lF = adj->lFf;
                 const float* lT = adj->lTf;
@@ -778,12 +837,12 @@ static __global__ void __launch_bounds__(kT) ka_lpsi(const aux_t* __restrict__ l
                                       cy * (lF[1] + lT[2] * d[0] - lT[0] * d[2]) +
                                       cz * (lF[2] + lT[0] * d[1] - lT[1] * d[0]);
                     const long long qi = pad_index(q[0], q[1], q[2], P);
-                    lp[1] += aux_t(kap * P.G * wv(i) * psi[qi]);           // d/d psiB(p) of rhoA(q) psiB(p)
-                    lp[0] += aux_t(kap * P.G * wv(i) * psi[P.padn + qi]);  // d/d psiA(p) of rhoB(q) psiA(p)
+                    lp[1] += double(kap * P.G * wv(i) * psi[qi]);           // d/d psiB(p) of rhoA(q) psiB(p)
+                    lp[0] += double(kap * P.G * wv(i) * psi[P.padn + qi]);  // d/d psiA(p) of rhoB(q) psiA(p)
                 }
                 const bool actA = psi[pi] > 0.0f, actB = psi[P.padn + pi] > 0.0f;
-                if (actA) { mu[0] = lp[0] / aux_t(cnt); dd += lp[0]; }
-                if (actB) { mu[1] = lp[1] / aux_t(cnt); dd -= lp[1]; }
+                if (actA) { mu[0] = lp[0] / double(cnt); dd += lp[0]; }
+                if (actB) { mu[1] = lp[1] / double(cnt); dd -= lp[1]; }
             }
             lpsi[pi] = mu[0];
             lpsi[P.padn + pi] = mu[1];
@@ -796,7 +855,7 @@ static __global__ void __launch_bounds__(kT) ka_lpsi(const aux_t* __restrict__ l
 
 // Wall ghosts of the psi shell (points outside along a wall axis, in range on
 // the periodic axes): mu_l = lambda psi_l / cnt, the mean over fluid neighbours.
-static __global__ void __launch_bounds__(kT) ka_lpsi_shell(const aux_t* __restrict__ lg, aux_t* __restrict__ lpsi,
+static __global__ void __launch_bounds__(kT) ka_lpsi_shell(const lg_t* __restrict__ lg, double* __restrict__ lpsi,
                                                            const DevState* __restrict__ s0,
                                                            const uint8_t* __restrict__ mk0, KParams P)
 {
@@ -831,19 +890,19 @@ static __global__ void __launch_bounds__(kT) ka_lpsi_shell(const aux_t* __restri
     }
     if (!ghost) return;
     const uint8_t* m0 = cur_mask(s0, mk0, P);
-    aux_t lp[2];
+    double lp[2];
     lpsi_gather(p, lg, P, lp);
     const int cnt = fluid_count(p, s0, m0, P);
     const long long dst = (long long)(p[0] + 1) + (long long)P.px * ((p[1] + 1) + (long long)P.py * (p[2] + 1));
-    lpsi[dst] = cnt ? lp[0] / aux_t(cnt) : aux_t(0);
-    lpsi[P.padn + dst] = cnt ? lp[1] / aux_t(cnt) : aux_t(0);
+    lpsi[dst] = cnt ? lp[0] / double(cnt) : 0.0;
+    lpsi[P.padn + dst] = cnt ? lp[1] / double(cnt) : 0.0;
 }
 
 // a_l of fluid nodes: lambda psi of the node (the Shan-Chen stencil
 // transposed) plus mu of every particle node and wall ghost among its
 // neighbours (each averaged this node's density).
-static __global__ void __launch_bounds__(kT) ka_final(lam_t* __restrict__ lam0, const aux_t* __restrict__ lg,
-                                                      const aux_t* __restrict__ lpsi, const DevState* __restrict__ s0,
+static __global__ void __launch_bounds__(kT) ka_final(lam_t* __restrict__ lam0, const lg_t* __restrict__ lg,
+                                                      const double* __restrict__ lpsi, const DevState* __restrict__ s0,
                                                       const uint8_t* __restrict__ mk0, KParams P)
 {
     const int x = blockIdx.x * P.tx + threadIdx.x;
@@ -852,9 +911,12 @@ static __global__ void __launch_bounds__(kT) ka_final(lam_t* __restrict__ lam0, 
     if (x >= P.lx || y >= P.ly) return;
     const uint8_t* m0 = cur_mask(s0, mk0, P);
     if (solid_at(x, y, z, s0, m0, P)) return;
-    const int p[3] = {x, y, z};
-    aux_t add[2];
-    lpsi_gather(p, lg, P, add);  // psi = rho on this fluid node
+    const uint32_t n = lin(x, y, z, P);
+    // Particle nodes and wall ghosts among the neighbours: their mu, and
+    // whether the stencil of this node meets any (the neighbours of a node
+    // are its own sources, -c_i running over the same 18 directions).
+    double add[2] = {0.0, 0.0};
+    bool edge = false;
     const int L[3] = {P.lx, P.ly, P.lz};
     for (int i = 1; i < 19; ++i) {
         int r[3] = {x + cxv(i), y + cyv(i), z + czv(i)};
@@ -866,13 +928,22 @@ static __global__ void __launch_bounds__(kT) ka_final(lam_t* __restrict__ lam0, 
             }
         }
         if (!ghost && !solid_at(r[0], r[1], r[2], s0, m0, P)) continue;
+        edge = true;
         const long long q = (long long)(r[0] + 1) + (long long)P.px * ((r[1] + 1) + (long long)P.py * (r[2] + 1));
         add[0] += lpsi[q];
         add[1] += lpsi[P.padn + q];
     }
-    const uint32_t n = lin(x, y, z, P);
-    lam0[n] = ssplit(sval(lam0[n]) + (double)add[0]);
-    lam0[P.N + n] = ssplit(sval(lam0[P.N + n]) + (double)add[1]);
+    double g[2];  // psi = rho on this fluid node
+    if (edge) {
+        const int p[3] = {x, y, z};
+        lpsi_gather(p, lg, P, g);
+    } else {
+        lpsi_gather_inner(x, y, z, n, lg, P, g);
+    }
+    add[0] += g[0];
+    add[1] += g[1];
+    lam0[n] = ssplit(sval(lam0[n]) + add[0]);
+    lam0[P.N + n] = ssplit(sval(lam0[P.N + n]) + add[1]);
 }
 
 // Per-tile partials -> adjoint of step n's particle state and the gradient
@@ -924,8 +995,8 @@ struct AdjBuffers {
     DevState* tape_st = nullptr;
     uint8_t* tape_m = nullptr;
     lam_t* lam[2] = {nullptr, nullptr};
-    aux_t* lgf = nullptr;
-    aux_t* lpsi = nullptr;
+    lg_t* lgf = nullptr;
+    double* lpsi = nullptr;
     double* uv = nullptr;
     double* parts = nullptr;
     double* parts2 = nullptr;
@@ -1051,7 +1122,7 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
     cudaStream_t st = h->stream;
     ACK(h, cudaMemsetAsync(b.adj, 0, sizeof(AdjState), st));
     ACK(h, cudaMemsetAsync(b.lam[0], 0, sizeof(lam_t) * 8 * N, st));
-    ACK(h, cudaMemsetAsync(b.lpsi, 0, sizeof(aux_t) * 2 * k.padn, st));
+    ACK(h, cudaMemsetAsync(b.lpsi, 0, sizeof(double) * 2 * k.padn, st));
     cudaEvent_t ev[3];
     for (auto& e : ev) ACK(h, cudaEventCreate(&e));
     struct EvGuard {
