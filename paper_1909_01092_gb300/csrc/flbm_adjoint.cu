@@ -42,6 +42,7 @@
 
 #include "flbm.h"
 #include "flbm_adjoint_math.h"
+#include "flbm_df.h"
 #include "flbm_sim.cuh"
 
 using namespace flbm;
@@ -529,17 +530,16 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
             const float* lF = adj->lFf;
             const float* lT = adj->lTf;
             double lrx[2] = {0.0, 0.0};  // extra adjoint of rho_l from links and the reaction
-            double axd[2], bxd[2][3];      // a_l, b_l of this node (FP64)
+            Split asv[2], bsv[2][3];         // a_l, b_l of this node
             float lm[2][10];               // mode adjoint of the neighbour differences
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
                 const Split as = lam1[(size_t)l * N + n];
                 Split bs[3];
                 for (int a = 0; a < 3; ++a) bs[a] = lam1[(size_t)(2 + 3 * l + a) * N + n];
-                axd[l] = sval(as);
-                for (int a = 0; a < 3; ++a) bxd[l][a] = sval(bs[a]);
-                const double ax = axd[l];
-                const double* bx = bxd[l];
+                asv[l] = as;
+                for (int a = 0; a < 3; ++a) bsv[l][a] = bs[a];
+                const double ax = sval(as);
                 float wl[19];
                 float wsum = 0.0f;
 #pragma unroll
@@ -548,7 +548,7 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                     // dv = lambda f*_li - a_l(x) - c_i . b_l(x): small, float32 is enough.
                     float dv;
                     if ((wall_nb | solid_nb) >> i & 1u) {
-                        const double cb = cx * bx[0] + cy * bx[1] + cz * bx[2];
+                        const double cb = cx * sval(bs[0]) + cy * sval(bs[1]) + cz * sval(bs[2]);
                         dv = (float)(-2.0 * cb);  // bounce-back reads (x, -c_i): a - c_i . b
                         if (PARTICLE && (solid_nb >> i & 1u)) {
                             const float d[3] = {rnf[0] + 0.5f * cx, rnf[1] + 0.5f * cy, rnf[2] + 0.5f * cz};
@@ -618,25 +618,55 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                 }
             }
             // Transpose of the collision: the float32 part from the differences, the
-            // FP64 part from (a_l, b_l) of this node (modes 0..3 only).
+            // 48-bit part from (a_l, b_l) of this node (modes 0..3 only).
             float lrho[2], lj[2][3], lgv[2][3], lG;
             adj_modes<float>(rho, j, g, ext, P.G, lm, lrho, lj, lgv, lG);
-            double rd[2], jd[2][3], gd[2][3], ed[3], lrd[2], ljd[2][3], lgd[2][3], lGd;
-            for (int l = 0; l < 2; ++l) {
-                rd[l] = rho[l];
-                for (int a = 0; a < 3; ++a) {
-                    jd[l][a] = j[l][a];
-                    gd[l][a] = g[l][a];
+            if constexpr (PARTICLE) {
+                // FP64, with the link terms lrx.
+                double rd[2], jd[2][3], gd[2][3], ed[3], axd[2], bxd[2][3], lrd[2], ljd[2][3], lgd[2][3], lGd;
+                for (int l = 0; l < 2; ++l) {
+                    rd[l] = rho[l];
+                    axd[l] = sval(asv[l]);
+                    for (int a = 0; a < 3; ++a) {
+                        jd[l][a] = j[l][a];
+                        gd[l][a] = g[l][a];
+                        bxd[l][a] = sval(bsv[l][a]);
+                    }
                 }
-            }
-            for (int a = 0; a < 3; ++a) ed[a] = ext[a];
-            adj_modes_ab<double>(rd, jd, gd, ed, (double)P.G, axd, bxd, lrd, ljd, lgd, lGd);
-            acc[9] += lGd + (double)lG;
-            for (int l = 0; l < 2; ++l) {
-                lam0[(size_t)l * N + n] = ssplit(lrd[l] + (double)lrho[l] + lrx[l]);
-                for (int a = 0; a < 3; ++a) {
-                    lam0[(size_t)(2 + 3 * l + a) * N + n] = ssplit(ljd[l][a] + (double)lj[l][a]);
-                    lg[(size_t)(3 * l + a) * N + n] = ssplit(lgd[l][a] + (double)lgv[l][a]);
+                for (int a = 0; a < 3; ++a) ed[a] = ext[a];
+                adj_modes_ab<double>(rd, jd, gd, ed, (double)P.G, axd, bxd, lrd, ljd, lgd, lGd);
+                acc[9] += lGd + (double)lG;
+                for (int l = 0; l < 2; ++l) {
+                    lam0[(size_t)l * N + n] = ssplit(lrd[l] + (double)lrho[l] + lrx[l]);
+                    for (int a = 0; a < 3; ++a) {
+                        lam0[(size_t)(2 + 3 * l + a) * N + n] = ssplit(ljd[l][a] + (double)lj[l][a]);
+                        lg[(size_t)(3 * l + a) * N + n] = ssplit(lgd[l][a] + (double)lgv[l][a]);
+                    }
+                }
+            } else {
+                // Double-float: the inputs are floats, (a_l, b_l) are stored as pairs.
+                df rf[2], jf[2][3], gf[2][3], ef[3], af[2], bf[2][3], lrf[2], ljf[2][3], lgf[2][3], lGf;
+                for (int l = 0; l < 2; ++l) {
+                    rf[l] = df(rho[l]);
+                    af[l] = df(asv[l].hi, asv[l].lo);
+                    for (int a = 0; a < 3; ++a) {
+                        jf[l][a] = df(j[l][a]);
+                        gf[l][a] = df(g[l][a]);
+                        bf[l][a] = df(bsv[l][a].hi, bsv[l][a].lo);
+                    }
+                }
+                for (int a = 0; a < 3; ++a) ef[a] = df(ext[a]);
+                adj_modes_ab<df>(rf, jf, gf, ef, df(P.G), af, bf, lrf, ljf, lgf, lGf);
+                acc[9] += lGf.value() + (double)lG;
+                for (int l = 0; l < 2; ++l) {
+                    const df v = lrf[l] + df(lrho[l]);
+                    lam0[(size_t)l * N + n] = Split{v.hi, v.lo};
+                    for (int a = 0; a < 3; ++a) {
+                        const df vj = ljf[l][a] + df(lj[l][a]);
+                        const df vg = lgf[l][a] + df(lgv[l][a]);
+                        lam0[(size_t)(2 + 3 * l + a) * N + n] = Split{vj.hi, vj.lo};
+                        lg[(size_t)(3 * l + a) * N + n] = Split{vg.hi, vg.lo};
+                    }
                 }
             }
         }

@@ -2,7 +2,11 @@
 (paper_1909_01092_gb300/csrc/flbm_adjoint_math.h): adj_modes must be the
 transpose of the Jacobian of fwd_modes. Compiled here with g++ in double
 precision; checked against central finite differences of fwd_modes through
-the identity <lambda, J v> = <J^T lambda, v> for random lambda and v."""
+the identity <lambda, J v> = <J^T lambda, v> for random lambda and v.
+
+Also the double-float arithmetic (csrc/flbm_df.h) the adjoint uses for its
+large parts: each operation against exact rational arithmetic, and
+adj_modes_ab evaluated in it against the double evaluation."""
 import ctypes
 import os
 import shutil
@@ -16,6 +20,26 @@ CSRC = os.path.join(os.path.dirname(HERE), "paper_1909_01092_gb300", "csrc")
 
 SHIM = r"""
 #include "flbm_adjoint_math.h"
+#include "flbm_df.h"
+extern "C" void df_op(int op, const float* a, const float* b, float* out) {
+    const flbm::df x(a[0], a[1]), y(b[0], b[1]);
+    const flbm::df r = op == 0 ? x + y : op == 1 ? x - y : op == 2 ? x * y : x / y;
+    out[0] = r.hi; out[1] = r.lo;
+}
+extern "C" void adj_ab_df(const double* in, double G, const double* ab, double* out) {
+    using flbm::df;
+    const df rho[2] = {df(in[0]), df(in[1])};
+    const df j[2][3] = {{df(in[2]), df(in[3]), df(in[4])}, {df(in[5]), df(in[6]), df(in[7])}};
+    const df g[2][3] = {{df(in[8]), df(in[9]), df(in[10])}, {df(in[11]), df(in[12]), df(in[13])}};
+    const df ext[3] = {df(in[14]), df(in[15]), df(in[16])};
+    const df a[2] = {df(ab[0]), df(ab[1])};
+    const df b[2][3] = {{df(ab[2]), df(ab[3]), df(ab[4])}, {df(ab[5]), df(ab[6]), df(ab[7])}};
+    df lrho[2], lj[2][3], lg[2][3], lG;
+    flbm::adj_modes_ab<df>(rho, j, g, ext, df(G), a, b, lrho, lj, lg, lG);
+    out[0] = lrho[0].value(); out[1] = lrho[1].value();
+    for (int l = 0; l < 2; ++l) for (int c = 0; c < 3; ++c) { out[2 + 3 * l + c] = lj[l][c].value(); out[8 + 3 * l + c] = lg[l][c].value(); }
+    out[14] = lG.value();
+}
 extern "C" void fwd(const double* in, double G, double* ms) {
     const double rho[2] = {in[0], in[1]};
     const double j[2][3] = {{in[2], in[3], in[4]}, {in[5], in[6], in[7]}};
@@ -68,6 +92,9 @@ def shim(tmp_path_factory):
     L.fwd.argtypes = [dp, ctypes.c_double, dp]
     L.adj.argtypes = [dp, ctypes.c_double, dp, dp]
     L.adj_ab.argtypes = [dp, ctypes.c_double, dp, dp]
+    L.adj_ab_df.argtypes = [dp, ctypes.c_double, dp, dp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.df_op.argtypes = [ctypes.c_int, fp, fp, fp]
     return L
 
 
@@ -125,3 +152,50 @@ def test_density_momentum_part_equals_the_general_transpose(shim, seed):
     shim.adj(_p(x), 1.3, _p(lm), _p(o1))
     shim.adj_ab(_p(x), 1.3, _p(ab), _p(o2))
     assert np.allclose(o1, o2, rtol=1e-13, atol=1e-15)
+
+
+def _split(v):
+    hi = np.float32(v)
+    return np.array([hi, np.float32(v - float(hi))], dtype=np.float32)
+
+
+@pytest.mark.parametrize("op", range(4))
+def test_double_float_operations_against_exact_arithmetic(shim, op):
+    """Sum, difference, product and quotient of double-float numbers agree
+    with the exact rational result of the represented values to 2^-44
+    relative (about 48-bit operands)."""
+    from fractions import Fraction
+
+    rng = np.random.default_rng(7 + op)
+    fp = ctypes.POINTER(ctypes.c_float)
+    worst = 0.0
+    for _ in range(2000):
+        a = _split(rng.standard_normal() * 10.0 ** rng.integers(-3, 4))
+        b = _split(rng.standard_normal() * 10.0 ** rng.integers(-3, 4))
+        if op == 1:  # differences of close numbers: the adjoint's use
+            b = _split(float(a[0]) * (1 + 1e-3 * rng.standard_normal()))
+        out = np.zeros(2, dtype=np.float32)
+        shim.df_op(op, a.ctypes.data_as(fp), b.ctypes.data_as(fp), out.ctypes.data_as(fp))
+        fa = Fraction(float(a[0])) + Fraction(float(a[1]))
+        fb = Fraction(float(b[0])) + Fraction(float(b[1]))
+        exact = [fa + fb, fa - fb, fa * fb, fa / fb][op]
+        got = Fraction(float(out[0])) + Fraction(float(out[1]))
+        scale = [max(abs(fa), abs(fb)), max(abs(fa), abs(fb)), abs(exact), abs(exact)][op]
+        worst = max(worst, float(abs(got - exact) / scale))
+    assert worst <= 2.0 ** -44, worst
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_density_momentum_part_in_double_float(shim, seed):
+    """adj_modes_ab in double-float arithmetic equals its double evaluation to
+    1e-12 of the largest adjoint input (the large parts it carries)."""
+    rng = np.random.default_rng(200 + seed)
+    x = np.concatenate([[1.0 + 0.05 * rng.standard_normal(), 0.05 + 0.01 * rng.standard_normal()],
+                        0.02 * rng.standard_normal(6), 0.1 * rng.standard_normal(6), 1e-4 * rng.standard_normal(3)])
+    x = np.array([float(np.float32(v)) for v in x])  # the kernels' inputs are float
+    ab = 1e3 * (1.0 + 0.01 * rng.standard_normal(8))
+    o1, o2 = np.zeros(15), np.zeros(15)
+    G = float(np.float32(1.2))
+    shim.adj_ab(_p(x), G, _p(ab), _p(o1))
+    shim.adj_ab_df(_p(x), G, _p(ab), _p(o2))
+    assert np.max(np.abs(o1 - o2)) <= 1e-12 * np.max(np.abs(ab)), np.max(np.abs(o1 - o2))
