@@ -621,29 +621,7 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
             // 48-bit part from (a_l, b_l) of this node (modes 0..3 only).
             float lrho[2], lj[2][3], lgv[2][3], lG;
             adj_modes<float>(rho, j, g, ext, P.G, lm, lrho, lj, lgv, lG);
-            if constexpr (PARTICLE) {
-                // FP64, with the link terms lrx.
-                double rd[2], jd[2][3], gd[2][3], ed[3], axd[2], bxd[2][3], lrd[2], ljd[2][3], lgd[2][3], lGd;
-                for (int l = 0; l < 2; ++l) {
-                    rd[l] = rho[l];
-                    axd[l] = sval(asv[l]);
-                    for (int a = 0; a < 3; ++a) {
-                        jd[l][a] = j[l][a];
-                        gd[l][a] = g[l][a];
-                        bxd[l][a] = sval(bsv[l][a]);
-                    }
-                }
-                for (int a = 0; a < 3; ++a) ed[a] = ext[a];
-                adj_modes_ab<double>(rd, jd, gd, ed, (double)P.G, axd, bxd, lrd, ljd, lgd, lGd);
-                acc[9] += lGd + (double)lG;
-                for (int l = 0; l < 2; ++l) {
-                    lam0[(size_t)l * N + n] = ssplit(lrd[l] + (double)lrho[l] + lrx[l]);
-                    for (int a = 0; a < 3; ++a) {
-                        lam0[(size_t)(2 + 3 * l + a) * N + n] = ssplit(ljd[l][a] + (double)lj[l][a]);
-                        lg[(size_t)(3 * l + a) * N + n] = ssplit(lgd[l][a] + (double)lgv[l][a]);
-                    }
-                }
-            } else {
+            {
                 // Double-float: the inputs are floats, (a_l, b_l) are stored as pairs.
                 df rf[2], jf[2][3], gf[2][3], ef[3], af[2], bf[2][3], lrf[2], ljf[2][3], lgf[2][3], lGf;
                 for (int l = 0; l < 2; ++l) {
@@ -659,7 +637,8 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                 adj_modes_ab<df>(rf, jf, gf, ef, df(P.G), af, bf, lrf, ljf, lgf, lGf);
                 acc[9] += lGf.value() + (double)lG;
                 for (int l = 0; l < 2; ++l) {
-                    const df v = lrf[l] + df(lrho[l]);
+                    df v = lrf[l] + df(lrho[l]);
+                    if (PARTICLE) v = v + df(lrx[l]);  // link and reaction terms (FP64 sums)
                     lam0[(size_t)l * N + n] = Split{v.hi, v.lo};
                     for (int a = 0; a < 3; ++a) {
                         const df vj = ljf[l][a] + df(lj[l][a]);
@@ -790,7 +769,7 @@ __device__ __forceinline__ void lpsi_gather(const int p[3], const lg_t* __restri
 // of the domain. Then sum_i w_i c_i = 0 over the sources, so the stencil is
 // taken on the differences from the node's own lambda g_l, in float.
 __device__ __forceinline__ void lpsi_gather_inner(int x, int y, int z, uint32_t n, const lg_t* __restrict__ lg,
-                                                  const KParams& P, double out[2])
+                                                  const KParams& P, float out[2])
 {
     const size_t N = P.N;
     Split r[6];
@@ -963,17 +942,22 @@ static __global__ void __launch_bounds__(kT) ka_final(lam_t* __restrict__ lam0, 
         add[0] += lpsi[q];
         add[1] += lpsi[P.padn + q];
     }
-    double g[2];  // psi = rho on this fluid node
+    // psi = rho on this fluid node
     if (edge) {
         const int p[3] = {x, y, z};
+        double g[2];
         lpsi_gather(p, lg, P, g);
+        lam0[n] = ssplit(sval(lam0[n]) + (add[0] + g[0]));
+        lam0[P.N + n] = ssplit(sval(lam0[P.N + n]) + (add[1] + g[1]));
     } else {
+        float g[2];
         lpsi_gather_inner(x, y, z, n, lg, P, g);
+        for (int c = 0; c < 2; ++c) {
+            const Split o = lam0[c * P.N + n];
+            const df v = df(o.hi, o.lo) + df(g[c]);
+            lam0[c * P.N + n] = Split{v.hi, v.lo};
+        }
     }
-    add[0] += g[0];
-    add[1] += g[1];
-    lam0[n] = ssplit(sval(lam0[n]) + add[0]);
-    lam0[P.N + n] = ssplit(sval(lam0[P.N + n]) + add[1]);
 }
 
 // Per-tile partials -> adjoint of step n's particle state and the gradient
