@@ -548,9 +548,10 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                     // dv = lambda f*_li - a_l(x) - c_i . b_l(x): small, float32 is enough.
                     float dv;
                     if ((wall_nb | solid_nb) >> i & 1u) {
-                        const double cb = cx * sval(bs[0]) + cy * sval(bs[1]) + cz * sval(bs[2]);
-                        dv = (float)(-2.0 * cb);  // bounce-back reads (x, -c_i): a - c_i . b
+                        // bounce-back reads (x, -c_i): a - c_i . b, so dv = -2 c_i . b (float)
+                        dv = -2.0f * (cx * bs[0].hi + cy * bs[1].hi + cz * bs[2].hi);
                         if (PARTICLE && (solid_nb >> i & 1u)) {
+                            const double cb = cx * sval(bs[0]) + cy * sval(bs[1]) + cz * sval(bs[2]);
                             const float d[3] = {rnf[0] + 0.5f * cx, rnf[1] + 0.5f * cy, rnf[2] + 0.5f * cz};
                             const float kap = cx * (lF[0] + lT[1] * d[2] - lT[2] * d[1]) +
                                               cy * (lF[1] + lT[2] * d[0] - lT[0] * d[2]) +
