@@ -22,7 +22,7 @@
 //   ka_cover     adjoint of cover/uncover at the new position
 //   ka_cover_mean  uncovered nodes' neighbour means -> a_l of those neighbours
 //   ka_update    leap-frog Newton-Euler update (FP64), dJ/dg
-//   ka_psi_tape, k_virtual, k_shell   density field of the step from the tape
+//   ka_psi_tape, k_shell_virtual  density field of the step from the tape
 //   ka_node_bulk, ka_node_near  streaming (pull of the adjoint), moving
 //                links, Shan-Chen reaction, collision (flbm_adjoint_math.h)
 //                per fluid node; tiles away from / near the particle
@@ -414,7 +414,8 @@ static __global__ void __launch_bounds__(kT) ka_cover_mean(lam_t* __restrict__ l
 }
 
 // ---------------------------------------------------------------------------
-// Leap-frog update adjoint (FP64, one thread): V' = V + (F + F_p z)/m_p,
+// Leap-frog update adjoint (FP64, one warp: lane k < 9 sums partial k over
+// the box blocks in order, lane 0 updates): V' = V + (F + F_p z)/m_p,
 // X' = X + V', Omega' = Omega + T/I_p, plus the two halves of Vavg in J.
 // On exit lX, lV, lOm, lP, lL hold the adjoint of step n's input state
 // without the link terms ka_node adds; dJ/dg accumulates.
@@ -422,9 +423,14 @@ static __global__ void __launch_bounds__(kT) ka_cover_mean(lam_t* __restrict__ l
 static __global__ void ka_update(AdjState* __restrict__ a, const double* __restrict__ parts, int nblocks,
                                  const DevState* __restrict__ s0, double inv2T, double dFp_dg)
 {
-    double c[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int b = 0; b < nblocks; ++b)
-        for (int k = 0; k < 9; ++k) c[k] += parts[b * 9 + k];
+    __shared__ double c[9];
+    if (threadIdx.x < 9) {
+        double sum = 0.0;
+        for (int b = 0; b < nblocks; ++b) sum += parts[b * 9 + threadIdx.x];
+        c[threadIdx.x] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     double lXp[3], lVp[3], lOmp[3];
     for (int k = 0; k < 3; ++k) {
         lXp[k] = a->lX[k] + c[k];
@@ -1086,15 +1092,14 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     const int G3 = (k.B + 2) * (k.B + 2) * (k.B + 2);
     ka_cover_mean<<<(G3 + kT - 1) / kT, kT, 0, st>>>(L1, s0, m0, s1, m1, b.uv, k);
     if (int rc = acheck(h, "ka_cover_mean")) return rc;
-    ka_update<<<1, 1, 0, st>>>(b.adj, b.cparts, h->box_blocks, s0, inv2T, dFp_dg);
+    ka_update<<<1, 32, 0, st>>>(b.adj, b.cparts, h->box_blocks, s0, inv2T, dFp_dg);
     if (int rc = acheck(h, "ka_update")) return rc;
     ka_psi_tape<<<h->grid, h->block, 0, st>>>(tn, h->psi, s0, m0, k);
     if (int rc = acheck(h, "ka_psi_tape")) return rc;
-    k_virtual<<<(unsigned)((B3 + kThreads - 1) / kThreads), kThreads, 0, st>>>(h->psi, s0, m0, k);
-    if (int rc = acheck(h, "k_virtual")) return rc;
     const unsigned nbs = (unsigned)((shell_count(k) + kThreads - 1) / kThreads);
-    k_shell<<<nbs, kThreads, 0, st>>>(h->psi, s0, m0, k);
-    if (int rc = acheck(h, "k_shell")) return rc;
+    const unsigned nbv = (unsigned)((B3 + kThreads - 1) / kThreads);
+    k_shell_virtual<<<nbs + nbv, kThreads, 0, st>>>(h->psi, s0, m0, k, (int)nbs);
+    if (int rc = acheck(h, "k_shell_virtual")) return rc;
     ka_node_bulk<<<h->grid, h->block, 0, st>>>(tn, h->psi, L1, L0, b.lgf, s0, m0, b.adj, b.parts, k);
     if (int rc = acheck(h, "ka_node_bulk")) return rc;
     ka_node_near<<<dim3(k.ncx, k.ncy, k.ncz), h->block, 0, st>>>(tn, h->psi, L1, L0, b.lgf, s0, m0, b.adj, b.parts, k);
