@@ -24,9 +24,9 @@ def flbm():
     return binding
 
 
-def _variances(flbm, p, burn, steps):
-    """Velocity variances per axis over `steps` steps after `burn`, in units of
-    kT / m_p: the half-step leap-frog velocity V and the step average Vavg."""
+def _trajectory(flbm, p, burn, steps):
+    """Half-step leap-frog velocity V and step average Vavg over `steps`
+    steps after `burn`, and kT / m_p."""
     sim = flbm.Sim(p)
     sim.step(burn)
     tr = sim.run_host(sim.read_f(), steps, traj=True)
@@ -34,6 +34,12 @@ def _variances(flbm, p, burn, steps):
     Va = np.array([t["Vavg"] for t in tr])
     s = p["kT"] / tr[-1]["mp"]
     sim.close()
+    return V, Va, s
+
+
+def _variances(flbm, p, burn, steps):
+    """Velocity variances per axis in units of kT / m_p: V and Vavg."""
+    V, Va, s = _trajectory(flbm, p, burn, steps)
     return V.var(axis=0) / s, Va.var(axis=0) / s
 
 
@@ -41,12 +47,20 @@ def test_heavy_sphere_velocity_equipartition(flbm):
     """rho_p = 5 rho, R = 3, fluctuating mixture in a 24x24x48 channel,
     200000 samples (a few thousand velocity relaxation times): both velocity
     estimates give kT / m_p to within their few-percent time-stepping bias,
-    the half-step velocity above the step average."""
+    the half-step velocity above the step average, and the velocity is
+    Gaussian."""
     p = W.params(lx=24, ly=24, lz=48, wall=(1, 1, 0), radius=3.0, rho_p_ratio=5.0, g=0.0, kT=1e-4, init_pert=0.0)
-    rv, ra = _variances(flbm, p, 2000, 200000)
+    V, Va, s = _trajectory(flbm, p, 2000, 200000)
+    rv, ra = V.var(axis=0) / s, Va.var(axis=0) / s
     assert 0.95 <= rv.mean() <= 1.15, rv
     assert 0.88 <= ra.mean() <= 1.06, ra
     assert rv.mean() > ra.mean()
+    # Gaussian velocity distribution (Section 3): kurtosis 3, no skew, 4.55 %
+    # of the samples beyond two standard deviations (pooled over the axes).
+    Z = (Va - Va.mean(axis=0)) / Va.std(axis=0)
+    assert 2.8 <= (Z ** 4).mean() <= 3.2, (Z ** 4).mean(axis=0)
+    assert abs((Z ** 3).mean()) <= 0.1, (Z ** 3).mean(axis=0)
+    assert 0.038 <= (np.abs(Z) > 2).mean() <= 0.053
 
 
 def test_light_sphere_leapfrog_estimates_bracket_equipartition(flbm):
