@@ -157,8 +157,19 @@ int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
     const bool noise = k.kT > 0.0f;
     const bool part = k.has_particle != 0;
     const dim3 gnear(k.ncx, k.ncy, k.ncz);
+    // Near tiles on the side stream (higher priority, so its few blocks start
+    // first), bulk tiles on the handle's stream, joined before the particle
+    // kernels: the near launch and its particle update overlap the bulk launch.
 #define FLBM_COLLIDE(NZ, T1)                                                                                  \
     do {                                                                                                      \
+        if (part) {                                                                                           \
+            CK(h, cudaEventRecord(h->fork_ev, h->stream));                                                    \
+            CK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));                                               \
+            k_collide_near<NZ, T1><<<gnear, h->block, 0, h->side>>>(fin, fout, h->psi, h->st, h->masks,       \
+                                                                    h->partials, k);                          \
+            if (int rc = launch_check(h, "k_collide_near")) return rc;                                        \
+            CK(h, cudaEventRecord(h->join_ev, h->side));                                                      \
+        }                                                                                                     \
         if (h->tma) {                                                                                         \
             k_collide_bulk_tma<NZ, T1><<<h->tma_grid, h->block, kTmaSmemBytes, h->stream>>>(                   \
                 h->tm_f[h->cur], h->tm_psi, fout, h->st, k);                                                  \
@@ -167,11 +178,7 @@ int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
             k_collide_bulk<NZ, T1><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, k);         \
             if (int rc = launch_check(h, "k_collide_bulk")) return rc;                                        \
         }                                                                                                     \
-        if (part) {                                                                                           \
-            k_collide_near<NZ, T1><<<gnear, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, h->masks,     \
-                                                                      h->partials, k);                        \
-            if (int rc = launch_check(h, "k_collide_near")) return rc;                                        \
-        }                                                                                                     \
+        if (part) CK(h, cudaStreamWaitEvent(h->stream, h->join_ev, 0));                                      \
     } while (0)
     if (noise && k.tau1) FLBM_COLLIDE(true, true);
     else if (noise) FLBM_COLLIDE(true, false);
@@ -302,6 +309,15 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
         cudaMalloc(&h->obs_tiles, sizeof(double) * 8 * h->ntiles) != cudaSuccess ||
         cudaMalloc(&h->obs_out, sizeof(double) * 8) != cudaSuccess)
         return bail(FLBM_E_NOMEM);
+
+    {
+        int lo = 0, hi = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess)
+            return bail(FLBM_E_CUDA);
+    }
 
     // Particle state (FP64): Eq. (fp) and the nominal sphere mass and inertia.
     const DevState s = initial_state(*p, k);
@@ -624,6 +640,12 @@ void flbm_destroy(flbm_t* h)
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     for (cudaGraphExec_t g : h->graph)
         if (g) cudaGraphExecDestroy(g);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
     delete[] h->traj_host;
     delete h;
 }

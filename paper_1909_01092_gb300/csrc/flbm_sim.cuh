@@ -48,6 +48,11 @@ struct flbm_sim {
     bool tma_ok = false;
     bool tma = false;
     int tma_grid = 0;
+    // The near-particle collide runs on a second, higher-priority stream,
+    // concurrently with the bulk collide (they write disjoint populations);
+    // fork and join by events.
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     long long ntiles = 0;
     int64_t launches = 0;
     std::string err;
