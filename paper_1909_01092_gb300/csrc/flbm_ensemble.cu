@@ -180,6 +180,10 @@ struct flbm_ens {
     std::vector<RepDesc> rd;
     flbm_ens_config cfg{0, 4, 0};
     cudaStream_t stream = nullptr;
+    // Near-particle collide on a higher-priority side stream, concurrent with
+    // the bulk collide (disjoint writes), forked and joined by events.
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     int nsm = 0;
     void* arena = nullptr;
     RepDesc* d_reps = nullptr;
@@ -369,17 +373,24 @@ int allocate(flbm_ens* e)
 
 namespace {
 
-// Launch work list w of kernel K with its trailing arguments.
+// Launch work list w of kernel K with its trailing arguments on stream s.
 template <typename... Args>
-int launch_list(flbm_ens* e, int w, void (*kern)(const RepDesc*, const int2*, int, Args...), const char* what,
-                Args... args)
+int launch_on(flbm_ens* e, cudaStream_t s, int w, void (*kern)(const RepDesc*, const int2*, int, Args...),
+              const char* what, Args... args)
 {
     const long long nitems = e->off[w + 1] - e->off[w];
     if (nitems == 0) return FLBM_OK;
     long long grid = nitems;
     if (e->cfg.ctas_per_sm > 0) grid = std::min(grid, (long long)e->cfg.ctas_per_sm * e->nsm);
-    kern<<<(unsigned)grid, 256, 0, e->stream>>>(e->d_reps, e->d_items + e->off[w], (int)nitems, args...);
+    kern<<<(unsigned)grid, 256, 0, s>>>(e->d_reps, e->d_items + e->off[w], (int)nitems, args...);
     return elaunch(e, what);
+}
+
+template <typename... Args>
+int launch_list(flbm_ens* e, int w, void (*kern)(const RepDesc*, const int2*, int, Args...), const char* what,
+                Args... args)
+{
+    return launch_on(e, e->stream, w, kern, what, args...);
 }
 
 // One step of every replica: reads f[cur], writes f[1 - cur].
@@ -388,14 +399,21 @@ int ens_step(flbm_ens* e)
     const int par = e->cur;
     if (int rc = launch_list(e, W_DENSITY, kb_density, "kb_density", par)) return rc;
     if (int rc = launch_list(e, W_SHELL, kb_shell, "kb_shell")) return rc;
+    const bool near = e->off[W_NEAR + 4] > e->off[W_NEAR];
+    if (near) {
+        ECK(e, cudaEventRecord(e->fork_ev, e->stream));
+        ECK(e, cudaStreamWaitEvent(e->side, e->fork_ev, 0));
+        if (int rc = launch_on(e, e->side, W_NEAR + 0, kb_near<false, false>, "kb_near", par)) return rc;
+        if (int rc = launch_on(e, e->side, W_NEAR + 1, kb_near<false, true>, "kb_near", par)) return rc;
+        if (int rc = launch_on(e, e->side, W_NEAR + 2, kb_near<true, false>, "kb_near", par)) return rc;
+        if (int rc = launch_on(e, e->side, W_NEAR + 3, kb_near<true, true>, "kb_near", par)) return rc;
+        ECK(e, cudaEventRecord(e->join_ev, e->side));
+    }
     if (int rc = launch_list(e, W_BULK + 0, kb_bulk<false, false>, "kb_bulk", par)) return rc;
     if (int rc = launch_list(e, W_BULK + 1, kb_bulk<false, true>, "kb_bulk", par)) return rc;
     if (int rc = launch_list(e, W_BULK + 2, kb_bulk<true, false>, "kb_bulk", par)) return rc;
     if (int rc = launch_list(e, W_BULK + 3, kb_bulk<true, true>, "kb_bulk", par)) return rc;
-    if (int rc = launch_list(e, W_NEAR + 0, kb_near<false, false>, "kb_near", par)) return rc;
-    if (int rc = launch_list(e, W_NEAR + 1, kb_near<false, true>, "kb_near", par)) return rc;
-    if (int rc = launch_list(e, W_NEAR + 2, kb_near<true, false>, "kb_near", par)) return rc;
-    if (int rc = launch_list(e, W_NEAR + 3, kb_near<true, true>, "kb_near", par)) return rc;
+    if (near) ECK(e, cudaStreamWaitEvent(e->stream, e->join_ev, 0));
     if (int rc = launch_list(e, W_MARK, kb_mark_next, "kb_mark_next")) return rc;
     if (int rc = launch_list(e, W_COVER, kb_cover, "kb_cover", par)) return rc;
     if (int rc = launch_list(e, W_FINISH, kb_finish, "kb_finish")) return rc;
@@ -479,7 +497,14 @@ int flbm_ensemble_create(const flbm_params* p, int32_t n, const flbm_ens_config*
     e->rd.resize(n);
     if (cfg) e->cfg = *cfg;
     e->stream = (cudaStream_t)stream;
-    int dev = 0;
+    int dev = 0, lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&e->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        flbm_ensemble_destroy(e);
+        return FLBM_E_CUDA;
+    }
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&e->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         flbm_ensemble_destroy(e);
@@ -604,6 +629,12 @@ void flbm_ensemble_destroy(flbm_ens_t* e)
     if (e->stream) cudaStreamSynchronize(e->stream);
     else cudaDeviceSynchronize();
     destroy_graphs(e);
+    if (e->side) {
+        cudaStreamSynchronize(e->side);
+        cudaStreamDestroy(e->side);
+    }
+    if (e->fork_ev) cudaEventDestroy(e->fork_ev);
+    if (e->join_ev) cudaEventDestroy(e->join_ev);
     cudaFree(e->arena);
     cudaFree(e->d_reps);
     cudaFree(e->d_items);
