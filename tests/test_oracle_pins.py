@@ -628,3 +628,31 @@ def test_particle_velocity_equipartition(oracle_mod):
     ra = float(np.mean(np.var(va, axis=0)) / s)
     assert 0.85 <= rv <= 1.15, rv
     assert 0.85 <= ra <= 1.15, ra
+
+
+@pytest.mark.parametrize("drho", [0.2, -0.2])
+def test_wetting_shift_enriches_the_preferred_component_at_the_surface(oracle_mod, drho):
+    """The sign convention of the wetting parameter (Section 2: the virtual
+    layer carries the neighbour mean plus delta_rho for A, minus for B).
+    delta_rho > 0 makes the particle hydrophilic to A: after relaxation the
+    fluid nodes touching a fixed sphere hold more A and less B than the fluid
+    far from it; delta_rho < 0 the reverse. Total mass stays exact."""
+    p = W.params(lx=14, ly=14, lz=14, wall=(0, 0, 0), radius=2.5, rho_p_ratio=1e9, g=0.0, kT=0.0, init_pert=0.0,
+                 rho_a0=0.6, rho_b0=0.4, G=1.2, delta_rho=drho, pos0=(6.5, 6.5, 6.5))
+    o = oracle_mod.Oracle(p)
+    m0 = o.observables()["mass"]
+    o.step(300)
+    fl = o.fields()
+    solid = fl["solid"]
+    touch = np.zeros_like(solid)
+    for c in C[1:]:
+        touch |= np.roll(solid, shift=(int(c[2]), int(c[1]), int(c[0])), axis=(0, 1, 2))
+    touch &= ~solid
+    zz, yy, xx = np.meshgrid(np.arange(14), np.arange(14), np.arange(14), indexing="ij")
+    r2 = (xx - 6.5) ** 2 + (yy - 6.5) ** 2 + (zz - 6.5) ** 2
+    far = r2 > 6.0 ** 2
+    ra, rb = fl["rho"][0], fl["rho"][1]
+    sgn = np.sign(drho)
+    assert sgn * (ra[touch].mean() - ra[far].mean()) > 1e-3, (ra[touch].mean(), ra[far].mean())
+    assert sgn * (rb[touch].mean() - rb[far].mean()) < -1e-3, (rb[touch].mean(), rb[far].mean())
+    assert np.allclose(o.observables()["mass"], m0, rtol=1e-12)
