@@ -102,3 +102,17 @@ def test_graphs_refused_on_the_legacy_stream(flbm):
         pytest.skip("default stream is not the legacy stream here")
     with pytest.raises(flbm.FLBMError):
         s.use_graphs(True)
+
+
+def test_legacy_default_stream_equals_another_stream(flbm):
+    """The near-particle collide forks to a second stream and joins back by
+    events; that must hold on the legacy default stream too."""
+    import torch
+
+    p = W.channel_small(kT=1e-5, g=1e-4)
+    a = flbm.Sim(p, stream=torch.cuda.default_stream())
+    b = flbm.Sim(p, stream=torch.cuda.Stream())
+    a.step(9)
+    b.step(9)
+    torch.cuda.synchronize()
+    _same_state(a, b, p)
