@@ -779,21 +779,33 @@ __device__ __forceinline__ void lpsi_gather_inner(int x, int y, int z, uint32_t 
                                                   const KParams& P, float out[2])
 {
     const size_t N = P.N;
+    const lg_t* g[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) g[k] = lg + k * N;
     Split r[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) r[k] = lg[k * N + n];
+    for (int k = 0; k < 6; ++k) r[k] = g[k][n];
+    // Away from the faces the source x - c_i is n minus a fixed offset.
+    const bool inside = (unsigned)(x - 1) < (unsigned)(P.lx - 2) && (unsigned)(y - 1) < (unsigned)(P.ly - 2) &&
+                        (unsigned)(z - 1) < (unsigned)(P.lz - 2);
+    const uint32_t sy = (uint32_t)P.lx, sz = (uint32_t)P.lx * (uint32_t)P.ly;
     float la = 0.0f, lb = 0.0f;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        int q[3];
-        nbr(x, y, z, -cxv(i), -cyv(i), -czv(i), P, q);  // in the domain: the caller checked
-        const uint32_t s = lin(q[0], q[1], q[2], P);
-        const float w = wv(i);
         const int cx = cxv(i), cy = cyv(i), cz = czv(i);
+        uint32_t s;
+        if (inside) {
+            s = n - (uint32_t)cx - (uint32_t)cy * sy - (uint32_t)cz * sz;
+        } else {
+            int q[3];
+            nbr(x, y, z, -cx, -cy, -cz, P, q);  // in the domain: the caller checked
+            s = lin(q[0], q[1], q[2], P);
+        }
+        const float w = wv(i);
         float tb = 0.0f, ta = 0.0f;
-        if (cx) { tb += cx * sdiff(lg[0 * N + s], r[0]); ta += cx * sdiff(lg[3 * N + s], r[3]); }
-        if (cy) { tb += cy * sdiff(lg[1 * N + s], r[1]); ta += cy * sdiff(lg[4 * N + s], r[4]); }
-        if (cz) { tb += cz * sdiff(lg[2 * N + s], r[2]); ta += cz * sdiff(lg[5 * N + s], r[5]); }
+        if (cx) { tb += cx * sdiff(g[0][s], r[0]); ta += cx * sdiff(g[3][s], r[3]); }
+        if (cy) { tb += cy * sdiff(g[1][s], r[1]); ta += cy * sdiff(g[4][s], r[4]); }
+        if (cz) { tb += cz * sdiff(g[2][s], r[2]); ta += cz * sdiff(g[5][s], r[5]); }
         lb += w * tb;
         la += w * ta;
     }
