@@ -63,12 +63,12 @@ struct AdjState {
 // the momentum and stress adjoints, lambda g_l (= -G rho_l lambda F_l, which
 // inherits b_l / 2) for the adjoint of psi. Stored in float32 they cost a
 // weakly coupled gradient (G or delta_rho in a dilute mixture) 1e-3 to 5e-2
-// relative accuracy within tens of steps. So these fields keep 48 significant
-// bits and the large parts enter in FP64; only the neighbour differences
+// relative accuracy within tens of steps. So these fields, and the arithmetic
+// on their large parts, keep 48 significant bits; only the neighbour differences
 // (a(x+c_i) - a(x)) + c_i . (b(x+c_i) - b(x)) go through the float32 mode
 // projection and collision transpose (adj_modes), the large part through
-// adj_modes_ab in FP64. The adjoint of psi at particle nodes and wall ghosts
-// (lpsi) is FP64.
+// adj_modes_ab in double-float arithmetic (flbm_df.h). The adjoint of psi at
+// particle nodes and wall ghosts (lpsi) and the reductions are FP64.
 //
 // The 48-bit fields are stored as two floats, v = hi + lo with
 // lo = fl(v - hi). A node reads its own values as FP64 (sval) and forms its
