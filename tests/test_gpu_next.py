@@ -70,32 +70,26 @@ def test_closed_channel(flbm, oracle_mod):
 
 def test_normalised_fluctuations_grow_with_confinement(flbm):
     """The paper's Section 3 result in the Langevin picture, on the ensemble
-    engine: a fluctuating sphere (R = 3, kT = 1e-4, same body force) settles
-    more slowly in narrower channels (c_m falls with d/L), while its velocity
-    fluctuation stays at equipartition, sqrt(kT / m_p); so the normalised
-    fluctuation Delta U / U grows with confinement. Channels L = 16, 24, 32, 48
-    (length 2L, walls on x and y, counterforce on the fluid), two noise
-    realisations each, in one ensemble."""
+    engine through paper_1909_01092_gb300.sweep: a fluctuating sphere (R = 3,
+    kT = 1e-4, same body force) settles more slowly in narrower channels (c_m
+    falls with d/L), while its velocity fluctuation stays at equipartition,
+    sqrt(kT / m_p) (Eq. (FLUCTUATIONSSCALING)); so the normalised fluctuation
+    Delta U / U grows with confinement (Eq. (normalizedconf)). Channels
+    L = 16, 24, 32, 48 (length 2L, walls on x and y, counterforce on the
+    fluid), two noise realisations each, in one ensemble; five-interval error
+    bars as in the paper's figures."""
+    from paper_1909_01092_gb300 import sweep
+
     Ls = (16, 24, 32, 48)
     plist = [W.params(lx=L, ly=L, lz=2 * L, radius=3.0, rho_p_ratio=5.0, g=2e-4, kT=1e-4, init_pert=0.0,
                       fluid_counterforce=1, replica=2 * k + s) for k, L in enumerate(Ls) for s in range(2)]
-    ens = flbm.Ensemble(plist)
-    ens.step(10000)  # about the viscous time of the widest channel
-    V = []
-    for _ in range(1500):
-        ens.step(10)
-        V.append([p["Vavg"][2] for p in ens.particles()])
-    V = np.array(V)  # samples x replicas
-    ufl = np.array([ens.observables(r)["momentum"][2] / ens.observables(r)["mass"].sum() for r in range(len(plist))])
-    parts = ens.particles()
-    ens.close()
-    U = (V.mean(axis=0) - ufl).reshape(len(Ls), 2).mean(axis=1)
-    t = np.arange(V.shape[0])
-    trend = np.array([np.polyval(np.polyfit(t, V[:, r], 1), t) for r in range(V.shape[1])]).T
-    resid = V - trend  # fluctuation about any slow drift
-    dU = resid.std(axis=0).reshape(len(Ls), 2).mean(axis=1)
-    s = np.sqrt(plist[0]["kT"] / parts[0]["mp"])
-    assert np.all(U > 0), U
-    assert np.all(np.diff(U) > 0), U            # c_m rises as d/L falls
-    assert np.all(np.abs(dU / s - 1.0) < 0.15), dU / s  # equipartition in every channel
-    assert np.all(np.diff(dU / U) < 0), dU / U  # Delta U / U falls as d/L falls
+    rows = sweep.settling_sweep(plist, burn=10000, samples=1500, every=10)
+    U = np.array([r["U"] for r in rows]).reshape(len(Ls), 2).mean(axis=1)
+    Uerr = np.array([r["U_err"] for r in rows]).reshape(len(Ls), 2).mean(axis=1)
+    cm = np.array([r["cm"] for r in rows]).reshape(len(Ls), 2).mean(axis=1)
+    dU = np.array([r["dU"] / r["dU_pred"] for r in rows]).reshape(len(Ls), 2).mean(axis=1)
+    ratio = np.array([r["dU_over_U"] for r in rows]).reshape(len(Ls), 2).mean(axis=1)
+    assert np.all((cm > 0) & (cm < 1)), cm
+    assert np.all(np.diff(U) > 3 * Uerr[1:]), (U, Uerr)  # c_m rises as d/L falls, beyond the error bars
+    assert np.all(np.abs(dU - 1.0) < 0.15), dU           # equipartition in every channel
+    assert np.all(np.diff(ratio) < 0), ratio              # Delta U / U falls as d/L falls
