@@ -93,3 +93,19 @@ def test_normalised_fluctuations_grow_with_confinement(flbm):
     assert np.all(np.diff(U) > 3 * Uerr[1:]), (U, Uerr)  # c_m rises as d/L falls, beyond the error bars
     assert np.all(np.abs(dU - 1.0) < 0.15), dU           # equipartition in every channel
     assert np.all(np.diff(ratio) < 0), ratio              # Delta U / U falls as d/L falls
+
+
+def test_hydrophilic_wetting_leaves_the_confined_drag_unchanged(flbm):
+    """Section 3 finds almost no dependency of c_m on the wettability. With
+    the particle wetted by the majority component (delta_rho = +0.5) the
+    noise-free settling velocity in 16- and 32-wide channels (R = 4) equals
+    the neutral one within 1 %."""
+    from paper_1909_01092_gb300 import sweep
+
+    plist = [W.params(lx=L, ly=L, lz=2 * L, radius=4.0, rho_p_ratio=1.5, g=1e-4, kT=0.0, init_pert=0.0,
+                      delta_rho=dr, fluid_counterforce=1, replica=k)
+             for k, (L, dr) in enumerate([(16, 0.0), (16, 0.5), (32, 0.0), (32, 0.5)])]
+    cm = [r["cm"] for r in sweep.settling_sweep(plist, burn=8000, samples=100, every=10)]
+    assert 0.0 < cm[0] < cm[2] < 1.0, cm
+    assert abs(cm[1] / cm[0] - 1.0) < 0.01, cm
+    assert abs(cm[3] / cm[2] - 1.0) < 0.01, cm
