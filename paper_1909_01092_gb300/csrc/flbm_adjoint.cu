@@ -1112,10 +1112,17 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     const unsigned nbv = (unsigned)((B3 + kThreads - 1) / kThreads);
     k_shell_virtual<<<nbs + nbv, kThreads, 0, st>>>(h->psi, s0, m0, k, (int)nbs);
     if (int rc = acheck(h, "k_shell_virtual")) return rc;
+    // Near tiles on the handle's side stream, concurrently with the bulk tiles
+    // (disjoint nodes and partials), joined before the psi adjoint.
+    ACK(h, cudaEventRecord(h->fork_ev, st));
+    ACK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+    ka_node_near<<<dim3(k.ncx, k.ncy, k.ncz), h->block, 0, h->side>>>(tn, h->psi, L1, L0, b.lgf, s0, m0, b.adj,
+                                                                       b.parts, k);
+    if (int rc = acheck(h, "ka_node_near")) return rc;
+    ACK(h, cudaEventRecord(h->join_ev, h->side));
     ka_node_bulk<<<h->grid, h->block, 0, st>>>(tn, h->psi, L1, L0, b.lgf, s0, m0, b.adj, b.parts, k);
     if (int rc = acheck(h, "ka_node_bulk")) return rc;
-    ka_node_near<<<dim3(k.ncx, k.ncy, k.ncz), h->block, 0, st>>>(tn, h->psi, L1, L0, b.lgf, s0, m0, b.adj, b.parts, k);
-    if (int rc = acheck(h, "ka_node_near")) return rc;
+    ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
     ka_lpsi<<<h->box_blocks, kT, 0, st>>>(b.lgf, h->psi, b.lpsi, s0, m0, b.adj, b.parts2, k);
     if (int rc = acheck(h, "ka_lpsi")) return rc;
     ka_lpsi_shell<<<nbs, kT, 0, st>>>(b.lgf, b.lpsi, s0, m0, k);
