@@ -1097,6 +1097,17 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     const uint8_t* m0 = b.tape_m + (size_t)kk * mbytes;
     const uint8_t* m1 = m0 + mbytes;
     cudaStream_t st = h->stream;
+    // The step's density field from the tape (side stream) does not depend on
+    // the particle adjoint (handle's stream); the two join before the node kernels.
+    ACK(h, cudaEventRecord(h->fork_ev, st));
+    ACK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+    ka_psi_tape<<<h->grid, h->block, 0, h->side>>>(tn, h->psi, s0, m0, k);
+    if (int rc = acheck(h, "ka_psi_tape")) return rc;
+    const unsigned nbs = (unsigned)((shell_count(k) + kThreads - 1) / kThreads);
+    const unsigned nbv = (unsigned)((B3 + kThreads - 1) / kThreads);
+    k_shell_virtual<<<nbs + nbv, kThreads, 0, h->side>>>(h->psi, s0, m0, k, (int)nbs);
+    if (int rc = acheck(h, "k_shell_virtual")) return rc;
+    ACK(h, cudaEventRecord(h->join_ev, h->side));
     ka_pre<<<1, 1, 0, st>>>(b.adj, s1);
     if (int rc = acheck(h, "ka_pre")) return rc;
     ka_cover<<<h->box_blocks, kT, 0, st>>>(L1, t1, s0, m0, s1, m1, b.adj, b.uv, b.cparts, k);
@@ -1106,12 +1117,7 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     if (int rc = acheck(h, "ka_cover_mean")) return rc;
     ka_update<<<1, 32, 0, st>>>(b.adj, b.cparts, h->box_blocks, s0, inv2T, dFp_dg);
     if (int rc = acheck(h, "ka_update")) return rc;
-    ka_psi_tape<<<h->grid, h->block, 0, st>>>(tn, h->psi, s0, m0, k);
-    if (int rc = acheck(h, "ka_psi_tape")) return rc;
-    const unsigned nbs = (unsigned)((shell_count(k) + kThreads - 1) / kThreads);
-    const unsigned nbv = (unsigned)((B3 + kThreads - 1) / kThreads);
-    k_shell_virtual<<<nbs + nbv, kThreads, 0, st>>>(h->psi, s0, m0, k, (int)nbs);
-    if (int rc = acheck(h, "k_shell_virtual")) return rc;
+    ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
     // Near tiles on the handle's side stream, concurrently with the bulk tiles
     // (disjoint nodes and partials), joined before the psi adjoint.
     ACK(h, cudaEventRecord(h->fork_ev, st));
@@ -1123,10 +1129,16 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     ka_node_bulk<<<h->grid, h->block, 0, st>>>(tn, h->psi, L1, L0, b.lgf, s0, m0, b.adj, b.parts, k);
     if (int rc = acheck(h, "ka_node_bulk")) return rc;
     ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
-    ka_lpsi<<<h->box_blocks, kT, 0, st>>>(b.lgf, h->psi, b.lpsi, s0, m0, b.adj, b.parts2, k);
+    // psi adjoint at particle nodes (side) and at wall ghosts (handle's
+    // stream): disjoint points of lpsi, joined before ka_final.
+    ACK(h, cudaEventRecord(h->fork_ev, st));
+    ACK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+    ka_lpsi<<<h->box_blocks, kT, 0, h->side>>>(b.lgf, h->psi, b.lpsi, s0, m0, b.adj, b.parts2, k);
     if (int rc = acheck(h, "ka_lpsi")) return rc;
+    ACK(h, cudaEventRecord(h->join_ev, h->side));
     ka_lpsi_shell<<<nbs, kT, 0, st>>>(b.lgf, b.lpsi, s0, m0, k);
     if (int rc = acheck(h, "ka_lpsi_shell")) return rc;
+    ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
     ka_final<<<h->grid, h->block, 0, st>>>(L0, b.lgf, b.lpsi, s0, m0, k);
     if (int rc = acheck(h, "ka_final")) return rc;
     ka_reduce<<<1, kT, 0, st>>>(b.adj, b.parts, h->ntiles, b.parts2, h->box_blocks);
