@@ -1139,10 +1139,17 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     ka_lpsi_shell<<<nbs, kT, 0, st>>>(b.lgf, b.lpsi, s0, m0, k);
     if (int rc = acheck(h, "ka_lpsi_shell")) return rc;
     ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
+    // The particle-adjoint reduction (side) and the a_l of fluid nodes
+    // (handle's stream) read and write disjoint data.
+    ACK(h, cudaEventRecord(h->fork_ev, st));
+    ACK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+    ka_reduce<<<1, kT, 0, h->side>>>(b.adj, b.parts, h->ntiles, b.parts2, h->box_blocks);
+    if (int rc = acheck(h, "ka_reduce")) return rc;
+    ACK(h, cudaEventRecord(h->join_ev, h->side));
     ka_final<<<h->grid, h->block, 0, st>>>(L0, b.lgf, b.lpsi, s0, m0, k);
     if (int rc = acheck(h, "ka_final")) return rc;
-    ka_reduce<<<1, kT, 0, st>>>(b.adj, b.parts, h->ntiles, b.parts2, h->box_blocks);
-    return acheck(h, "ka_reduce");
+    ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
+    return FLBM_OK;
 }
 
 }  // namespace
