@@ -139,12 +139,6 @@ __device__ __forceinline__ void virtual_node(int t, float* __restrict__ psi, con
     psi[P.padn + q] = vb;
 }
 
-static __global__ void __launch_bounds__(kThreads) k_virtual(float* __restrict__ psi, const DevState* __restrict__ st,
-                                                             const uint8_t* __restrict__ masks, KParams P)
-{
-    virtual_node(blockIdx.x * blockDim.x + threadIdx.x, psi, st, masks, P);
-}
-
 // Shell nodes of the padded psi field: z faces (full padded planes), y faces
 // (interior z), x faces (interior y and z). A padded row holds lx + 2 nodes;
 // its stride P.px may be larger (rounded up to 16 bytes).
@@ -240,12 +234,6 @@ __device__ __forceinline__ void shell_node(long long t, float* __restrict__ psi,
     const float inv = cnt ? 1.0f / (float)cnt : 0.0f;
     psi[dst] = sa * inv;
     psi[P.padn + dst] = sb * inv;
-}
-
-static __global__ void __launch_bounds__(kThreads) k_shell(float* __restrict__ psi, const DevState* __restrict__ st,
-                                                           const uint8_t* __restrict__ masks, KParams P)
-{
-    shell_node(blockIdx.x * (long long)blockDim.x + threadIdx.x, psi, st, masks, P);
 }
 
 // Shell and virtual layer in one launch: the first nshell_blocks blocks run

@@ -546,12 +546,6 @@ __device__ __forceinline__ void update_particle(DevState* __restrict__ st, const
     st->box_next[0] = o[0]; st->box_next[1] = o[1]; st->box_next[2] = o[2];
 }
 
-static __global__ void __launch_bounds__(256) k_update(DevState* __restrict__ st, const double* __restrict__ partials,
-                                                       KParams P)
-{
-    update_particle(st, partials, P);
-}
-
 // (2) Particle nodes at the new position -> mask[1 - cur]; per-block counts.
 // Block blk of 256 box entries.
 __device__ __forceinline__ void mark_next_block(int blk, const DevState* __restrict__ st, uint8_t* __restrict__ masks,
