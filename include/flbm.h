@@ -127,8 +127,11 @@ size_t flbm_state_bytes(const flbm_params* p);
 int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* stream, flbm_t** out);
 
 /* Advance nsteps >= 0 time steps (Eq. (lbe) with all of Section 2's particle
- * coupling). Asynchronous on the handle's stream. Errors: FLBM_E_INVAL,
- * FLBM_E_CUDA (launch failure). */
+ * coupling). Asynchronous on the handle's stream. Within a step the
+ * near-particle collide runs on a second, higher-priority stream that the
+ * handle owns, forked from and joined back to the handle's stream by events,
+ * so every step is complete in the handle's stream order. Errors:
+ * FLBM_E_INVAL, FLBM_E_CUDA (launch failure). */
 int flbm_step(flbm_t* h, int64_t nsteps);
 
 /* Copy the particle record to host memory `out`; synchronises the stream.
