@@ -30,3 +30,26 @@ def test_gaussian_series_recovers_its_parameters():
 def test_too_short_a_series_is_refused():
     with pytest.raises(ValueError):
         sweep.interval_stats(np.ones(9))
+
+
+def test_command_line_builds_the_channel_set(monkeypatch, capsys):
+    """The command line makes L x L x 2L channels (walls on x and y, the
+    counterforce on), `realisations` noise realisations per channel with
+    distinct replica indices, and prints one JSON line per replica."""
+    seen = {}
+
+    def fake(plist, burn, samples, every=10, intervals=5):
+        seen.update(plist=plist, burn=burn, samples=samples, every=every)
+        return [{"L": p["lx"], "replica": p["replica"]} for p in plist]
+
+    monkeypatch.setattr(sweep, "settling_sweep", fake)
+    sweep.main(["--L", "16", "32", "--radius", "4", "--kT", "1e-5", "--g", "1e-4", "--realisations", "3",
+                "--burn", "100", "--samples", "20", "--every", "5"])
+    plist = seen["plist"]
+    assert [p["lx"] for p in plist] == [16, 16, 16, 32, 32, 32]
+    assert all(p["lz"] == 2 * p["lx"] and p["ly"] == p["lx"] for p in plist)
+    assert all(p["wall"] == (1, 1, 0) and p["fluid_counterforce"] == 1 for p in plist)
+    assert len({p["replica"] for p in plist}) == 6
+    assert all(p["radius"] == 4.0 and p["kT"] == 1e-5 and p["g"] == 1e-4 for p in plist)
+    assert (seen["burn"], seen["samples"], seen["every"]) == (100, 20, 5)
+    assert len(capsys.readouterr().out.strip().splitlines()) == 6
