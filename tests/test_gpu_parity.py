@@ -245,3 +245,20 @@ def test_full_size_workload_conserves_mass(flbm):
     pg = sim.particle()
     assert pg["V"][2] > 0 and pg["step"] == 20
     assert math.isclose(pg["Fp"], 4 / 3 * math.pi * 12 ** 3 * 0.5 * 1.05 * 1e-5, rel_tol=1e-12)
+
+
+@pytest.mark.parametrize("drho", [-0.5, 0.0, 0.5])
+def test_fluctuating_channel_with_each_wetting(flbm, oracle_mod, drho):
+    """The 32x32x64 fluctuating channel (kT = 1e-5, R = 4) at each wetting
+    parameter of that workload, the particle given a velocity that makes it
+    cross nodes: 30 steps with identical Philox noise, populations within
+    1e-5 and the particle velocity within 1e-4 of its scale."""
+    p = W.channel_fluct(delta_rho=drho)
+    V = (0.01, -0.02, 0.04)
+    sim, orc = _pair(flbm, oracle_mod, p, X=p["pos0"], V=V, Om=(0.0, 0.01, 0.0))
+    sim.step(30)
+    orc.step(30)
+    pg, po = sim.particle(), orc.particle()
+    _compare_particle(pg, po, max(0.04, float(np.max(np.abs(po["V"])))), 30)
+    err = _max_rel(sim.read_f(), orc.get_f(), _fluid_mask(orc))
+    assert err < RTOL_F, f"max rel err {err:.3e}"
