@@ -263,7 +263,7 @@ def small_bench(binding, W, steps: int = 2000) -> list:
     """The two small channels (16x16x32 noise-free R=3; 32x32x64 kT=1e-5 R=4):
     their populations (2.5 and 20 MB) stay in L2 and a step is a few
     microseconds of work per kernel, so they are launch-bound. Each is timed
-    with graph replay (two-step CUDA graphs on a dedicated stream) and with
+    with graph replay (eight-step CUDA graphs on a dedicated stream) and with
     plain launches from the host."""
     import torch
 

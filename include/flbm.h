@@ -207,9 +207,9 @@ int flbm_checkpoint(flbm_t* h, const char* path);
 int flbm_restore(flbm_t* h, const char* path);
 
 /* CUDA-graph replay for flbm_step: with enable = 1, flbm_step replays a
- * captured graph of two steps (captured on first use) instead of issuing
- * each kernel, which removes the per-launch host cost that dominates small
- * lattices. Results are identical to plain launches. The handle's stream
+ * captured graph of eight steps (captured on first use; a remainder of fewer
+ * than eight steps runs as plain launches) instead of issuing each kernel,
+ * which removes the per-launch host cost that dominates small lattices. Results are identical to plain launches. The handle's stream
  * must not be the legacy default stream (capture is not allowed there):
  * FLBM_E_UNSUPPORTED then. enable = 0 returns to plain launches.
  * Errors: FLBM_E_INVAL, FLBM_E_UNSUPPORTED, FLBM_E_CUDA (capture failed). */

@@ -244,7 +244,7 @@ class Sim:
         return {k: getattr(r, k) for k, _ in AdjResult._fields_ if k != "reserved"}
 
     def use_graphs(self, enable: bool = True) -> None:
-        """Replay flbm_step as captured two-step CUDA graphs (needs a
+        """Replay flbm_step as captured eight-step CUDA graphs (needs a
         non-default stream)."""
         self._check(self.lib.flbm_use_graphs(self.h, int(bool(enable))), "flbm_use_graphs")
 

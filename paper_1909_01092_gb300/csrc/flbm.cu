@@ -201,14 +201,18 @@ int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
     return FLBM_OK;
 }
 
-// Capture two steps starting from cur = c into h->graph[c] (once).
+// Steps per captured graph (even, so that a replay brings cur back). More
+// steps per graph spread the replay's own launch cost over more steps.
+constexpr int kGraphSteps = 8;
+
+// Capture kGraphSteps steps starting from cur = c into h->graph[c] (once).
 int ensure_graph(flbm_sim* h, int c)
 {
     if (h->graph[c]) return FLBM_OK;
     const int64_t before = h->launches;
     CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = launch_step(h);
-    if (!rc) rc = launch_step(h);
+    int rc = FLBM_OK;
+    for (int k = 0; k < kGraphSteps && !rc; ++k) rc = launch_step(h);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (rc) {
@@ -351,10 +355,10 @@ int flbm_step(flbm_t* h, int64_t nsteps)
     h->launches = 0;
     int64_t s = 0;
     if (h->use_graphs) {
-        for (; s + 2 <= nsteps; s += 2) {
+        for (; s + kGraphSteps <= nsteps; s += kGraphSteps) {
             if (int rc = ensure_graph(h, h->cur)) return rc;
             CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
-            h->launches += h->graph_launches[h->cur];  // two steps bring cur back
+            h->launches += h->graph_launches[h->cur];  // an even number of steps brings cur back
         }
     }
     for (; s < nsteps; ++s)
