@@ -656,3 +656,36 @@ def test_wetting_shift_enriches_the_preferred_component_at_the_surface(oracle_mo
     assert sgn * (ra[touch].mean() - ra[far].mean()) > 1e-3, (ra[touch].mean(), ra[far].mean())
     assert sgn * (rb[touch].mean() - rb[far].mean()) < -1e-3, (rb[touch].mean(), rb[far].mean())
     assert np.allclose(o.observables()["mass"], m0, rtol=1e-12)
+
+
+def test_static_structure_factor_is_flat(oracle_mod):
+    """Fluctuation-dissipation at every wavelength (Section 2): in a
+    fluctuating ideal mixture (G = 0) the equal-time spectra of the density
+    and momentum fluctuations are flat, <|drho_k|^2>/N = 3 kT rho (per
+    component and in total) and <|j_k|^2>/N = kT rho_tot per axis, because the
+    noise thermalises every non-conserved mode, ghosts included. Checked on
+    every wavevector of an 8^3 box off the Nyquist planes, shell by shell."""
+    kT = 1e-4
+    p = W.params(lx=8, ly=8, lz=8, wall=(0, 0, 0), G=0.0, kT=kT, init_pert=0.0, rho_a0=1.0, rho_b0=0.3)
+    o = oracle_mod.Oracle(p)
+    o.step(100)
+    S = {"rho": np.zeros((8, 8, 8)), "rhoA": np.zeros((8, 8, 8)), "j": np.zeros((8, 8, 8))}
+    n = 1000
+    for _ in range(n):
+        o.step(1)
+        f = o.get_f()
+        rho, ra = f.sum((0, 1)), f[0].sum(0)
+        j = np.einsum("li...,ia->a...", f, C)
+        S["rho"] += np.abs(np.fft.fftn(rho - rho.mean())) ** 2 / rho.size
+        S["rhoA"] += np.abs(np.fft.fftn(ra - ra.mean())) ** 2 / rho.size
+        S["j"] += sum(np.abs(np.fft.fftn(j[a])) ** 2 for a in range(3)) / (3 * rho.size)
+    want = {"rho": 3 * kT * 1.3, "rhoA": 3 * kT * 1.0, "j": kT * 1.3}
+    kz, ky, kx = np.meshgrid(np.arange(8), np.arange(8), np.arange(8), indexing="ij")
+    fold = [np.minimum(k, 8 - k) for k in (kx, ky, kz)]
+    k2 = sum(k * k for k in fold)
+    keep = (k2 > 0) & np.all([k != 4 for k in fold], axis=0)
+    for name, s in S.items():
+        r = s / n / want[name]
+        shells = [r[keep & (k2 == q)].mean() for q in np.unique(k2[keep])]
+        assert abs(r[keep].mean() - 1.0) < 0.03, (name, r[keep].mean())
+        assert all(abs(v - 1.0) < 0.15 for v in shells), (name, np.round(shells, 3))  # about 4 sigma at k^2 = 1
