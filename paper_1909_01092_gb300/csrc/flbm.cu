@@ -1,6 +1,7 @@
 // C-ABI of the FLBM step library (declared in include/flbm.h): handle
-// management, validation, launch sequence of one time step, and the host
-// copies. All compute runs in the kernels of flbm_kernels.cuh.
+// management, validation, launch sequence of one time step (on the handle's
+// stream and its second stream), and the host copies. All compute runs in the
+// kernels of flbm_kernels.cuh, flbm_step.cuh and flbm_tma.cuh.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
