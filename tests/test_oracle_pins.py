@@ -689,3 +689,36 @@ def test_static_structure_factor_is_flat(oracle_mod):
         shells = [r[keep & (k2 == q)].mean() for q in np.unique(k2[keep])]
         assert abs(r[keep].mean() - 1.0) < 0.03, (name, r[keep].mean())
         assert all(abs(v - 1.0) < 0.15 for v in shells), (name, np.round(shells, 3))  # about 4 sigma at k^2 = 1
+
+
+def test_sphere_corotating_with_rigidly_rotating_fluid_feels_no_torque(oracle_mod):
+    """The moving link rule (Section 2) with rotation: fluid in rigid rotation
+    Omega about the sphere's centre (equilibrium populations at u = Omega x r)
+    exerts no torque on a sphere spinning with the same Omega; on a sphere at
+    rest it exerts a torque along Omega. After one step the co-rotating torque
+    and force are below 1e-3 of the resting sphere's torque (a wrong lever,
+    surface velocity or sign in the link rule gives a ratio of order one)."""
+    L = 16
+    X = np.array([7.3, 7.6, 7.45])
+    Om = np.array([0.0005, -0.0003, 0.002])
+    p = W.params(lx=L, ly=L, lz=L, wall=(0, 0, 0), G=0.0, kT=0.0, init_pert=0.0, radius=3.3, pos0=tuple(X))
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    zz, yy, xx = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    r = np.stack([xx - X[0], yy - X[1], zz - X[2]], 0)
+    u = np.cross(Om[:, None, None, None], r, axis=0)
+    cu = np.einsum("ia,a...->i...", C.astype(float), u)
+    feq = w[:, None, None, None] * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * (u ** 2).sum(0))
+    f = np.stack([p["rho_a0"] * feq, p["rho_b0"] * feq], 0)
+
+    def after_one_step(om_p):
+        o = oracle_mod.Oracle(p)
+        o.set_f(f)
+        o.set_particle(tuple(X), (0.0, 0.0, 0.0), tuple(om_p))
+        o.step(1)
+        return o.particle()
+
+    co, rest = after_one_step(Om), after_one_step((0.0, 0.0, 0.0))
+    Tref = np.linalg.norm(rest["T"])
+    assert np.dot(rest["T"], Om) > 0.9 * Tref * np.linalg.norm(Om)  # dragged along the rotation
+    assert np.linalg.norm(co["T"]) < 1e-3 * Tref
+    assert np.linalg.norm(co["F"]) < 1e-3 * Tref
