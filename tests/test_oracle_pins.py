@@ -401,6 +401,41 @@ def test_shear_wave_gives_printed_viscosity(oracle_mod, tau_s):
         assert abs(2.3 * nu - 0.383) < 0.001
 
 
+@pytest.mark.parametrize("tau_s", [0.8, 1.3])
+def test_sound_wave_speed_and_damping(oracle_mod, tau_s):
+    """The momentum equation of Section 2 has the pressure P_b = rho_tot / 3 at
+    G = 0 and the viscous stress eta (grad v + grad v^T), with no separate
+    bulk term. Linearised, a standing density wave of wavenumber k then
+    oscillates at omega = k / sqrt(3) and its amplitude decays at
+    Gamma = nu k^2. The wave runs through the trace and normal-stress modes,
+    which a shear wave never touches. omega and Gamma are the eigenvalue
+    e^(-Gamma +- i omega) of the one-step map of the (density, momentum)
+    amplitudes, fitted by least squares once the kinetic modes have relaxed."""
+    L, eps, steps, skip = 48, 1e-4, 400, 20
+    p = W.params(lx=L, ly=1, lz=1, wall=(0, 0, 0), G=0.0, tau_s=tau_s, init_pert=0.0, rho_a0=2.21, rho_b0=0.09)
+    o = oracle_mod.Oracle(p)
+    k = 2 * np.pi / L
+    x = np.arange(L)
+    f = np.zeros((2, 19, 1, 1, L))
+    for l, r in enumerate((2.21, 0.09)):
+        for n in range(L):
+            f[l, :, 0, 0, n] = _feq(r * (1 + eps * np.cos(k * x[n])), np.zeros(3))
+    o.set_f(f)
+    amps = []
+    for _ in range(steps):
+        g = o.get_f()
+        rho = g.sum((0, 1)).reshape(L)
+        jx = np.einsum("li...,i->...", g, C[:, 0]).reshape(L)
+        amps.append([2 * ((rho - rho.mean()) * np.cos(k * x)).mean(), 2 * (jx * np.sin(k * x)).mean()])
+        o.step(1)
+    a = np.array(amps[skip:])
+    M = np.linalg.lstsq(a[:-1], a[1:], rcond=None)[0].T
+    lam = np.linalg.eigvals(M)[0]
+    nu = (tau_s - 0.5) / 3
+    assert abs(-math.log(abs(lam)) / (nu * k * k) - 1) < 0.01
+    assert abs(abs(np.angle(lam)) / (k / math.sqrt(3)) - 1) < 0.003
+
+
 def test_interdiffusion_gives_printed_diffusivity(oracle_mod):
     """A composition wave at constant total density (G = 0) decays with the
     diffusivity D = (tau_d - 1/2)/3 = 1/6 at tau_d = 1 (Section 2)."""
