@@ -511,6 +511,39 @@ def test_single_node_mode_variances(oracle_mod):
     assert np.abs(corr).max() < 6 / math.sqrt(n)
 
 
+def test_single_node_relaxation_rates_and_stationary_variances(oracle_mod):
+    """With separate relaxation times for the stress, the component-momentum
+    and the ghost modes (the MRT of Section 2), one node of a 1x1x1 periodic
+    box (streaming maps it onto itself) makes every non-conserved mode a
+    discrete Ornstein-Uhlenbeck process m' = gamma_k m + noise with
+    gamma_k = 1 - 1/tau_k. Its lag-one autocorrelation is gamma_k, which pins
+    which modes relax at which rate. Its stationary variance is still
+    3 kT rho_l b_k (the interdiffusion current's kT rho_A rho_B / rho), as
+    fluctuation-dissipation requires whatever the rates."""
+    kT, taus, n = 1e-4, {"tau_s": 0.8, "tau_d": 0.7, "tau_g": 1.3}, 8000
+    p = W.params(lx=1, ly=1, lz=1, wall=(0, 0, 0), G=0.0, kT=kT, init_pert=0.0, rho_a0=1.0, rho_b0=0.5, **taus)
+    o = oracle_mod.Oracle(p)
+    L = oracle_mod.lattice()
+    e, b = L["e"], L["b"]
+    modes = np.empty((n, 2, 19))
+    for s in range(n):
+        o.step(1)
+        modes[s] = o.get_f()[:, :, 0, 0, 0] @ e.T
+    rho = np.array([1.0, 0.5])
+    gamma = np.array([0.0] * 4 + [1 - 1 / taus["tau_s"]] * 6 + [1 - 1 / taus["tau_g"]] * 9)
+    gamma[1:4] = 1 - 1 / taus["tau_d"]
+    want_var = 3 * kT * np.outer(rho, b)
+    want_var[:, 1:4] = kT * rho[0] * rho[1] / rho.sum()
+    for l in range(2):
+        for k in range(1, 19):
+            m = modes[:, l, k]
+            var = (m ** 2).mean()
+            ac = (m[1:] * m[:-1]).mean() / var
+            g = gamma[k]
+            assert abs(ac - g) < 5 / math.sqrt(n), (l, k, ac, g)
+            assert abs(var / want_var[l, k] - 1) < 5 * math.sqrt(2 * (1 + g * g) / (1 - g * g) / n), (l, k)
+
+
 @pytest.mark.slow
 def test_fluid_equipartition(oracle_mod):
     kT = 1e-4
