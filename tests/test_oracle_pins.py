@@ -479,6 +479,33 @@ def test_poiseuille_profile_curvature(oracle_mod):
     assert np.allclose(uz, uz[::-1], rtol=1e-9)
 
 
+@pytest.mark.parametrize("tau_s,tau_g,steps", [(0.875, 1.0, 3000), (1.3, 0.734375, 3000), (0.9, 1.0, 3000),
+                                               (0.6, 23 / 6, 6000)])
+def test_poiseuille_with_halfway_walls_matches_the_two_rate_closed_form(oracle_mod, tau_s, tau_g, steps):
+    """Steady plane Poiseuille flow with bounce-back walls at x = -1/2 and
+    L - 1/2, in a scheme whose even non-conserved modes relax at tau_s and odd
+    ones at tau_g (the MRT of Section 2 with a single component). The
+    two-relaxation-time analysis of bounce-back (Ginzburg and d'Humieres 2003)
+    gives the exact discrete profile
+        u(x) = g / (2 nu) [(x + 1/2)(L - 1/2 - x) + (16 Lambda - 3) / 12],
+    Lambda = (tau_s - 1/2)(tau_g - 1/2): the parabola of the halfway walls,
+    with no slip at Lambda = 3/16 and a uniform slip otherwise. A wall at
+    another place, a wrong rate on an odd mode or a wrong force term breaks it."""
+    L, g = 8, 1e-6
+    p = W.params(lx=L, ly=1, lz=1, wall=(1, 0, 0), G=0.0, tau_s=tau_s, tau_g=tau_g, init_pert=0.0,
+                 rho_a0=1.0, rho_b0=0.0, fluid_force=(0.0, 0.0, g))
+    o = oracle_mod.Oracle(p)
+    o.step(steps)
+    f = o.get_f()
+    rho = f.sum((0, 1)).reshape(L)
+    uz = (np.einsum("li...,i->...", f, C[:, 2]).reshape(L) + 0.5 * g) / rho
+    nu = (tau_s - 0.5) / 3
+    lam = (tau_s - 0.5) * (tau_g - 0.5)
+    x = np.arange(L)
+    want = g / (2 * nu) * ((x + 0.5) * (L - 0.5 - x) + (16 * lam - 3) / 12)
+    assert np.allclose(uz, want, rtol=1e-9, atol=0)
+
+
 # ---------------------------------------------------------------------------
 # Fluctuation-dissipation (Section 2): noise only on non-conserved modes with
 # variance 3 kT rho_l b_k; equipartition <j^2>/rho = kT per direction.
