@@ -96,6 +96,12 @@ CASES = [
                                     fluid_force=(1e-5, -2e-5, 3e-5), tau_s=0.7), 40, 4),
     ("single_node", W.params(lx=1, ly=1, lz=1, wall=(0, 0, 0), kT=1e-4), 30, 5),
     ("thin_channel", W.params(lx=1, ly=33, lz=2, wall=(0, 1, 0), G=1.2, kT=1e-5), 30, 6),
+    # noise amplitudes of all three relaxation classes, each at its own rate
+    ("noise_three_rates", W.params(lx=10, ly=9, lz=11, wall=(0, 1, 0), G=1.2, kT=1e-4, tau_s=0.8, tau_d=0.7,
+                                   tau_g=1.3), 40, 7),
+    # a line of nodes between halfway walls, forced along z (one row per tile)
+    ("line_walls_forced", W.params(lx=48, ly=1, lz=1, wall=(1, 0, 0), G=1.5, tau_s=0.875, tau_g=1.0,
+                                   fluid_force=(0.0, 0.0, 1e-6)), 200, 8),
 ]
 
 
