@@ -144,6 +144,35 @@ def cpu_baseline(max_seconds: float = 12.0, max_steps: int = 40) -> dict:
                       f"{dt:.1f} s, OpenMP over nodes"}
 
 
+def oracle_configs(seconds: float = 2.5) -> list:
+    """The FP64 oracle, as it stands, at one thread and at all threads on the
+    three single-GPU channels: 16x16x32 (noise-free, R=3), 32x32x64 (kT=1e-5,
+    R=4) and the 128x128x32 slab of the 128x128x512 channel. Each figure is
+    MLUPS over as many whole steps as fit in `seconds` (at least one)."""
+    import oracle
+    from paper_1909_01092_gb300 import workloads as W
+
+    full = oracle.num_threads()
+    out = []
+    for name, p in (("channel_16x16x32_R3", W.channel_small()),
+                    ("channel_32x32x64_kT1e-5_R4", W.channel_fluct()),
+                    ("channel_128x128x32_kT1e-5_R12 (slab)", W.channel_large(lz=32))):
+        n = p["lx"] * p["ly"] * p["lz"]
+        for threads in (1, full):
+            oracle.set_threads(threads)
+            o = oracle.Oracle(p)
+            steps, t0 = 0, time.perf_counter()
+            while steps == 0 or time.perf_counter() - t0 < seconds:
+                o.step(1)
+                steps += 1
+            dt = time.perf_counter() - t0
+            out.append({"workload": name, "threads": threads, "mlups": n * steps / dt / 1e6, "steps": steps,
+                        "seconds": round(dt, 2)})
+            del o
+    oracle.set_threads(full)
+    return out
+
+
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -395,6 +424,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
+        cpu["configs"] = oracle_configs()
     nfluid = sim.particle()["nfluid"]
     ens = adj = small = None
     if rank == 0 and world == 1 and not args.no_ensemble:

@@ -95,6 +95,7 @@ def _load():
         lib.oracle_uniform.restype = ctypes.c_double
         lib.oracle_uniform.argtypes = [ctypes.c_uint32]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
         _LIB = lib
         return lib
 
@@ -237,5 +238,5 @@ def num_threads() -> int:
 
 
 def set_threads(n: int) -> None:
-    """Thread count for the oracle's OpenMP loops (set before the first call)."""
-    os.environ["OMP_NUM_THREADS"] = str(int(n))
+    """Thread count (n >= 1) for the OpenMP loops of the oracle's later calls."""
+    _load().oracle_set_threads(int(n))

@@ -823,3 +823,13 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads for the OpenMP loops of later calls (n >= 1; ignored without OpenMP). */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
