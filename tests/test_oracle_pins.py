@@ -461,6 +461,45 @@ def test_interdiffusion_gives_printed_diffusivity(oracle_mod):
     assert abs(D - 1 / 6) < 0.005 / 6
 
 
+@pytest.mark.parametrize("G,tau_d", [(0.5, 1.0), (0.8, 1.0), (0.8, 0.8)])
+def test_shan_chen_interaction_slows_interdiffusion_as_the_chemical_potential_says(oracle_mod, G, tau_d):
+    """Section 2: the composition relaxes down the gradient of the chemical
+    potential mu = (1/3) ln rho_A - (1/3) ln rho_B - (G/3)(rho_A - rho_B)
+    (with the sign that makes the printed coexistence densities equal mu).
+    Around a uniform mixture at constant total density, d mu / d rho_A is
+    scaled by 1 - 2 G rho_A rho_B / rho_tot when the interaction is on, and
+    the mobility in front of grad mu is the same with or without it. So a
+    composition wave decays at the G = 0 diffusivity times that factor. The
+    Shan-Chen stencil turns the gradient of a wave exp(i k x) into sin(k)
+    instead of k, which the factor carries for the force term. The symmetric
+    mixture rho_A = rho_B keeps the wave away from pressure, since
+    rho_A rho_B is then stationary to first order."""
+    L, eps, skip, steps = 96, 1e-4, 50, 300
+    k = 2 * np.pi / L
+    x = np.arange(L)
+
+    def decay_rate(g):
+        p = W.params(lx=L, ly=1, lz=1, wall=(0, 0, 0), G=g, tau_d=tau_d, init_pert=0.0, rho_a0=1.0, rho_b0=1.0)
+        o = oracle_mod.Oracle(p)
+        c = eps * np.sin(k * x)
+        f = np.zeros((2, 19, 1, 1, L))
+        for n in range(L):
+            f[0, :, 0, 0, n] = _feq(1.0 + c[n], np.zeros(3))
+            f[1, :, 0, 0, n] = _feq(1.0 - c[n], np.zeros(3))
+        o.set_f(f)
+
+        def amp():
+            return 2 * ((o.get_f()[0].sum(0).reshape(L) - 1.0) * np.sin(k * x)).mean()
+
+        o.step(skip)
+        a0 = amp()
+        o.step(steps)
+        return -math.log(amp() / a0) / steps
+
+    factor = 1 - 2 * G * 1.0 * 1.0 / 2.0 * math.sin(k) / k
+    assert abs(decay_rate(G) / decay_rate(0.0) / factor - 1) < 3e-3
+
+
 def test_poiseuille_profile_curvature(oracle_mod):
     """Plane Poiseuille flow between halfway walls: the steady velocity has
     constant second difference -g / (rho nu) with nu = (tau - 1/2)/3, and is
