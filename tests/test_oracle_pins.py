@@ -401,23 +401,28 @@ def test_shear_wave_gives_printed_viscosity(oracle_mod, tau_s):
         assert abs(2.3 * nu - 0.383) < 0.001
 
 
-@pytest.mark.parametrize("tau_s", [0.8, 1.3])
-def test_sound_wave_speed_and_damping(oracle_mod, tau_s):
-    """The momentum equation of Section 2 has the pressure P_b = rho_tot / 3 at
-    G = 0 and the viscous stress eta (grad v + grad v^T), with no separate
-    bulk term. Linearised, a standing density wave of wavenumber k then
-    oscillates at omega = k / sqrt(3) and its amplitude decays at
-    Gamma = nu k^2. The wave runs through the trace and normal-stress modes,
-    which a shear wave never touches. omega and Gamma are the eigenvalue
-    e^(-Gamma +- i omega) of the one-step map of the (density, momentum)
-    amplitudes, fitted by least squares once the kinetic modes have relaxed."""
+@pytest.mark.parametrize("tau_s,G,rho_a,rho_b", [(0.8, 0.0, 2.21, 0.09), (1.3, 0.0, 2.21, 0.09),
+                                               (0.8, 0.5, 1.0, 1.0), (1.3, 0.8, 1.0, 1.0)])
+def test_sound_wave_speed_and_damping(oracle_mod, tau_s, G, rho_a, rho_b):
+    """The momentum equation of Section 2 has the printed bulk pressure
+    P_b = rho_tot / 3 + (G/3) rho_A rho_B and the viscous stress
+    eta (grad v + grad v^T), with no separate bulk term. Linearised, a
+    standing density wave of wavenumber k at fixed composition then oscillates
+    at omega^2 = k^2 dP_b/drho = k^2 [1/3 + (2G/3) rho_A rho_B / rho_tot] (the
+    Shan-Chen stencil turning one k of the interaction term into sin k), and
+    its amplitude decays at Gamma = nu k^2. The wave runs through the trace and
+    normal-stress modes, which a shear wave never touches. In the symmetric
+    mixture rho_A = rho_B the wave leaves the composition alone. omega and
+    Gamma are the eigenvalue e^(-Gamma +- i omega) of the one-step map of the
+    (density, momentum) amplitudes, fitted by least squares once the kinetic
+    modes have relaxed."""
     L, eps, steps, skip = 48, 1e-4, 400, 20
-    p = W.params(lx=L, ly=1, lz=1, wall=(0, 0, 0), G=0.0, tau_s=tau_s, init_pert=0.0, rho_a0=2.21, rho_b0=0.09)
+    p = W.params(lx=L, ly=1, lz=1, wall=(0, 0, 0), G=G, tau_s=tau_s, init_pert=0.0, rho_a0=rho_a, rho_b0=rho_b)
     o = oracle_mod.Oracle(p)
     k = 2 * np.pi / L
     x = np.arange(L)
     f = np.zeros((2, 19, 1, 1, L))
-    for l, r in enumerate((2.21, 0.09)):
+    for l, r in enumerate((rho_a, rho_b)):
         for n in range(L):
             f[l, :, 0, 0, n] = _feq(r * (1 + eps * np.cos(k * x[n])), np.zeros(3))
     o.set_f(f)
@@ -432,8 +437,9 @@ def test_sound_wave_speed_and_damping(oracle_mod, tau_s):
     M = np.linalg.lstsq(a[:-1], a[1:], rcond=None)[0].T
     lam = np.linalg.eigvals(M)[0]
     nu = (tau_s - 0.5) / 3
+    omega = math.sqrt(k * k / 3 + (2 * G / 3) * rho_a * rho_b / (rho_a + rho_b) * k * math.sin(k))
     assert abs(-math.log(abs(lam)) / (nu * k * k) - 1) < 0.01
-    assert abs(abs(np.angle(lam)) / (k / math.sqrt(3)) - 1) < 0.003
+    assert abs(abs(np.angle(lam)) / omega - 1) < 0.003
 
 
 def test_interdiffusion_gives_printed_diffusivity(oracle_mod):
