@@ -8,7 +8,7 @@ line per channel: the mean settling velocity U relative to the mean fluid
 velocity, its velocity fluctuation Delta U, both with error bars, the
 confinement ratio c_m = U / U_0 with U_0 = F_p / (3 pi eta d) (Eq. (cm)), and
 the Langevin predictions Delta U^2 = kT / m_p (Eq. (FLUCTUATIONSSCALING)) and
-Delta U / U (Eq. (normalizedconf)).
+Delta U / U (Eq. (normalizedconf)), confined and unconfined (c_m = 1).
 
 Error bars follow the figure captions of Section 3: in the stationary state the
 record is split into five equal time intervals, and the error is the standard
@@ -40,11 +40,33 @@ def interval_stats(v: np.ndarray, n: int = 5) -> dict:
             "fluct": float(stds.mean()), "fluct_err": float(stds.std())}
 
 
+def settling_row(p: dict, vz: np.ndarray, ufl: float, mp: float, Fp: float, intervals: int = 5) -> dict:
+    """Statistics of one replica: p its parameters, vz its particle velocity
+    record along z (equally spaced, stationary), ufl the mean fluid velocity
+    along z, mp the particle mass and Fp the driving force (Eq. (fp)).
+
+    U and Delta U are the interval mean and fluctuation of vz - ufl. The
+    unconfined Stokes velocity is U_0 = F_p / (3 pi eta d), eta = rho_tot
+    (tau_s - 1/2) / 3, so c_m = U / U_0 (Eq. (cm)). The Langevin predictions
+    are Delta U = sqrt(kT / m_p) (Eq. (FLUCTUATIONSSCALING)) and
+    Delta U / U = sqrt(kT / m_p) / (c_m U_0) (Eq. (normalizedconf)), whose
+    unconfined form sets c_m = 1."""
+    st = interval_stats(vz, intervals)
+    eta = (p["rho_a0"] + p["rho_b0"]) * (p["tau_s"] - 0.5) / 3.0
+    U = st["mean"] - ufl
+    U0 = Fp / (3.0 * math.pi * eta * 2.0 * p["radius"])
+    dU_pred = math.sqrt(p["kT"] / mp)
+    return {"L": p["lx"], "d_over_L": 2.0 * p["radius"] / p["lx"], "kT": p["kT"], "g": p["g"],
+            "U": U, "U_err": st["mean_err"], "dU": st["fluct"], "dU_err": st["fluct_err"],
+            "cm": U / U0, "cm_err": st["mean_err"] / U0,
+            "dU_pred": dU_pred, "dU_over_U": st["fluct"] / U, "dU_over_U_pred": dU_pred / U,
+            "dU0_over_U0_pred": dU_pred / U0}
+
+
 def settling_sweep(plist: list[dict], burn: int, samples: int, every: int = 10, intervals: int = 5) -> list[dict]:
     """Advance the replicas of plist as one ensemble: burn steps, then
     samples x every steps, recording Vavg_z every `every` steps. Returns one
-    dict per replica with U, Delta U, their error bars, c_m and the Langevin
-    predictions. Needs the CUDA library (binding.Ensemble)."""
+    settling_row per replica. Needs the CUDA library (binding.Ensemble)."""
     from . import binding
 
     ens = binding.Ensemble(plist)
@@ -61,16 +83,7 @@ def settling_sweep(plist: list[dict], burn: int, samples: int, every: int = 10, 
     out = []
     for r, p in enumerate(plist):
         ufl = obs[r]["momentum"][2] / float(np.sum(obs[r]["mass"]))
-        st = interval_stats(rec[:, r], intervals)
-        mp, Fp = parts[r]["mp"], parts[r]["Fp"]
-        eta = (p["rho_a0"] + p["rho_b0"]) * (p["tau_s"] - 0.5) / 3.0
-        U = st["mean"] - ufl
-        U0 = Fp / (3.0 * math.pi * eta * 2.0 * p["radius"])
-        dU_pred = math.sqrt(p["kT"] / mp)
-        out.append({"L": p["lx"], "d_over_L": 2.0 * p["radius"] / p["lx"], "kT": p["kT"], "g": p["g"],
-                    "U": U, "U_err": st["mean_err"], "dU": st["fluct"], "dU_err": st["fluct_err"],
-                    "cm": U / U0, "cm_err": st["mean_err"] / U0,
-                    "dU_pred": dU_pred, "dU_over_U": st["fluct"] / U, "dU_over_U_pred": dU_pred / U})
+        out.append(settling_row(p, rec[:, r], ufl, parts[r]["mp"], parts[r]["Fp"], intervals))
     return out
 
 

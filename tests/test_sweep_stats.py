@@ -53,3 +53,31 @@ def test_command_line_builds_the_channel_set(monkeypatch, capsys):
     assert all(p["radius"] == 4.0 and p["kT"] == 1e-5 and p["g"] == 1e-4 for p in plist)
     assert (seen["burn"], seen["samples"], seen["every"]) == (100, 20, 5)
     assert len(capsys.readouterr().out.strip().splitlines()) == 6
+
+
+def test_row_matches_the_printed_langevin_predictions():
+    """At the paper's particle density rho_p = 2 rho_tot, with F_p from
+    Eq. (fp) and m_p = pi d^3 rho_p / 6, the row's predictions equal the
+    closed forms printed in Section 3: Delta U = sqrt(6 / (pi rho_p L^3))
+    (kT)^(1/2) (d/L)^(-3/2) (Eq. (FLUCTUATIONSSCALING)) and Delta U / U =
+    18 sqrt(6 eta^2 / (rho_tot^2 pi rho_p L^7)) (kT)^(1/2) (d/L)^(-7/2) / (g c_m)
+    (Eq. (normalizedconf)), the unconfined one with c_m = 1."""
+    from paper_1909_01092_gb300 import workloads as W
+
+    p = W.params(lx=32, ly=32, lz=64, radius=4.0, rho_p_ratio=2.0, g=5e-6, kT=1e-5, tau_s=0.9)
+    rho = p["rho_a0"] + p["rho_b0"]
+    rho_p, d, L, kT, g = 2.0 * rho, 8.0, 32.0, 1e-5, 5e-6
+    mp = np.pi * d ** 3 / 6 * rho_p
+    Fp = np.pi * d ** 3 / 6 * (rho_p - rho) * g
+    eta = rho * (0.9 - 0.5) / 3
+    U0 = Fp / (3 * np.pi * eta * d)
+    rng = np.random.default_rng(5)
+    ufl = -1e-6
+    vz = ufl + 0.6 * U0 + 1e-4 * rng.standard_normal(5000)
+    row = sweep.settling_row(p, vz, ufl, mp, Fp)
+    assert row["cm"] == pytest.approx(0.6, abs=5 * 1e-4 / np.sqrt(5000) / U0)
+    assert row["dU"] == pytest.approx(1e-4, rel=0.05)
+    assert row["dU_pred"] == pytest.approx(np.sqrt(6 / (np.pi * rho_p * L ** 3)) * kT ** 0.5 * (d / L) ** -1.5)
+    printed = 18 * np.sqrt(6 * eta ** 2 / (rho ** 2 * np.pi * rho_p * L ** 7)) * kT ** 0.5 * (d / L) ** -3.5 / g
+    assert row["dU_over_U_pred"] == pytest.approx(printed / row["cm"])
+    assert row["dU0_over_U0_pred"] == pytest.approx(printed)
