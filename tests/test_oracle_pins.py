@@ -897,3 +897,61 @@ def test_angular_momentum_about_the_sphere_is_conserved(oracle_mod, G, drho):
         torque += o.particle()["T"]
     assert np.linalg.norm(torque) > 1.0
     assert np.abs(fluid_angular_momentum() - L0 + torque).max() < 1e-12 * np.linalg.norm(torque)
+
+
+def _direction_map(M):
+    """Index of M c_i in the lattice, for each direction i."""
+    Ci = C.astype(int)
+    return np.array([int(np.flatnonzero((Ci == M @ Ci[i]).all(axis=1))[0]) for i in range(19)])
+
+
+def test_square_channel_symmetry_is_kept_through_cover_and_uncover(oracle_mod):
+    """The step commutes with the symmetries of the square channel (walls on
+    x and y) about its axis: the mirrors x -> L-1-x and y -> L-1-y and the swap
+    x <-> y, each acting on positions and on the velocity set. A state with
+    that symmetry, a wetted sphere (G = 1.2, Delta rho = 0.3) on the axis
+    moving along it, keeps it exactly, through the Shan-Chen force, the wall
+    ghosts, the virtual layer, the link rule and the cover/uncover events of a
+    settling sphere; and the sphere stays on the axis without spin. A
+    direction or an axis handled unlike its images breaks it."""
+    L, Lz = 10, 16
+    p = W.params(lx=L, ly=L, lz=Lz, wall=(1, 1, 0), G=1.2, delta_rho=0.3, radius=2.6, rho_p_ratio=1.5, g=2e-3,
+                 kT=0.0, init_pert=0.0)
+    mx = _direction_map(np.diag([-1, 1, 1]))
+    my = _direction_map(np.diag([1, -1, 1]))
+    sw = _direction_map(np.array([[0, 1, 0], [1, 0, 0], [0, 0, 1]]))
+
+    def mirror_x(f):
+        g = np.empty_like(f)
+        g[:, mx] = f[..., ::-1]
+        return g
+
+    def mirror_y(f):
+        g = np.empty_like(f)
+        g[:, my] = f[..., ::-1, :]
+        return g
+
+    def swap_xy(f):
+        g = np.empty_like(f)
+        g[:, sw] = np.swapaxes(f, -1, -2)
+        return g
+
+    f = W.random_populations(p, 11)
+    images = [f, swap_xy(f)]
+    images += [mirror_x(g) for g in images]
+    images += [mirror_y(g) for g in images]
+    f = sum(images) / len(images)  # average over the eight symmetries of the square
+    o = oracle_mod.Oracle(p)
+    o.set_f(f)
+    o.set_particle(((L - 1) / 2, (L - 1) / 2, 7.3), V=(0.0, 0.0, 0.05))
+    nfluid = set()
+    for _ in range(60):
+        o.step(1)
+        nfluid.add(o.particle()["nfluid"])
+    assert len(nfluid) > 1  # nodes were covered and uncovered
+    g = o.get_f()
+    for T in (mirror_x, mirror_y, swap_xy):
+        assert np.abs(T(g) - g).max() < 1e-13 * np.abs(g).max()
+    pa = o.particle()
+    assert np.abs(pa["X"][:2] - (L - 1) / 2).max() < 1e-13
+    assert np.abs(pa["V"][:2]).max() < 1e-15 and np.abs(pa["Omega"]).max() < 1e-15
