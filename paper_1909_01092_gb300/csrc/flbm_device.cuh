@@ -209,7 +209,7 @@ struct DevState {
 constexpr int kThreadsStep = 256;
 
 // Signed offset of box coordinate of lattice coordinate c on one axis.
-__device__ __forceinline__ int box_rel(int c, int o, int L, int wall)
+__host__ __device__ __forceinline__ int box_rel(int c, int o, int L, int wall)
 {
     int t = c - o;
     if (!wall && t < 0) t += L;
@@ -234,7 +234,7 @@ __device__ __forceinline__ bool is_solid(int x, int y, int z, const int o[3], co
 }
 
 // Does [a0, a0+la) meet [b0, b0+lb) on an axis of length L (periodic: modulo L)?
-__device__ __forceinline__ bool ranges_meet(int a0, int la, int b0, int lb, int L, int wall)
+__host__ __device__ __forceinline__ bool ranges_meet(int a0, int la, int b0, int lb, int L, int wall)
 {
     if (wall) return a0 < b0 + lb && b0 < a0 + la;
     if (lb >= L) return true;
@@ -245,7 +245,7 @@ __device__ __forceinline__ bool ranges_meet(int a0, int la, int b0, int lb, int 
 
 // Tile (bx, by, bz) meets the particle box grown by one node on every side:
 // only such tiles have fluid nodes whose stencil touches a particle node.
-__device__ __forceinline__ bool tile_near(int bx, int by, int bz, const int o[3], const KParams& P)
+__host__ __device__ __forceinline__ bool tile_near(int bx, int by, int bz, const int o[3], const KParams& P)
 {
     const int x0 = bx * P.tx, y0 = by * P.ty;
     const int lxr = min(P.tx, P.lx - x0), lyr = min(P.ty, P.ly - y0);
@@ -261,7 +261,7 @@ __device__ __forceinline__ long long pad_index(int x, int y, int z, const KParam
 }
 
 // Vector from the particle centre to point r, minimum image on periodic axes.
-__device__ __forceinline__ double rel_axis(double r, double X, int L, int wall)
+__host__ __device__ __forceinline__ double rel_axis(double r, double X, int L, int wall)
 {
     double d = r - X;
     if (!wall) {

@@ -367,7 +367,7 @@ static __global__ void __launch_bounds__(kThreadsStep, FLBM_BULK_MINBLOCKS)
 
 // Candidate c on one axis -> tile index, or -1. e0 = first coordinate of the
 // grown box on that axis; tiles of size T, gt of them, axis length L.
-__device__ __forceinline__ int candidate_tile(int c, int o, int T, int gt, int L, int wall)
+__host__ __device__ __forceinline__ int candidate_tile(int c, int o, int T, int gt, int L, int wall)
 {
     int e0 = o - 1;
     if (wall) {
@@ -469,7 +469,7 @@ static __global__ void __launch_bounds__(kThreadsStep, TAU1 ? 3 : 2)
                            threadIdx.x + blockDim.x * threadIdx.y, fin, fout, psi, st, masks, partials, P);
 }
 
-__device__ __forceinline__ void box_origin(const double X[3], const KParams& P, int o[3])
+__host__ __device__ __forceinline__ void box_origin(const double X[3], const KParams& P, int o[3])
 {
     const int L[3] = {P.lx, P.ly, P.lz};
 #pragma unroll
@@ -484,7 +484,7 @@ __device__ __forceinline__ void box_origin(const double X[3], const KParams& P, 
 }
 
 // Particle node test for box entry t of a box at origin o around centre X (FP64).
-__device__ __forceinline__ bool box_node_inside(int t, const int o[3], const double X[3], const KParams& P)
+__host__ __device__ __forceinline__ bool box_node_inside(int t, const int o[3], const double X[3], const KParams& P)
 {
     const int B = P.B;
     const int d[3] = {t % B, (t / B) % B, t / (B * B)};
