@@ -216,7 +216,7 @@ __host__ __device__ __forceinline__ int box_rel(int c, int o, int L, int wall)
     return t;
 }
 
-__device__ __forceinline__ bool in_box(int x, int y, int z, const int o[3], const KParams& P, int& bi)
+__host__ __device__ __forceinline__ bool in_box(int x, int y, int z, const int o[3], const KParams& P, int& bi)
 {
     const int dx = box_rel(x, o[0], P.lx, P.wall[0]);
     const int dy = box_rel(y, o[1], P.ly, P.wall[1]);
@@ -227,7 +227,7 @@ __device__ __forceinline__ bool in_box(int x, int y, int z, const int o[3], cons
     return true;
 }
 
-__device__ __forceinline__ bool is_solid(int x, int y, int z, const int o[3], const uint8_t* mask, const KParams& P)
+__host__ __device__ __forceinline__ bool is_solid(int x, int y, int z, const int o[3], const uint8_t* mask, const KParams& P)
 {
     int bi;
     return in_box(x, y, z, o, P, bi) && mask[bi];
@@ -255,7 +255,7 @@ __host__ __device__ __forceinline__ bool tile_near(int bx, int by, int bz, const
            ranges_meet(bz, 1, o[2] - 1, B2, P.lz, P.wall[2]);
 }
 
-__device__ __forceinline__ long long pad_index(int x, int y, int z, const KParams& P)
+__host__ __device__ __forceinline__ long long pad_index(int x, int y, int z, const KParams& P)
 {
     return (long long)(x + 1) + (long long)P.px * ((y + 1) + (long long)P.py * (z + 1));
 }

@@ -83,7 +83,7 @@ static __global__ void __launch_bounds__(kThreads) k_density(const float* __rest
 // B, clipped at 0. One thread per node of the particle box.
 // ---------------------------------------------------------------------------
 // Virtual-layer densities of particle node c (lattice coordinates, in range).
-__device__ __forceinline__ void virtual_value(const int c[3], const float* __restrict__ psi, const int o[3],
+__host__ __device__ __forceinline__ void virtual_value(const int c[3], const float* __restrict__ psi, const int o[3],
                                               const uint8_t* __restrict__ mask, const KParams& P, float& va,
                                               float& vb)
 {
@@ -116,7 +116,7 @@ __device__ __forceinline__ void virtual_value(const int c[3], const float* __res
     }
 }
 
-__device__ __forceinline__ void virtual_node(int t, float* __restrict__ psi, const DevState* __restrict__ st,
+__host__ __device__ __forceinline__ void virtual_node(int t, float* __restrict__ psi, const DevState* __restrict__ st,
                                              const uint8_t* __restrict__ masks, const KParams& P)
 {
     const int B = P.B;
@@ -153,7 +153,7 @@ __host__ __device__ __forceinline__ long long shell_count(const KParams& P)
 // interior node, whose value it copies, or is a wall ghost, which takes the
 // mean over its fluid neighbours (neutral wetting, Section 3).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void shell_node(long long t, float* __restrict__ psi, const DevState* __restrict__ st,
+__host__ __device__ __forceinline__ void shell_node(long long t, float* __restrict__ psi, const DevState* __restrict__ st,
                                            const uint8_t* __restrict__ masks, const KParams& P)
 {
     const long long pw = P.lx + 2;                  // padded row length

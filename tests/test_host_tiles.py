@@ -1,11 +1,17 @@
-"""Tile classification of the step kernels, checked on the host (no GPU).
+"""Geometry of the step kernels, checked on the host (no GPU).
 
-tests/host_tiles.cu includes the library's headers and runs the geometry
-helpers the kernels call (box_origin, box_node_inside, tile_near,
-candidate_tile, make_kparams) on random lattices, walls, radii, positions and
-tile policies, against a brute-force scan of the lattice: the particle box
-holds exactly the sphere's nodes, every fluid node next to the sphere is in a
-near tile, and the near launch reaches every near tile exactly once.
+The two programs include the library's headers and run the helpers the
+kernels call, on random lattices, wall flags, radii and positions, against a
+brute-force scan of the lattice:
+
+* tests/host_tiles.cu (box_origin, box_node_inside, tile_near,
+  candidate_tile, make_kparams, both tile policies): the particle box holds
+  exactly the sphere's nodes, every fluid node next to the sphere is in a
+  near tile, and the near launch reaches every near tile exactly once;
+* tests/host_shell.cu (shell_node, virtual_node): every shell node of the
+  padded density field holds its periodic image or its wall-ghost mean, every
+  particle node with fluid neighbours holds the virtual-layer value, in
+  either order of the two, and the padding columns are never written.
 """
 import os
 import subprocess
@@ -15,12 +21,24 @@ from paper_1909_01092_gb300 import build
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def test_near_tiles_cover_the_sphere_exactly_once(tmp_path):
-    exe = str(tmp_path / "host_tiles")
+def _build_and_run(tmp_path, name, trials):
+    exe = str(tmp_path / name)
     cmd = [build.nvcc(), *build.ARCH_FLAGS, "-O2", "-std=c++17", "-I", build.INCLUDE, "-I", build.CSRC,
-           "-o", exe, os.path.join(HERE, "host_tiles.cu")]
+           "-o", exe, os.path.join(HERE, name + ".cu")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
-    r = subprocess.run([exe, "600"], capture_output=True, text=True, timeout=300)
+    r = subprocess.run([exe, str(trials)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert "failed 0" in r.stdout and "configurations 1200" in r.stdout, r.stdout
+    return r.stdout
+
+
+def test_near_tiles_cover_the_sphere_exactly_once(tmp_path):
+    out = _build_and_run(tmp_path, "host_tiles", 600)
+    assert "configurations 1200 failed 0" in out, out
+
+
+def test_shell_and_virtual_layer_of_the_padded_density_field(tmp_path):
+    out = _build_and_run(tmp_path, "host_shell", 300)
+    words = out.split()
+    run, failed, with_particle = (int(words[words.index(w) + 1]) for w in ("configurations", "failed", "with_particle"))
+    assert failed == 0 and run > 300 and with_particle > run // 2, out
