@@ -134,33 +134,44 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
  * FLBM_E_INVAL, FLBM_E_CUDA (launch failure). */
 int flbm_step(flbm_t* h, int64_t nsteps);
 
-/* Copy the particle record to host memory `out`; synchronises the stream.
+/* Copy the particle record (the sphere of Section 2, advanced by Newton's
+ * equation with leap-frog; F_p of Eq. (fp)) to host memory `out`;
+ * synchronises the stream. Errors: FLBM_E_INVAL (NULL argument), FLBM_E_CUDA,
  * FLBM_E_TIMEOUT if a bounded device-side wait of an earlier step gave up. */
 int flbm_particle_state(flbm_t* h, flbm_particle* out);
 
-/* Reduce the observables of the current state (FP64) into `out`;
- * synchronises the stream. Returns FLBM_E_NONFINITE if any fluid population
- * is not finite (out is still filled), FLBM_E_TIMEOUT as flbm_particle_state. */
+/* Reduce the observables of the current state (FP64) into `out`: the
+ * component masses and the total momentum of Eq. (density) over the fluid
+ * nodes, the kinetic energy, the particle's momentum and the pending mass
+ * correction; synchronises the stream. Errors: FLBM_E_INVAL (NULL argument),
+ * FLBM_E_CUDA, FLBM_E_NONFINITE if any fluid population is not finite (out
+ * is still filled), FLBM_E_TIMEOUT as flbm_particle_state. */
 int flbm_observables(flbm_t* h, flbm_obs* out);
 
 /* Copy the current populations to host_f (2*19*N float32, layout above) and,
  * if host_rho is not NULL, the densities used by the Shan-Chen force of the
  * next step (2*N float32: rho on fluid nodes, virtual-layer values on surface
- * particle nodes, 0 elsewhere). Either pointer may be NULL. Synchronises. */
+ * particle nodes, 0 elsewhere). Either pointer may be NULL. Synchronises.
+ * Errors: FLBM_E_INVAL (NULL handle), FLBM_E_CUDA. */
 int flbm_read_fields(flbm_t* h, float* host_f, float* host_rho);
 
-/* Overwrite the current populations from host_f (2*19*N float32). */
+/* Overwrite the current populations from host_f (2*19*N float32, host
+ * memory, layout above). Errors: FLBM_E_INVAL (NULL argument), FLBM_E_CUDA. */
 int flbm_write_fields(flbm_t* h, const float* host_f);
 
 /* Set the particle centre, velocity (V_{n-1/2}) and angular velocity, and
  * re-mark the particle nodes. Pending impulses and mass corrections are
- * cleared. FLBM_E_UNSUPPORTED if the simulation has no particle. */
+ * cleared. Errors: FLBM_E_INVAL (NULL argument, a non-finite value, or a
+ * centre that puts the sphere outside the walls), FLBM_E_UNSUPPORTED if the simulation has no
+ * particle, FLBM_E_CUDA. */
 int flbm_set_particle(flbm_t* h, const double X[3], const double V[3], const double Omega[3]);
 
 /* End-to-end call from host memory: copy host_f_in (2*19*N float32) to the
  * device, advance nsteps, write the particle record of every step to
  * traj[0..nsteps-1] (may be NULL), copy the final populations to host_f_out
- * (may be NULL). Synchronises before returning. */
+ * (may be NULL). Synchronises before returning. Errors: FLBM_E_INVAL (NULL
+ * handle or input, nsteps < 0), FLBM_E_NOMEM (host or device staging of the trajectory),
+ * FLBM_E_CUDA. */
 int flbm_run_host(flbm_t* h, const float* host_f_in, int64_t nsteps, float* host_f_out, flbm_particle* traj);
 
 /* Kernel classes of one step, in launch order. */
