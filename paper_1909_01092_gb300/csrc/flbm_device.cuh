@@ -15,6 +15,7 @@
 //   DevState                                         float64 particle state
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 
 namespace flbm {
@@ -135,13 +136,24 @@ __device__ __forceinline__ void from_modes(const float n[19], float f[19])
 // perturbation and the thermal noise: ((x >> 9) + 1/2) * 2^-23, exact in
 // binary32.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void philox4x32_10(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,
-                                              uint32_t k0, uint32_t k1)
+// High 32 bits of a 32 x 32-bit product (the device instruction; on the host,
+// where the header's tests run it, the 64-bit product).
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ void philox4x32_10(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,
+                                                       uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
-        const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+        const uint32_t lo0 = 0xD2511F53u * x0, hi0 = mulhi32(0xD2511F53u, x0);
+        const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = mulhi32(0xCD9E8D57u, x2);
         const uint32_t y0 = hi1 ^ x1 ^ k0;
         const uint32_t y2 = hi0 ^ x3 ^ k1;
         x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
@@ -150,9 +162,13 @@ __device__ __forceinline__ void philox4x32_10(uint32_t& x0, uint32_t& x1, uint32
     }
 }
 
-__device__ __forceinline__ float uniform_open(uint32_t x)
+__host__ __device__ __forceinline__ float uniform_open(uint32_t x)
 {
+#ifdef __CUDA_ARCH__
     return __fmaf_rn((float)(x >> 9), 1.0f / 8388608.0f, 0.5f / 8388608.0f);
+#else
+    return std::fmaf((float)(x >> 9), 1.0f / 8388608.0f, 0.5f / 8388608.0f);
+#endif
 }
 
 // ---------------------------------------------------------------------------

@@ -27,12 +27,13 @@ namespace flbm {
 // Philox4x32-10 with the round keys precomputed on the host (key + r * Weyl).
 // The high and low halves of each 32 x 32-bit product are taken separately
 // (this compiles to fewer instructions and registers than a 64-bit product).
-__device__ __forceinline__ void philox_rk(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, const KParams& P)
+__host__ __device__ __forceinline__ void philox_rk(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,
+                                                   const KParams& P)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t h0 = __umulhi(0xD2511F53u, x0), l0 = 0xD2511F53u * x0;
-        const uint32_t h1 = __umulhi(0xCD9E8D57u, x2), l1 = 0xCD9E8D57u * x2;
+        const uint32_t h0 = mulhi32(0xD2511F53u, x0), l0 = 0xD2511F53u * x0;
+        const uint32_t h1 = mulhi32(0xCD9E8D57u, x2), l1 = 0xCD9E8D57u * x2;
         const uint32_t y0 = h1 ^ x1 ^ P.rk0[r];
         const uint32_t y2 = h0 ^ x3 ^ P.rk1[r];
         x0 = y0;

@@ -1,6 +1,6 @@
-"""Geometry of the step kernels, checked on the host (no GPU).
+"""Header functions of the step kernels, checked on the host (no GPU).
 
-The two programs include the library's headers and run the helpers the
+The programs include the library's headers and run the helpers the
 kernels call, on random lattices, wall flags, radii and positions, against a
 brute-force scan of the lattice:
 
@@ -11,7 +11,11 @@ brute-force scan of the lattice:
 * tests/host_shell.cu (shell_node, virtual_node): every shell node of the
   padded density field holds its periodic image or its wall-ghost mean, every
   particle node with fluid neighbours holds the virtual-layer value, in
-  either order of the two, and the padding columns are never written.
+  either order of the two, and the padding columns are never written;
+* tests/host_philox.cu (philox4x32_10, philox_rk with the round keys that
+  make_kparams precomputes, uniform_open): the published Philox4x32-10
+  known-answer vectors, agreement of the two Philox forms on random keys and
+  counters, and the exact uniform map.
 """
 import os
 import subprocess
@@ -21,13 +25,13 @@ from paper_1909_01092_gb300 import build
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def _build_and_run(tmp_path, name, trials):
+def _build_and_run(tmp_path, name, arg):
     exe = str(tmp_path / name)
     cmd = [build.nvcc(), *build.ARCH_FLAGS, "-O2", "-std=c++17", "-I", build.INCLUDE, "-I", build.CSRC,
            "-o", exe, os.path.join(HERE, name + ".cu")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
-    r = subprocess.run([exe, str(trials)], capture_output=True, text=True, timeout=300)
+    r = subprocess.run([exe, str(arg)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     return r.stdout
 
@@ -42,3 +46,8 @@ def test_shell_and_virtual_layer_of_the_padded_density_field(tmp_path):
     words = out.split()
     run, failed, with_particle = (int(words[words.index(w) + 1]) for w in ("configurations", "failed", "with_particle"))
     assert failed == 0 and run > 300 and with_particle > run // 2, out
+
+
+def test_cuda_philox_matches_the_published_known_answers(tmp_path):
+    out = _build_and_run(tmp_path, "host_philox", os.path.join(HERE, "golden", "philox4x32_10_kat.txt"))
+    assert "kat_rows 3 draws 80000 failed 0" in out, out
