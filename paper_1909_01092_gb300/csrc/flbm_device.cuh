@@ -59,7 +59,7 @@ __host__ __device__ constexpr float bnorm(int k)
 // Forward mode transform m_k = sum_i e_k(c_i) f_i of the D3Q19 MRT basis
 // (density, momentum, 6 stress, 9 ghost modes), evaluated with opposite-pair
 // sums (even modes) and differences (odd modes).
-__device__ __forceinline__ void to_modes(const float f[19], float m[19])
+__host__ __device__ __forceinline__ void to_modes(const float f[19], float m[19])
 {
     const float s1 = f[1] + f[2], d1 = f[1] - f[2];
     const float s2 = f[3] + f[4], d2 = f[3] - f[4];
@@ -96,7 +96,7 @@ __device__ __forceinline__ void to_modes(const float f[19], float m[19])
 
 // Back transform f_i = w_i sum_k e_k(c_i) n_k with n_k = m_k / b_k already
 // normalised, split into the even and odd parts of each opposite pair.
-__device__ __forceinline__ void from_modes(const float n[19], float f[19])
+__host__ __device__ __forceinline__ void from_modes(const float n[19], float f[19])
 {
     const float k18 = 1.0f / 18.0f, k36 = 1.0f / 36.0f;
     f[0] = (n[0] - n[4] + n[16]) * (1.0f / 3.0f);

@@ -15,7 +15,10 @@ brute-force scan of the lattice:
 * tests/host_philox.cu (philox4x32_10, philox_rk with the round keys that
   make_kparams precomputes, uniform_open): the published Philox4x32-10
   known-answer vectors, agreement of the two Philox forms on random keys and
-  counters, and the exact uniform map.
+  counters, and the exact uniform map;
+* tests/host_modes.cu (to_modes, from_modes, bnorm): the collision's
+  hand-factored transforms against the D3Q19 mode basis written out from its
+  polynomials, exactly, and their round trip.
 """
 import os
 import subprocess
@@ -51,3 +54,8 @@ def test_shell_and_virtual_layer_of_the_padded_density_field(tmp_path):
 def test_cuda_philox_matches_the_published_known_answers(tmp_path):
     out = _build_and_run(tmp_path, "host_philox", os.path.join(HERE, "golden", "philox4x32_10_kat.txt"))
     assert "kat_rows 3 draws 80000 failed 0" in out, out
+
+
+def test_collision_mode_transforms_match_the_basis_polynomials(tmp_path):
+    out = _build_and_run(tmp_path, "host_modes", "")
+    assert "failed 0" in out, out
