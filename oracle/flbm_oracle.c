@@ -619,7 +619,11 @@ static void cover_uncover(oracle* o, const double Xold[3])
                 for (int a = 0; a < 3; ++a) { o->Ppend[a] += j[a]; o->Lpend[a] += t[a]; }
             }
     /* Uncovered nodes: equilibrium at the neighbour-mean densities and the
-     * local surface velocity; the particle pays the momentum. [R] */
+     * local surface velocity; the particle pays the momentum. [R]
+     * Parity unpinned: Section 2 defers this rule to Jansen and Harting
+     * (2011). Only its consequences are pinned: exact mass and momentum
+     * closure, the square channel's symmetries through uncover events, and
+     * the uniform-flow case, where the mean is the bulk density. */
     for (int64_t z = 0; z < o->p.lz; ++z)
         for (int64_t y = 0; y < o->p.ly; ++y)
             for (int64_t x = 0; x < o->p.lx; ++x) {
