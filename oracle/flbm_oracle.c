@@ -620,10 +620,12 @@ static void cover_uncover(oracle* o, const double Xold[3])
             }
     /* Uncovered nodes: equilibrium at the neighbour-mean densities and the
      * local surface velocity; the particle pays the momentum. [R]
-     * Parity unpinned: Section 2 defers this rule to Jansen and Harting
-     * (2011). Only its consequences are pinned: exact mass and momentum
-     * closure, the square channel's symmetries through uncover events, and
-     * the uniform-flow case, where the mean is the bulk density. */
+     * Section 2 defers this rule to Jansen and Harting (2011). Pinned by a
+     * sphere moving with a uniform flow through uncover events (the refill
+     * must reproduce the flow exactly, with arbitrary values inside the
+     * sphere), by exact mass and momentum closure and by the square
+     * channel's symmetries. The rotational part of the surface velocity is
+     * pinned only through the moving link rule, which uses the same formula. */
     for (int64_t z = 0; z < o->p.lz; ++z)
         for (int64_t y = 0; y < o->p.ly; ++y)
             for (int64_t x = 0; x < o->p.lx; ++x) {

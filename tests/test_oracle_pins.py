@@ -660,6 +660,62 @@ def test_sphere_comoving_with_uniform_flow_is_invisible(oracle_mod):
         assert np.allclose(g[l][:, keep], f[l][:, keep], rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("G", [0.0, 1.2])
+def test_uncovered_nodes_are_refilled_with_the_comoving_flow(oracle_mod, G):
+    """Cover and uncover (Section 2, particle paragraph) leave a flow that
+    moves with the sphere unchanged. The fluid starts each step exactly
+    uniform at f_eq(rho_l, U) and the sphere moves at U. The particle nodes
+    hold arbitrary values, since their populations are not part of the state.
+    After one step every fluid node, newly uncovered ones included, must hold
+    f_eq(rho_l, U) again.
+
+    So the refill of an uncovered node must use the sphere's surface velocity
+    and the density of its fluid neighbours. A refill at rest fails this. So
+    does a mean that takes in particle nodes or other uncovered nodes (they
+    hold the arbitrary values). The step's ledgers must also match exactly:
+    the mass ledger is rho_l (covered - uncovered), the pending impulse is
+    rho_tot U (covered - uncovered), and force and torque vanish. The
+    sphere is stepped along a trajectory X_k = X_0 + k U, one fresh step per
+    position, so that each step meets different cover and uncover sets.
+    Only the translational part of the surface velocity is pinned here (the
+    sphere does not spin)."""
+    U = np.array([0.29, -0.23, 0.31])
+    L = (16, 15, 17)
+    X0 = np.array([7.13, 6.71, 8.37])
+    rho = (1.0, 0.05)
+    rng = np.random.default_rng(5)
+    n_cov = n_unc = 0
+    for k in range(8):
+        X = np.mod(X0 + k * U, L)
+        p = W.params(lx=L[0], ly=L[1], lz=L[2], wall=(0, 0, 0), G=G, init_pert=0.0, radius=3.3,
+                     rho_p_ratio=2.0, delta_rho=0.0, pos0=tuple(X))
+        o = oracle_mod.Oracle(p)
+        o.set_particle(X, V=U)
+        solid0 = o.fields()["solid"].copy()
+        f = np.empty((2, 19, L[2], L[1], L[0]))
+        for l in range(2):
+            f[l] = _feq(rho[l], U)[:, None, None, None]
+            f[l][:, solid0] = rng.uniform(0.0, 3.0, size=(19, int(solid0.sum())))
+        o.set_f(f)
+        o.step(1)
+        pa = o.particle()
+        assert np.allclose(pa["V"], U, rtol=0, atol=1e-16)
+        assert np.abs(pa["F"]).max() < 1e-13
+        assert np.abs(pa["T"]).max() < 1e-12
+        solid1 = o.fields()["solid"]
+        cov = int((solid1 & ~solid0).sum())
+        unc = int((solid0 & ~solid1).sum())
+        n_cov += cov
+        n_unc += unc
+        g = o.get_f()
+        fluid = ~solid1
+        for l in range(2):
+            assert np.allclose(g[l][:, fluid], _feq(rho[l], U)[:, None], rtol=0, atol=2e-15), (k, l)
+            assert abs(pa["delta"][l] * pa["nfluid"] - rho[l] * (cov - unc)) < 1e-13
+        assert np.allclose(pa["Ppend"], sum(rho) * U * (cov - unc), rtol=0, atol=1e-13)
+    assert n_unc >= 40 and n_cov >= 40, (n_cov, n_unc)
+
+
 # ---------------------------------------------------------------------------
 # Brute force on a 4^3 box
 # ---------------------------------------------------------------------------
