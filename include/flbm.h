@@ -94,7 +94,22 @@ typedef struct flbm_particle {
     int64_t step;         /* completed steps */
 } flbm_particle;
 
-/* Observables of the current state (host memory, filled by the library). */
+/* Observables of the current state (host memory, filled by the library).
+ *
+ * The "temperatures" below check the fluctuation-dissipation requirement of
+ * Section 2 (thermal noise on the non-conserved modes, none on mass and total
+ * momentum). They are reduced over the bulk fluid nodes: fluid nodes with no
+ * particle node among their 18 neighbours. With m_lk = sum_i e_k(c_i) f_li the
+ * modes of component l (the basis of Section 2's MRT collision, in the order
+ * 1, c, c^2-1, 3c_x^2-c^2, c_y^2-c_z^2, c_xc_y, c_yc_z, c_xc_z, (3c^2-5)c,
+ * (c_y^2-c_z^2)c_x and cyclic, 3c^4-6c^2+1, (2c^2-3)(3c_x^2-c^2),
+ * (2c^2-3)(c_y^2-c_z^2)), b_k their norms sum_i w_i e_k(c_i)^2, and
+ * n_lk = m_lk - m_lk^eq(rho_l, u) with u = (j_A + j_B)/rho_tot:
+ *   mode_temp[l][k] = sum n_lk^2 / (3 b_k sum rho_l), k = 4..18;
+ *   diff_temp[a]    = sum d_a^2 / sum (rho_A rho_B / rho_tot),
+ *                     d = (rho_B j_A - rho_A j_B)/rho_tot (interdiffusion current);
+ *   mom_temp[a]     = sum j_a^2 / sum rho_tot, j = j_A + j_B.
+ * In a thermalised ideal mixture (G = 0) every one of them equals kT. */
 typedef struct flbm_obs {
     double mass[2];              /* sum over fluid nodes of rho_A, rho_B */
     double momentum[3];          /* sum over fluid nodes of sum_l sum_i f_li c_i */
@@ -104,6 +119,10 @@ typedef struct flbm_obs {
     int64_t nfluid;
     int64_t step;
     int64_t nonfinite;           /* number of non-finite populations on fluid nodes */
+    double mode_temp[2][19];     /* per component and mode, as above; entries k = 0..3 are 0 */
+    double diff_temp[3];         /* interdiffusion current per axis, as above */
+    double mom_temp[3];          /* total momentum per axis, as above */
+    int64_t n_bulk;              /* bulk fluid nodes the temperatures are reduced over */
 } flbm_obs;
 
 typedef struct flbm_sim flbm_t;
@@ -142,8 +161,10 @@ int flbm_particle_state(flbm_t* h, flbm_particle* out);
 
 /* Reduce the observables of the current state (FP64) into `out`: the
  * component masses and the total momentum of Eq. (density) over the fluid
- * nodes, the kinetic energy, the particle's momentum and the pending mass
- * correction; synchronises the stream. Errors: FLBM_E_INVAL (NULL argument),
+ * nodes, the kinetic energy, the particle's momentum, the pending mass
+ * correction and the mode, interdiffusion and momentum temperatures of the
+ * fluctuating modes (Section 2; definitions at flbm_obs); synchronises the
+ * stream. Errors: FLBM_E_INVAL (NULL argument),
  * FLBM_E_CUDA, FLBM_E_NONFINITE if any fluid population is not finite (out
  * is still filled), FLBM_E_TIMEOUT as flbm_particle_state. */
 int flbm_observables(flbm_t* h, flbm_obs* out);

@@ -89,6 +89,7 @@ def _load():
         lib.oracle_set_particle.argtypes = [P, dp, dp, dp]
         lib.oracle_fields.argtypes = [P, dp, dp, dp, dp, dp]
         lib.oracle_observables.argtypes = [P, dp]
+        lib.oracle_mode_temps.argtypes = [P, dp]
         lib.oracle_lattice.argtypes = [dp, dp, ctypes.POINTER(ctypes.c_int64), dp, dp]
         lib.oracle_philox.argtypes = [u32p, u32p, u32p]
         lib.oracle_normals.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32, dp]
@@ -198,6 +199,16 @@ class Oracle:
         self.lib.oracle_observables(self.h, _dptr(out))
         return dict(mass=out[0:2].copy(), momentum=out[2:5].copy(), kinetic=float(out[5]),
                     particle_momentum=out[6:9].copy(), pending_mass=out[9:11].copy())
+
+
+    def mode_temps(self) -> dict:
+        """Temperatures of the fluctuating modes over the bulk fluid nodes:
+        mode_temp (2, 19) for k = 4..18, interdiffusion diff_temp (3),
+        momentum mom_temp (3), node count n_bulk."""
+        out = np.empty(45)
+        self.lib.oracle_mode_temps(self.h, _dptr(out))
+        return dict(mode_temp=out[:38].reshape(2, 19).copy(), diff_temp=out[38:41].copy(),
+                    mom_temp=out[41:44].copy(), n_bulk=int(out[44]))
 
 
 def lattice() -> dict:

@@ -794,6 +794,67 @@ void oracle_observables(const oracle* o, double* out)
     out[10] = o->delta[1] * (double)o->nfluid;
 }
 
+/* Temperatures of the fluctuating modes (Section 2: thermal noise on the
+ * non-conserved modes, in compliance with the fluctuation-dissipation
+ * relation; none on mass and total momentum). Sums over the bulk fluid nodes,
+ * the fluid nodes with no particle node among their 18 neighbours. With the
+ * modes m_lk = sum_i e_k(c_i) f_li of each component, u = (j_A + j_B)/rho_tot
+ * and m_lk^eq = sum_i e_k(c_i) f_eq,i(rho_l, u):
+ *   out[19 l + k] = sum (m_lk - m_lk^eq)^2 / (3 b_k sum rho_l), k = 4..18 (0 for k < 4)
+ *   out[38 + a]   = sum d_a^2 / sum (rho_A rho_B / rho_tot), d = (rho_B j_A - rho_A j_B)/rho_tot
+ *   out[41 + a]   = sum j_a^2 / sum rho_tot, j = j_A + j_B
+ *   out[44]       = number of bulk fluid nodes.
+ * In a thermalised ideal mixture each temperature equals kT. */
+void oracle_mode_temps(const oracle* o, double* out)
+{
+    double s2[2][19], sr[2] = {0, 0}, sd[3] = {0, 0, 0}, sdr = 0.0, sj[3] = {0, 0, 0};
+    int64_t cnt = 0;
+    memset(s2, 0, sizeof(s2));
+    for (int64_t z = 0; z < o->p.lz; ++z)
+        for (int64_t y = 0; y < o->p.ly; ++y)
+            for (int64_t x = 0; x < o->p.lx; ++x) {
+                int64_t n = nidx(o, x, y, z);
+                if (o->solid[n]) continue;
+                int next_to_particle = 0;
+                for (int i = 1; i < 19; ++i) {
+                    int64_t q[3];
+                    if (!neighbour(o, x, y, z, i, q) && o->solid[nidx(o, q[0], q[1], q[2])]) next_to_particle = 1;
+                }
+                if (next_to_particle) continue;
+                double m[2][19];
+                for (int l = 0; l < 2; ++l)
+                    for (int k = 0; k < 19; ++k) {
+                        m[l][k] = 0.0;
+                        for (int i = 0; i < 19; ++i) m[l][k] += EM[k][i] * F_AT(o->f, l, i, n);
+                    }
+                double rt = m[0][0] + m[1][0];
+                double j[3] = {m[0][1] + m[1][1], m[0][2] + m[1][2], m[0][3] + m[1][3]};
+                double u[3] = {j[0] / rt, j[1] / rt, j[2] / rt};
+                for (int l = 0; l < 2; ++l) {
+                    for (int k = 4; k < 19; ++k) {
+                        double meq = 0.0;
+                        for (int i = 0; i < 19; ++i) meq += EM[k][i] * feq(i, m[l][0], u);
+                        s2[l][k] += (m[l][k] - meq) * (m[l][k] - meq);
+                    }
+                    sr[l] += m[l][0];
+                }
+                for (int a = 0; a < 3; ++a) {
+                    double d = (m[1][0] * m[0][1 + a] - m[0][0] * m[1][1 + a]) / rt;
+                    sd[a] += d * d;
+                    sj[a] += j[a] * j[a];
+                }
+                sdr += m[0][0] * m[1][0] / rt;
+                ++cnt;
+            }
+    for (int l = 0; l < 2; ++l)
+        for (int k = 0; k < 19; ++k) out[19 * l + k] = (k >= 4 && sr[l] > 0.0) ? s2[l][k] / (3.0 * BN[k] * sr[l]) : 0.0;
+    for (int a = 0; a < 3; ++a) {
+        out[38 + a] = sdr > 0.0 ? sd[a] / sdr : 0.0;
+        out[41 + a] = (sr[0] + sr[1]) > 0.0 ? sj[a] / (sr[0] + sr[1]) : 0.0;
+    }
+    out[44] = (double)cnt;
+}
+
 /* Lattice tables for the tests: c[19][3], w[19], opp[19], e[19][19] (mode
  * k, direction i), b[19]. */
 void oracle_lattice(double* c, double* w, int64_t* opp, double* e, double* b)

@@ -71,6 +71,8 @@ class Obs(ctypes.Structure):
         ("mass", ctypes.c_double * 2), ("momentum", ctypes.c_double * 3), ("kinetic", ctypes.c_double),
         ("particle_momentum", ctypes.c_double * 3), ("pending_mass", ctypes.c_double * 2),
         ("nfluid", ctypes.c_int64), ("step", ctypes.c_int64), ("nonfinite", ctypes.c_int64),
+        ("mode_temp", (ctypes.c_double * 19) * 2), ("diff_temp", ctypes.c_double * 3),
+        ("mom_temp", ctypes.c_double * 3), ("n_bulk", ctypes.c_int64),
     ]
 
 
@@ -179,7 +181,9 @@ def particle_dict(r: Particle) -> dict:
 def obs_dict(r: Obs) -> dict:
     return dict(mass=np.array(r.mass[:]), momentum=np.array(r.momentum[:]), kinetic=r.kinetic,
                 particle_momentum=np.array(r.particle_momentum[:]), pending_mass=np.array(r.pending_mass[:]),
-                nfluid=r.nfluid, step=r.step, nonfinite=r.nonfinite)
+                nfluid=r.nfluid, step=r.step, nonfinite=r.nonfinite,
+                mode_temp=np.array([r.mode_temp[l][:] for l in range(2)]), diff_temp=np.array(r.diff_temp[:]),
+                mom_temp=np.array(r.mom_temp[:]), n_bulk=r.n_bulk)
 
 
 class Sim:

@@ -312,7 +312,9 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
         cudaMalloc(&h->box_counts, sizeof(int) * h->box_blocks) != cudaSuccess ||
         cudaMalloc(&h->box_parts, sizeof(double) * 8 * h->box_blocks) != cudaSuccess ||
         cudaMalloc(&h->obs_tiles, sizeof(double) * 8 * h->ntiles) != cudaSuccess ||
-        cudaMalloc(&h->obs_out, sizeof(double) * 8) != cudaSuccess)
+        cudaMalloc(&h->obs_out, sizeof(double) * 8) != cudaSuccess ||
+        cudaMalloc(&h->obs_mode_tiles, sizeof(double) * kObsModes * h->ntiles) != cudaSuccess ||
+        cudaMalloc(&h->obs_mode_out, sizeof(double) * kObsModes) != cudaSuccess)
         return bail(FLBM_E_NOMEM);
 
     {
@@ -480,12 +482,18 @@ int flbm_observables(flbm_t* h, flbm_obs* out)
     if (int rc = launch_check(h, "k_obs_tiles")) return rc;
     k_obs_final<<<1, 1024, 0, h->stream>>>(h->obs_tiles, h->ntiles, h->obs_out);
     if (int rc = launch_check(h, "k_obs_final")) return rc;
-    double v[8];
+    k_obs_modes<<<h->grid, h->block, 0, h->stream>>>(h->fbuf[h->cur], h->st, h->masks, h->obs_mode_tiles, k);
+    if (int rc = launch_check(h, "k_obs_modes")) return rc;
+    k_obs_final_n<kObsModes><<<1, 1024, 0, h->stream>>>(h->obs_mode_tiles, h->ntiles, h->obs_mode_out);
+    if (int rc = launch_check(h, "k_obs_final_n")) return rc;
+    double v[8], vm[kObsModes];
     DevState s;
     CK(h, cudaMemcpyAsync(v, h->obs_out, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(vm, h->obs_mode_out, sizeof(vm), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemcpyAsync(&s, h->st, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     fill_obs(v, s, out);
+    fill_mode_obs(vm, out);
     if (s.err) return fail(h, FLBM_E_TIMEOUT, "a bounded device-side wait gave up");
     return out->nonfinite ? fail(h, FLBM_E_NONFINITE, "non-finite populations") : FLBM_OK;
 }
@@ -640,6 +648,8 @@ void flbm_destroy(flbm_t* h)
     cudaFree(h->box_parts);
     cudaFree(h->obs_tiles);
     cudaFree(h->obs_out);
+    cudaFree(h->obs_mode_tiles);
+    cudaFree(h->obs_mode_out);
     cudaFree(h->scratch_rho);
     cudaFree(h->traj_dev);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);

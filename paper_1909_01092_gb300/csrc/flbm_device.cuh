@@ -58,41 +58,45 @@ __host__ __device__ constexpr float bnorm(int k)
 
 // Forward mode transform m_k = sum_i e_k(c_i) f_i of the D3Q19 MRT basis
 // (density, momentum, 6 stress, 9 ghost modes), evaluated with opposite-pair
-// sums (even modes) and differences (odd modes).
-__host__ __device__ __forceinline__ void to_modes(const float f[19], float m[19])
+// sums (even modes) and differences (odd modes); T = float in the step, double
+// in the observables.
+template <class T>
+__host__ __device__ __forceinline__ void to_modes_t(const T f[19], T m[19])
 {
-    const float s1 = f[1] + f[2], d1 = f[1] - f[2];
-    const float s2 = f[3] + f[4], d2 = f[3] - f[4];
-    const float s3 = f[5] + f[6], d3 = f[5] - f[6];
-    const float s7 = f[7] + f[8], d7 = f[7] - f[8];
-    const float s9 = f[9] + f[10], d9 = f[9] - f[10];
-    const float s11 = f[11] + f[12], d11 = f[11] - f[12];
-    const float s13 = f[13] + f[14], d13 = f[13] - f[14];
-    const float s15 = f[15] + f[16], d15 = f[15] - f[16];
-    const float s17 = f[17] + f[18], d17 = f[17] - f[18];
-    const float sax = s1 + s2 + s3;
-    const float sxy = s7 + s9, sxz = s11 + s13, syz = s15 + s17;
-    const float sdg = sxy + sxz + syz;
+    const T s1 = f[1] + f[2], d1 = f[1] - f[2];
+    const T s2 = f[3] + f[4], d2 = f[3] - f[4];
+    const T s3 = f[5] + f[6], d3 = f[5] - f[6];
+    const T s7 = f[7] + f[8], d7 = f[7] - f[8];
+    const T s9 = f[9] + f[10], d9 = f[9] - f[10];
+    const T s11 = f[11] + f[12], d11 = f[11] - f[12];
+    const T s13 = f[13] + f[14], d13 = f[13] - f[14];
+    const T s15 = f[15] + f[16], d15 = f[15] - f[16];
+    const T s17 = f[17] + f[18], d17 = f[17] - f[18];
+    const T sax = s1 + s2 + s3;
+    const T sxy = s7 + s9, sxz = s11 + s13, syz = s15 + s17;
+    const T sdg = sxy + sxz + syz;
     m[0] = f[0] + sax + sdg;
     m[1] = d1 + d7 + d9 + d11 + d13;
     m[2] = d2 + d7 - d9 + d15 + d17;
     m[3] = d3 + d11 - d13 + d15 - d17;
     m[4] = sdg - f[0];
-    m[5] = 2.0f * s1 - s2 - s3 + sxy + sxz - 2.0f * syz;
+    m[5] = T(2) * s1 - s2 - s3 + sxy + sxz - T(2) * syz;
     m[6] = s2 - s3 + sxy - sxz;
     m[7] = s7 - s9;
     m[8] = s15 - s17;
     m[9] = s11 - s13;
-    m[10] = -2.0f * d1 + d7 + d9 + d11 + d13;
-    m[11] = -2.0f * d2 + d7 - d9 + d15 + d17;
-    m[12] = -2.0f * d3 + d11 - d13 + d15 - d17;
+    m[10] = -T(2) * d1 + d7 + d9 + d11 + d13;
+    m[11] = -T(2) * d2 + d7 - d9 + d15 + d17;
+    m[12] = -T(2) * d3 + d11 - d13 + d15 - d17;
     m[13] = d7 + d9 - d11 - d13;
     m[14] = -d7 + d9 + d15 + d17;
     m[15] = d11 - d13 - d15 + d17;
-    m[16] = f[0] - 2.0f * sax + sdg;
-    m[17] = -2.0f * s1 + s2 + s3 + sxy + sxz - 2.0f * syz;
+    m[16] = f[0] - T(2) * sax + sdg;
+    m[17] = -T(2) * s1 + s2 + s3 + sxy + sxz - T(2) * syz;
     m[18] = -s2 + s3 + sxy - sxz;
 }
+
+__host__ __device__ __forceinline__ void to_modes(const float f[19], float m[19]) { to_modes_t<float>(f, m); }
 
 // Back transform f_i = w_i sum_k e_k(c_i) n_k with n_k = m_k / b_k already
 // normalised, split into the even and odd parts of each opposite pair.

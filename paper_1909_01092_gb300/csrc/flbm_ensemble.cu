@@ -193,6 +193,8 @@ struct flbm_ens {
     long long off[W_COUNT + 1] = {};  // work list k = d_items[off[k] .. off[k+1])
     double* obs_tiles = nullptr;
     double* obs_out = nullptr;
+    double* obs_mode_tiles = nullptr;
+    double* obs_mode_out = nullptr;
     long long max_tiles = 0;
     int cur = 0;                   // all replicas read f[cur] in the next step
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -348,7 +350,9 @@ int allocate(flbm_ens* e)
     ECK(e, cudaMemsetAsync(e->arena, 0, off, e->stream));
     if (cudaMalloc(&e->d_reps, sizeof(RepDesc) * e->n) != cudaSuccess ||
         cudaMalloc(&e->obs_tiles, sizeof(double) * 8 * e->max_tiles) != cudaSuccess ||
-        cudaMalloc(&e->obs_out, sizeof(double) * 8) != cudaSuccess)
+        cudaMalloc(&e->obs_out, sizeof(double) * 8) != cudaSuccess ||
+        cudaMalloc(&e->obs_mode_tiles, sizeof(double) * kObsModes * e->max_tiles) != cudaSuccess ||
+        cudaMalloc(&e->obs_mode_out, sizeof(double) * kObsModes) != cudaSuccess)
         return efail(e, FLBM_E_NOMEM, "ensemble descriptors");
     char* base = static_cast<char*>(e->arena);
     e->d_states = reinterpret_cast<DevState*>(base);
@@ -608,12 +612,19 @@ int flbm_ensemble_observables(flbm_ens_t* e, int32_t r, flbm_obs* out)
     if (int rc = elaunch(e, "k_obs_tiles")) return rc;
     k_obs_final<<<1, 1024, 0, e->stream>>>(e->obs_tiles, tile_count(k), e->obs_out);
     if (int rc = elaunch(e, "k_obs_final")) return rc;
-    double v[8];
+    k_obs_modes<<<dim3(k.gx, k.gy, k.lz), dim3(k.tx, k.ty, 1), 0, e->stream>>>(d.f[e->cur], d.st, d.masks,
+                                                                               e->obs_mode_tiles, k);
+    if (int rc = elaunch(e, "k_obs_modes")) return rc;
+    k_obs_final_n<kObsModes><<<1, 1024, 0, e->stream>>>(e->obs_mode_tiles, tile_count(k), e->obs_mode_out);
+    if (int rc = elaunch(e, "k_obs_final_n")) return rc;
+    double v[8], vm[kObsModes];
     DevState s;
     ECK(e, cudaMemcpyAsync(v, e->obs_out, sizeof(v), cudaMemcpyDeviceToHost, e->stream));
+    ECK(e, cudaMemcpyAsync(vm, e->obs_mode_out, sizeof(vm), cudaMemcpyDeviceToHost, e->stream));
     ECK(e, cudaMemcpyAsync(&s, d.st, sizeof(s), cudaMemcpyDeviceToHost, e->stream));
     ECK(e, cudaStreamSynchronize(e->stream));
     fill_obs(v, s, out);
+    fill_mode_obs(vm, out);
     return out->nonfinite ? efail(e, FLBM_E_NONFINITE, "non-finite populations") : FLBM_OK;
 }
 
@@ -640,6 +651,8 @@ void flbm_ensemble_destroy(flbm_ens_t* e)
     cudaFree(e->d_items);
     cudaFree(e->obs_tiles);
     cudaFree(e->obs_out);
+    cudaFree(e->obs_mode_tiles);
+    cudaFree(e->obs_mode_out);
     delete e;
 }
 

@@ -157,6 +157,24 @@ inline void fill_obs(const double v[8], const DevState& s, flbm_obs* out)
     out->nonfinite = (int64_t)v[6];
 }
 
+// Temperatures of the fluctuating modes from the kObsModes sums of
+// k_obs_modes (definitions at flbm_obs): each is a ratio of two sums over the
+// bulk fluid nodes.
+inline void fill_mode_obs(const double vm[kObsModes], flbm_obs* out)
+{
+    const double b[19] = {1, 1. / 3, 1. / 3, 1. / 3, 2. / 3, 4. / 3, 4. / 9, 1. / 9, 1. / 9, 1. / 9,
+                          2. / 3, 2. / 3, 2. / 3, 2. / 9, 2. / 9, 2. / 9, 2, 4. / 3, 4. / 9};
+    for (int l = 0; l < 2; ++l)
+        for (int k = 0; k < 19; ++k)
+            out->mode_temp[l][k] = (k >= 4 && vm[30 + l] > 0.0) ? vm[15 * l + k - 4] / (3.0 * b[k] * vm[30 + l]) : 0.0;
+    const double rt = vm[30] + vm[31];
+    for (int a = 0; a < 3; ++a) {
+        out->diff_temp[a] = vm[35] > 0.0 ? vm[32 + a] / vm[35] : 0.0;
+        out->mom_temp[a] = rt > 0.0 ? vm[36 + a] / rt : 0.0;
+    }
+    out->n_bulk = (int64_t)vm[39];
+}
+
 inline int copy_particle(const DevState& s, flbm_particle* out)
 {
     for (int a = 0; a < 3; ++a) {

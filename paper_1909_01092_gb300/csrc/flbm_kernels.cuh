@@ -308,6 +308,118 @@ static __global__ void __launch_bounds__(1024) k_obs_final(const double* __restr
     if (threadIdx.x < 8) out[threadIdx.x] = s_out[threadIdx.x];
 }
 
+// ---------------------------------------------------------------------------
+// Fluctuation observables (Section 2, fluctuation-dissipation): per-tile FP64
+// sums over the bulk fluid nodes (fluid, no particle node among the 18
+// neighbours) of
+//   [0..29]  n_lk^2 for l = A, B and k = 4..18, n_lk = m_lk - m_lk^eq(rho_l, u)
+//   [30..31] rho_A, rho_B
+//   [32..34] d_a^2, d = (rho_B j_A - rho_A j_B) / rho_tot
+//   [35]     rho_A rho_B / rho_tot
+//   [36..38] j_a^2, j = j_A + j_B
+//   [39]     node count
+// with u = j / rho_tot. The host turns them into temperatures.
+// ---------------------------------------------------------------------------
+constexpr int kObsModes = 40;
+
+__device__ __forceinline__ bool has_particle_neighbour(int x, int y, int z, const int o[3], const uint8_t* mask,
+                                                       const KParams& P)
+{
+    const int L[3] = {P.lx, P.ly, P.lz};
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        int q[3] = {x + cxv(i), y + cyv(i), z + czv(i)};
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (q[a] < 0 || q[a] >= L[a]) {
+                if (P.wall[a]) ok = false;
+                else q[a] += (q[a] < 0) ? L[a] : -L[a];
+            }
+        }
+        if (ok && is_solid(q[0], q[1], q[2], o, mask, P)) return true;
+    }
+    return false;
+}
+
+static __global__ void __launch_bounds__(kThreads) k_obs_modes(const float* __restrict__ f,
+                                                               const DevState* __restrict__ st,
+                                                               const uint8_t* __restrict__ masks,
+                                                               double* __restrict__ out, KParams P)
+{
+    __shared__ double s_red[(kThreads / 32) * 8];
+    __shared__ double s_out[kObsModes];
+    const int x = blockIdx.x * P.tx + threadIdx.x;
+    const int y = blockIdx.y * P.ty + threadIdx.y;
+    const int z = blockIdx.z;
+    double v[kObsModes];
+#pragma unroll
+    for (int q = 0; q < kObsModes; ++q) v[q] = 0.0;
+    bool bulk = x < P.lx && y < P.ly;
+    if (bulk && P.has_particle) {
+        const int o[3] = {st->box0[0], st->box0[1], st->box0[2]};
+        const uint8_t* mask = masks + (size_t)st->cur * P.B * P.B * P.B;
+        bulk = !is_solid(x, y, z, o, mask, P) && !has_particle_neighbour(x, y, z, o, mask, P);
+    }
+    if (bulk) {
+        const long long n = x + (long long)P.lx * (y + (long long)P.ly * z);
+        double m[2][19];
+        for (int l = 0; l < 2; ++l) {
+            double fl[19];
+#pragma unroll
+            for (int i = 0; i < 19; ++i) fl[i] = (double)f[(long long)(19 * l + i) * P.N + n];
+            to_modes_t<double>(fl, m[l]);
+        }
+        const double rt = m[0][0] + m[1][0];
+        const double j[3] = {m[0][1] + m[1][1], m[0][2] + m[1][2], m[0][3] + m[1][3]};
+        const double u[3] = {j[0] / rt, j[1] / rt, j[2] / rt};
+        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const double eq[6] = {uu, 3.0 * u[0] * u[0] - uu, u[1] * u[1] - u[2] * u[2],
+                              u[0] * u[1], u[1] * u[2], u[0] * u[2]};
+        for (int l = 0; l < 2; ++l) {
+#pragma unroll
+            for (int k = 4; k < 19; ++k) {
+                const double nk = k <= 9 ? m[l][k] - m[l][0] * eq[k - 4] : m[l][k];
+                v[15 * l + k - 4] = nk * nk;
+            }
+            v[30 + l] = m[l][0];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double d = (m[1][0] * m[0][1 + a] - m[0][0] * m[1][1 + a]) / rt;
+            v[32 + a] = d * d;
+            v[36 + a] = j[a] * j[a];
+        }
+        v[35] = m[0][0] * m[1][0] / rt;
+        v[39] = 1.0;
+    }
+#pragma unroll
+    for (int c = 0; c < kObsModes / 8; ++c) block_sum8<kThreads>(v + 8 * c, s_red, s_out + 8 * c);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const long long tile = blockIdx.x + (long long)P.gx * (blockIdx.y + (long long)P.gy * blockIdx.z);
+        for (int k = 0; k < kObsModes; ++k) out[tile * kObsModes + k] = s_out[k];
+    }
+}
+
+// Sum of NV per-tile values over the tiles, in tile order per thread and a
+// fixed reduction tree (deterministic).
+template <int NV>
+static __global__ void __launch_bounds__(1024) k_obs_final_n(const double* __restrict__ tiles, long long ntiles,
+                                                             double* __restrict__ out)
+{
+    __shared__ double s_red[(1024 / 32) * 8];
+    __shared__ double s_out[NV];
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    for (long long t = threadIdx.x; t < ntiles; t += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += tiles[t * NV + k];
+#pragma unroll
+    for (int c = 0; c < NV / 8; ++c) block_sum8<1024>(v + 8 * c, s_red, s_out + 8 * c);
+    if (threadIdx.x < NV) out[threadIdx.x] = s_out[threadIdx.x];
+}
+
 // Unpad psi interior into a dense [2][N] array.
 static __global__ void k_unpad(const float* __restrict__ psi, float* __restrict__ out, KParams P)
 {

@@ -30,6 +30,8 @@ struct flbm_sim {
     long long ncand = 0;
     double* obs_tiles = nullptr;
     double* obs_out = nullptr;
+    double* obs_mode_tiles = nullptr;  // per tile: kObsModes sums of k_obs_modes
+    double* obs_mode_out = nullptr;
     float* scratch_rho = nullptr;
     DevState* traj_dev = nullptr;
     size_t traj_cap = 0;

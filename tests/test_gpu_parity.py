@@ -3,11 +3,14 @@
 Both sides start from the same seeded input (the method's own Philox-seeded
 initial state, or a seeded random population field from
 paper_1909_01092_gb300.workloads) and are compared element by element on the
-fluid nodes. Tolerances: every population within 1e-5 relative to the mean
-magnitude of its (component, direction) field, noise-free and noisy runs alike
-(both sides draw the same Philox normals; with noise a few populations of the
-minority component pass close to zero, where an element-wise ratio is
-meaningless); the particle velocity within 1e-4 of its velocity scale.
+fluid nodes. Tolerances:
+* noise-free runs: every population within 1e-5 of its own value
+  (element-wise relative error);
+* noisy runs: every population within 1e-5 of the mean magnitude of its
+  (component, direction) field. Both sides draw the same Philox normals, but a
+  few populations of the minority component pass close to zero, where an
+  element-wise ratio says nothing about the arithmetic;
+* the particle velocity within 1e-4 of its velocity scale.
 """
 import math
 
@@ -46,11 +49,25 @@ def _fluid_mask(orc):
 
 
 def _max_rel(g, o, mask):
-    """max |g - o| / mean|o| per (component, direction), over fluid nodes."""
+    """max |g - o| / mean|o| per (component, direction), over fluid nodes
+    (noisy runs)."""
     g = g[:, :, mask].astype(np.float64)
     o = o[:, :, mask]
     scale = np.mean(np.abs(o), axis=2, keepdims=True)
     return float(np.max(np.abs(g - o) / scale))
+
+
+def _max_rel_elem(g, o, mask):
+    """max |g - o| / |o| over every population of every fluid node
+    (noise-free runs)."""
+    g = g[:, :, mask].astype(np.float64)
+    o = o[:, :, mask]
+    return float(np.max(np.abs(g - o) / np.abs(o)))
+
+
+def _rel_err(g, o, mask, p):
+    """Element-wise relative error without noise, mean-normalised with it."""
+    return (_max_rel_elem if p["kT"] == 0 else _max_rel)(g, o, mask)
 
 
 def _pair(flbm, oracle_mod, p, init_seed=None, X=None, V=(0, 0, 0), Om=(0, 0, 0)):
@@ -111,7 +128,8 @@ def test_fluid_parity(flbm, oracle_mod, name, p, steps, seed):
     sim.step(steps)
     orc.step(steps)
     assert sim.launches() == _launches_per_step(p) * steps
-    err = _max_rel(sim.read_f(), orc.get_f(), _fluid_mask(orc))
+    err = _rel_err(sim.read_f(), orc.get_f(), _fluid_mask(orc), p)
+    print(f"{name}: max rel err {err:.3e}")
     assert err < RTOL_F, f"{name}: max rel err {err:.3e}"
 
 
@@ -134,7 +152,8 @@ def test_channel_small_100_noise_free_steps(flbm, oracle_mod):
     # float32 populations bound its error by ~1e-6 of that sum, i.e. well under
     # 1e-3 of the driving force F_p.
     assert np.max(np.abs(pg["F"] - po["F"])) <= 1e-3 * abs(po["Fp"])
-    err = _max_rel(sim.read_f(), orc.get_f(), _fluid_mask(orc))
+    err = _max_rel_elem(sim.read_f(), orc.get_f(), _fluid_mask(orc))
+    print(f"channel 16x16x32, 100 noise-free steps: element-wise max rel err {err:.3e}")
     assert err < RTOL_F, f"max rel err {err:.3e}"
 
 
@@ -169,7 +188,8 @@ def test_particle_parity(flbm, oracle_mod, name, p, X, V, Om, steps):
         _compare_particle(pg, po, vmax, k + 1)
         flips += po["nfluid"] != n0
         n0 = po["nfluid"]
-    err = _max_rel(sim.read_f(), orc.get_f(), _fluid_mask(orc))
+    err = _rel_err(sim.read_f(), orc.get_f(), _fluid_mask(orc), p)
+    print(f"{name}: max rel err {err:.3e}")
     assert err < RTOL_F, f"{name}: max rel err {err:.3e}"
     if X is not None:
         assert flips > 0, "expected cover/uncover events"
@@ -177,8 +197,17 @@ def test_particle_parity(flbm, oracle_mod, name, p, X, V, Om, steps):
 
 def test_trajectory_1000_fluctuating_steps(flbm, oracle_mod):
     """The 16x16x32 channel with thermal noise (kT = 1e-5) and the R=3 sphere
-    started with a velocity that makes it cross lattice nodes: the particle
-    velocity over 1000 steps stays within 1e-4 of the oracle's (identical Philox noise)."""
+    started at V_z = 0.01, so that it crosses lattice nodes: 1000 steps with
+    identical Philox noise on both sides.
+
+    The kick decays within a few tens of steps. After that the velocity is
+    thermal, sqrt(kT/m_p) = 2.4e-4, plus a settling drift of order 1e-5. The
+    velocity error of every step must stay within 1e-4 of the velocity
+    scale of the late part (steps 200 to 999): the largest |V| the oracle
+    reaches there. That scale is at least sqrt(kT/m_p), not the kick, so
+    the tolerance holds the fluctuating motion itself to 1e-4. The
+    position error after k steps must stay within the velocity tolerance
+    times k (the sum of the per-step velocity errors)."""
     p = W.channel_small(kT=1e-5)
     X0 = np.array(p["pos0"])
     sim, orc = _pair(flbm, oracle_mod, p, X=X0, V=(0.0, 0.0, 0.01))
@@ -192,10 +221,16 @@ def test_trajectory_1000_fluctuating_steps(flbm, oracle_mod):
         orc.step(1)
         po = orc.particle()
         Vo[k], Xo[k] = po["V"], po["X"]
-    scale = np.max(np.abs(Vo))
-    assert np.max(np.abs(Vg - Vo)) <= RTOL_TRAJ * scale
-    disp = np.max(np.abs(Xo - X0))
-    assert np.max(np.abs(Xg - Xo)) <= RTOL_TRAJ * disp
+    v_th = math.sqrt(p["kT"] / po["mp"])
+    scale = max(float(np.max(np.abs(Vo[200:]))), v_th)
+    dv = np.max(np.abs(Vg - Vo), axis=1)
+    dx = np.max(np.abs(Xg - Xo), axis=1)
+    steps = np.arange(1, 1001)
+    print(f"trajectory: velocity scale {scale:.3e} (thermal {v_th:.3e}); max velocity error "
+          f"{dv.max():.3e} = {dv.max() / scale:.2e} of scale (steps 200-999: {dv[200:].max() / scale:.2e}); "
+          f"max position error / (scale k) {np.max(dx / (scale * steps)):.2e}")
+    assert dv.max() <= RTOL_TRAJ * scale
+    assert np.all(dx <= RTOL_TRAJ * scale * steps)
     assert traj[-1]["step"] == 1000
 
 
@@ -268,3 +303,56 @@ def test_fluctuating_channel_with_each_wetting(flbm, oracle_mod, drho):
     _compare_particle(pg, po, max(0.04, float(np.max(np.abs(po["V"])))), 30)
     err = _max_rel(sim.read_f(), orc.get_f(), _fluid_mask(orc))
     assert err < RTOL_F, f"max rel err {err:.3e}"
+
+
+def test_benchmarked_channel_slab_with_moving_sphere(flbm, oracle_mod):
+    """The benchmarked configuration against the oracle: 128-wide rows, walls
+    on x and y, kT = 1e-5 and the R = 12 sphere, so the same bulk and
+    near-particle launches (tile shapes, candidate grid around the particle
+    box) as the 128x128x512 throughput run. It runs on a 128x128x32 slab,
+    which the oracle steps in seconds. The sphere is given V_z = 0.02 so that
+    nodes are covered and uncovered. After 12 steps with identical Philox
+    noise, the populations must agree within 1e-5 (mean-normalised, noisy
+    run) and the particle velocity within 1e-4 of its scale at every step,
+    with the fluid node count exact."""
+    p = W.channel_large(lz=32)
+    V = (0.0, 0.0, 0.02)
+    sim, orc = _pair(flbm, oracle_mod, p, X=p["pos0"], V=V)
+    n0 = orc.particle()["nfluid"]
+    flips = 0
+    vmax = 0.02
+    for k in range(12):
+        sim.step(1)
+        orc.step(1)
+        po, pg = orc.particle(), sim.particle()
+        vmax = max(vmax, float(np.max(np.abs(po["V"]))))
+        _compare_particle(pg, po, vmax, k + 1)
+        flips += po["nfluid"] != n0
+        n0 = po["nfluid"]
+    assert sim.launches() == _launches_per_step(p)
+    err = _max_rel(sim.read_f(), orc.get_f(), _fluid_mask(orc))
+    print(f"128x128x32 slab, R=12, kT=1e-5, 12 steps: max rel err {err:.3e}, {flips} steps with cover/uncover")
+    assert err < RTOL_F, f"max rel err {err:.3e}"
+    assert flips > 0, "expected cover/uncover events"
+
+
+def test_mode_temperatures_match_the_oracle(flbm, oracle_mod):
+    """The fluctuation temperatures of flbm_observables (modes 4..18 of each
+    component, interdiffusion current, total momentum; Section 2's
+    fluctuation-dissipation requirement) against the oracle's own reduction of
+    its state. The run has 40 noisy steps with a moving, wetted sphere. The
+    populations agree to about 1e-6, and the non-equilibrium modes are
+    differences of them about a tenth of their size, so the temperatures
+    must agree to 1e-3 relative. The bulk node count (fluid nodes with no
+    particle neighbour) must be exact."""
+    p = W.params(lx=14, ly=14, lz=14, wall=(0, 0, 0), G=1.2, kT=1e-4, radius=2.6, delta_rho=0.3)
+    sim, orc = _pair(flbm, oracle_mod, p, init_seed=9, X=(6.3, 6.8, 7.1), V=(0.03, -0.02, 0.05))
+    sim.step(40)
+    orc.step(40)
+    go = sim.observables()
+    oo = orc.mode_temps()
+    assert go["n_bulk"] == oo["n_bulk"] > 0
+    for key in ("mode_temp", "diff_temp", "mom_temp"):
+        err = float(np.max(np.abs(go[key] - oo[key]) / np.maximum(np.abs(oo[key]), 1e-300)))
+        print(f"{key}: max rel err {err:.2e}")
+        np.testing.assert_allclose(go[key], oo[key], rtol=1e-3, atol=0)

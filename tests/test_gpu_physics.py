@@ -95,3 +95,35 @@ def test_confinement_lowers_the_settling_velocity(flbm):
         sim.close()
     assert all(0.0 < c < 1.0 for c in cm), cm
     assert cm[0] > cm[1] > cm[2], cm
+
+
+def test_fluctuating_modes_are_at_equipartition_on_the_benchmark_channel(flbm):
+    """Fluctuation-dissipation (Section 2) on the GPU at the benchmarked size:
+    the 128x128x512 channel (walls on x and y) at kT = 1e-5 as an ideal
+    mixture (G = 0) without the sphere. There the populations are independent
+    Gaussians of variance 3 kT rho_l w_i, walls included, so every mode
+    temperature of flbm_observables (modes 4..18 of A and B), the
+    interdiffusion temperature and the momentum temperature equal kT. After
+    300 steps, the mean over 4 snapshots 5 steps apart must lie within
+    6 sigma, sigma = sqrt(2 / (4 n)) = 2.4e-4 for the n = 8.4 M nodes
+    (momentum: 8 sigma, its long waves decorrelate more slowly)."""
+    p = W.channel_large(radius=0.0, G=0.0)
+    kT = p["kT"]
+    sim = flbm.Sim(p)
+    sim.step(300)
+    acc = []
+    for _ in range(4):
+        sim.step(5)
+        acc.append(sim.observables())
+    n = acc[0]["n_bulk"]
+    assert n == 128 * 128 * 512
+    sigma = math.sqrt(2.0 / (4 * n))
+    mt = np.mean([a["mode_temp"] for a in acc], axis=0) / kT
+    dt = np.mean([a["diff_temp"] for a in acc], axis=0) / kT
+    jt = np.mean([a["mom_temp"] for a in acc], axis=0) / kT
+    print("mode temperatures / kT, A:", np.round(mt[0, 4:], 5), "B:", np.round(mt[1, 4:], 5))
+    print("interdiffusion / kT:", np.round(dt, 5), "momentum / kT:", np.round(jt, 5), f"sigma {sigma:.1e}")
+    assert np.all(mt[:, :4] == 0.0)
+    assert np.max(np.abs(mt[:, 4:] - 1.0)) < 6 * sigma
+    assert np.max(np.abs(dt - 1.0)) < 6 * sigma
+    assert np.max(np.abs(jt - 1.0)) < 8 * sigma

@@ -555,6 +555,62 @@ def test_poiseuille_with_halfway_walls_matches_the_two_rate_closed_form(oracle_m
 # Fluctuation-dissipation (Section 2): noise only on non-conserved modes with
 # variance 3 kT rho_l b_k; equipartition <j^2>/rho = kT per direction.
 # ---------------------------------------------------------------------------
+def test_mode_temperatures_of_a_thermalised_ideal_mixture_equal_kT(oracle_mod):
+    """Fluctuation-dissipation (Section 2): in a thermalised ideal mixture
+    (G = 0) the populations are independent Gaussians of variance
+    3 kT rho_l w_i, so every non-conserved mode of either component holds
+    <(m_k - m_k^eq)^2> = 3 kT rho_l b_k. The interdiffusion current holds
+    kT rho_A rho_B / rho_tot and the total momentum kT rho_tot per axis.
+    Halfway bounce-back only swaps populations of equal weight, so this holds
+    next to walls too. The channel here is 4 x 5 nodes in cross-section
+    between walls, so every node touches a wall. The oracle's temperature
+    reductions must give kT within their statistical error (400 snapshots of
+    800 nodes, sigma about 0.25 %; momentum relaxes slowly, so its
+    snapshots are correlated and its tolerance is wider). A wrong mode norm
+    or a missing factor fails this."""
+    kT = 1e-4
+    p = W.params(lx=4, ly=5, lz=40, wall=(1, 1, 0), G=0.0, kT=kT, init_pert=0.0)
+    o = oracle_mod.Oracle(p)
+    o.step(50)
+    acc = []
+    for _ in range(400):
+        o.step(2)
+        acc.append(o.mode_temps())
+    mt = np.mean([a["mode_temp"] for a in acc], axis=0) / kT
+    assert np.all(mt[:, :4] == 0.0)
+    assert np.max(np.abs(mt[:, 4:] - 1.0)) < 0.015, mt
+    dt = np.mean([a["diff_temp"] for a in acc], axis=0) / kT
+    assert np.max(np.abs(dt - 1.0)) < 0.02, dt
+    jt = np.mean([a["mom_temp"] for a in acc], axis=0) / kT
+    assert np.max(np.abs(jt - 1.0)) < 0.03, jt
+    assert acc[0]["n_bulk"] == 4 * 5 * 40
+
+
+def test_mode_temperatures_of_a_uniform_flow_are_zero(oracle_mod):
+    """A uniform equilibrium flow has no fluctuation: its modes equal the
+    equilibrium ones and the two components move together. So every mode
+    temperature and the interdiffusion temperature vanish, and the momentum
+    temperature is the flow's rho_tot U_a^2. A sphere at rest in the flow
+    removes its own nodes and their neighbours from the bulk count."""
+    U = np.array([0.04, -0.03, 0.05])
+    p = W.params(lx=12, ly=11, lz=13, wall=(0, 0, 0), G=0.0, init_pert=0.0, radius=2.6, pos0=(5.3, 5.1, 6.2))
+    o = oracle_mod.Oracle(p)
+    f = o.get_f()
+    rho = (p["rho_a0"], p["rho_b0"])
+    for l in range(2):
+        f[l] = _feq(rho[l], U)[:, None, None, None] * np.ones((1, 13, 11, 12))
+    o.set_f(f)
+    t = o.mode_temps()
+    assert np.max(np.abs(t["mode_temp"])) < 1e-28
+    assert np.max(np.abs(t["diff_temp"])) < 1e-28
+    assert np.allclose(t["mom_temp"], sum(rho) * U ** 2, rtol=1e-13, atol=0)
+    solid = o.fields()["solid"]
+    near = solid.copy()
+    for c in C[1:].astype(int):
+        near |= np.roll(solid, shift=(c[2], c[1], c[0]), axis=(0, 1, 2))
+    assert t["n_bulk"] == int((~near).sum())
+
+
 def test_single_node_mode_variances(oracle_mod):
     kT = 1e-4
     p = W.params(lx=1, ly=1, lz=1, wall=(0, 0, 0), G=0.0, kT=kT, init_pert=0.0, rho_a0=1.0, rho_b0=0.5)
