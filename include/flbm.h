@@ -261,6 +261,19 @@ int flbm_use_graphs(flbm_t* h, int enable);
  * lattice that does not allow it), FLBM_E_CUDA. */
 int flbm_use_tma(flbm_t* h, int enable);
 
+/* Limit, in SM clock cycles, of each wait of the TMA-staged collide for a
+ * tile's tensor copies (cycles = 0 restores the default of 2^31, about a
+ * second). A block whose wait runs out sets the handle's error flag, waits
+ * with the default limit for its copies still in flight, and returns, so the
+ * kernel ends without touching the rest of its tiles. The next
+ * flbm_particle_state or flbm_observables then returns FLBM_E_TIMEOUT, and
+ * the handle's state is no longer a step of the method: destroy it. This
+ * exists to exercise the error path of the bounded waits: a limit near 0
+ * makes them give up (the paper has no counterpart). Captured step graphs are
+ * dropped on a change (the stream is synchronised).
+ * Errors: FLBM_E_INVAL (cycles < 0), FLBM_E_CUDA. */
+int flbm_set_tma_wait(flbm_t* h, int64_t cycles);
+
 /* Observables of a population field, allocating nothing.
  *
  * For callers that cannot allocate device memory: code whose device memory is
@@ -281,8 +294,11 @@ int flbm_use_tma(flbm_t* h, int enable);
  * (2 MiB), held by every GPU that loads the library until the process exits.
  * A lattice that needs more tiles (more than 128x128x512 nodes or equivalent)
  * is rejected with FLBM_E_INVAL and a message on stderr. The first call on a
- * device looks up the array's device address with that device current; make
- * that first call before any stream capture. All calls share the array:
+ * device looks up the array's device address with that device current, and
+ * so does the first call from any other CUDA context (the address belongs to
+ * the context: a primary context re-created after cudaDeviceReset, or a
+ * context made current through the driver API, gets its own lookup); make
+ * those first calls before any stream capture. All calls share the array:
  * calls that overlap on the GPU (other streams, other host threads) race and
  * must be serialised by the caller. Every scratch slot a call reads is
  * written earlier in the same call, so no clearing is needed. */

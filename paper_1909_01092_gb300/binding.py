@@ -24,7 +24,7 @@ EXPORTS = (
     "flbm_read_fields", "flbm_write_fields", "flbm_set_particle", "flbm_run_host",
     "flbm_last_launch_count", "flbm_destroy", "flbm_error_string", "flbm_last_error",
     "flbm_step_timed", "flbm_kernel_name", "flbm_observables_noalloc",
-    "flbm_checkpoint", "flbm_restore", "flbm_use_graphs", "flbm_use_tma", "flbm_adjoint_run",
+    "flbm_checkpoint", "flbm_restore", "flbm_use_graphs", "flbm_use_tma", "flbm_set_tma_wait", "flbm_adjoint_run",
     "flbm_ensemble_create", "flbm_ensemble_step", "flbm_ensemble_tune", "flbm_ensemble_config",
     "flbm_ensemble_particles", "flbm_ensemble_read_fields", "flbm_ensemble_observables", "flbm_ensemble_nodes",
     "flbm_ensemble_last_launch_count", "flbm_ensemble_last_error", "flbm_ensemble_destroy",
@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True):
         lib.flbm_restore.argtypes = [vp, ctypes.c_char_p]
         lib.flbm_use_graphs.argtypes = [vp, ctypes.c_int]
         lib.flbm_use_tma.argtypes = [vp, ctypes.c_int]
+        lib.flbm_set_tma_wait.argtypes = [vp, ctypes.c_int64]
         lib.flbm_adjoint_run.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(AdjResult)]
         ens_p = ctypes.POINTER(EnsConfig)
         lib.flbm_ensemble_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, ens_p, vp,
@@ -256,6 +257,11 @@ class Sim:
         """Select the bulk collide kernel with TMA-staged inputs (where the
         lattice allows it) or the one reading global memory directly (default)."""
         self._check(self.lib.flbm_use_tma(self.h, int(bool(enable))), "flbm_use_tma")
+
+    def set_tma_wait(self, cycles: int) -> None:
+        """Limit of the TMA-staged collide's waits for its tensor copies, in SM
+        cycles (0: the default); a limit near 0 exercises the timeout path."""
+        self._check(self.lib.flbm_set_tma_wait(self.h, int(cycles)), "flbm_set_tma_wait")
 
     def checkpoint(self, path) -> None:
         self._check(self.lib.flbm_checkpoint(self.h, os.fsencode(path)), "flbm_checkpoint")

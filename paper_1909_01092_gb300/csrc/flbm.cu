@@ -91,6 +91,7 @@ void setup_tma(flbm_sim* h)
 {
     const KParams& k = h->kp;
     h->tma_ok = h->tma = false;
+    h->tma_wait = kTmaWaitCycles;
     if (k.lx % 4 != 0 || k.tx != kTmaTX || k.ty != kTmaTY || k.px % 4 != 0) return;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return;
@@ -117,7 +118,7 @@ void setup_tma(flbm_sim* h)
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return;
-    void (*kern[4])(const CUtensorMap, const CUtensorMap, float*, DevState*, KParams) = {
+    void (*kern[4])(const CUtensorMap, const CUtensorMap, float*, DevState*, KParams, long long) = {
         k_collide_bulk_tma<false, false>, k_collide_bulk_tma<false, true>, k_collide_bulk_tma<true, false>,
         k_collide_bulk_tma<true, true>};
     for (auto* f : kern)
@@ -173,7 +174,7 @@ int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
         }                                                                                                     \
         if (h->tma) {                                                                                         \
             k_collide_bulk_tma<NZ, T1><<<h->tma_grid, h->block, kTmaSmemBytes, h->stream>>>(                   \
-                h->tm_f[h->cur], h->tm_psi, fout, h->st, k);                                                  \
+                h->tm_f[h->cur], h->tm_psi, fout, h->st, k, h->tma_wait);                                     \
             if (int rc = launch_check(h, "k_collide_bulk_tma")) return rc;                                    \
         } else {                                                                                              \
             k_collide_bulk<NZ, T1><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, k);         \
@@ -387,6 +388,23 @@ int flbm_use_tma(flbm_t* h, int enable)
     return FLBM_OK;
 }
 
+int flbm_set_tma_wait(flbm_t* h, int64_t cycles)
+{
+    if (!h || cycles < 0) return fail(h, FLBM_E_INVAL, "invalid argument");
+    if (cycles == 0) cycles = kTmaWaitCycles;
+    if (h->tma_wait != cycles) {
+        // Captured graphs hold the old limit.
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (int c = 0; c < 2; ++c)
+            if (h->graph[c]) {
+                cudaGraphExecDestroy(h->graph[c]);
+                h->graph[c] = nullptr;
+            }
+    }
+    h->tma_wait = cycles;
+    return FLBM_OK;
+}
+
 int flbm_use_graphs(flbm_t* h, int enable)
 {
     if (!h || (enable != 0 && enable != 1)) return fail(h, FLBM_E_INVAL, "invalid argument");
@@ -447,6 +465,8 @@ int flbm_restore(flbm_t* h, const char* path)
          std::fread(f.data(), 1, want.f_bytes, fp) == want.f_bytes;
     std::fclose(fp);
     if (!ok) return fail(h, FLBM_E_INVAL, std::string(path) + ": truncated checkpoint");
+    const std::string bad = check_restored_state(st, h->kp);
+    if (!bad.empty()) return fail(h, FLBM_E_INVAL, std::string(path) + ": " + bad);
     // Values derived from the parameters follow this handle's parameters.
     if (h->kp.has_particle) {
         const DevState s0 = initial_state(h->p, h->kp);
@@ -456,7 +476,10 @@ int flbm_restore(flbm_t* h, const char* path)
         st.fc = (h->p.fluid_counterforce && st.nfluid > 0) ? -st.Fp / (double)st.nfluid : 0.0;
         st.fc_f = (float)st.fc;
     }
+    // Counters of the step's launches start from zero on this handle.
     st.err = 0;
+    st.near_done = 0;
+    st.cover_done = 0;
     CK(h, cudaMemcpyAsync(h->st, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->masks, masks.data(), want.mask_bytes, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->fbuf[h->cur], f.data(), want.f_bytes, cudaMemcpyHostToDevice, h->stream));
@@ -698,15 +721,45 @@ static __device__ __align__(256) double g_noalloc_tiles[FLBM_NOALLOC_MAX_TILES *
 
 namespace {
 
-// Device address of g_noalloc_tiles, looked up once per device on the first
-// call made with that device current (host code may not use the symbol
-// itself: in host code its name is only a stand-in, not a device address).
+// Device address of g_noalloc_tiles, looked up on the first call made with a
+// device current (host code may not use the symbol itself: in host code its
+// name is only a stand-in, not a device address). The address belongs to the
+// CUDA context the lookup ran in, so each slot remembers that context's
+// unique ID and the lookup runs again when a call comes from another context
+// (a primary context re-created after cudaDeviceReset, or a context the
+// caller made current through the driver API).
 struct NoallocSlot {
     double* ptr = nullptr;
+    unsigned long long ctx_id = 0;
     bool ready = false;
 };
 NoallocSlot g_noalloc_slots[64];
 std::mutex g_noalloc_mutex;
+
+// Unique ID of the calling thread's current CUDA context (0 if there is none
+// or the driver cannot tell), from the driver's cuCtxGetCurrent and
+// cuCtxGetId reached through the runtime (no link to libcuda).
+unsigned long long current_context_id()
+{
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
 
 }  // namespace
 
@@ -737,11 +790,14 @@ extern "C" int flbm_observables_noalloc(const flbm_params* p, const float* f_dev
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
         NoallocSlot& s = g_noalloc_slots[dev];
-        if (!s.ready) {
+        const unsigned long long id = current_context_id();
+        if (!s.ready || id == 0 || id != s.ctx_id) {
             void* ptr = nullptr;
             if (cudaGetSymbolAddress(&ptr, g_noalloc_tiles) != cudaSuccess) return FLBM_E_CUDA;
             s.ptr = (double*)ptr;
-            s.ready = true;
+            // The lookup made the runtime's context current if none was.
+            s.ctx_id = current_context_id();
+            s.ready = s.ctx_id != 0;
         }
         scratch = s.ptr;
     }

@@ -175,6 +175,34 @@ inline void fill_mode_obs(const double vm[kObsModes], flbm_obs* out)
     out->n_bulk = (int64_t)vm[39];
 }
 
+// Checks of a particle record read from a checkpoint file before it goes to
+// the device; returns an empty string if it is usable. The step kernels index
+// the particle masks with cur and the box origin, so a corrupt or foreign
+// record must not reach them.
+inline std::string check_restored_state(const DevState& s, const KParams& k)
+{
+    if (s.cur != 0 && s.cur != 1) return "mask index out of range";
+    if (s.nfluid < 0 || s.nfluid > k.N) return "fluid node count out of range";
+    if (s.step < 0) return "negative step count";
+    if (!std::isfinite(s.delta[0]) || !std::isfinite(s.delta[1])) return "non-finite mass correction";
+    if (!k.has_particle) return "";
+    for (int a = 0; a < 3; ++a) {
+        const double v[6] = {s.X[a], s.V[a], s.Vavg[a], s.Om[a], s.Ppend[a], s.Lpend[a]};
+        for (double x : v)
+            if (!std::isfinite(x)) return "non-finite particle state";
+    }
+    const int L[3] = {k.lx, k.ly, k.lz};
+    for (int a = 0; a < 3; ++a) {
+        if (k.wall[a] && (s.X[a] - k.R < -0.5 || s.X[a] + k.R > L[a] - 0.5)) return "sphere outside the walls";
+        if (!k.wall[a] && (s.X[a] < 0.0 || s.X[a] >= L[a])) return "centre outside the periodic box";
+    }
+    int o[3];
+    box_origin(s.X, k, o);
+    for (int a = 0; a < 3; ++a)
+        if (o[a] != s.box0[a]) return "box origin does not match the centre";
+    return "";
+}
+
 inline int copy_particle(const DevState& s, flbm_particle* out)
 {
     for (int a = 0; a < 3; ++a) {

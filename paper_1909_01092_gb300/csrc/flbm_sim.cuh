@@ -50,6 +50,7 @@ struct flbm_sim {
     bool tma_ok = false;
     bool tma = false;
     int tma_grid = 0;
+    long long tma_wait = 0;  // limit of its waits for a tile's inputs, SM cycles (set at creation)
     // The near-particle collide runs on a second, higher-priority stream,
     // concurrently with the bulk collide (they write disjoint populations);
     // fork and join by events.

@@ -12,9 +12,11 @@
 // next tile are in flight, so the HBM reads no longer wait on the warps. The
 // stores of the streamed populations go straight to global memory as before.
 //
-// Every wait on a stage's mbarrier is bounded (about a second of SM clock).
-// A block that gives up sets DevState::err, waits (bounded again) for its
-// other copies and returns; the host reports FLBM_E_TIMEOUT.
+// Every wait on a stage's mbarrier is bounded: the waits for a tile's inputs
+// by the launch's wait_cycles (default about a second of SM clock, set with
+// flbm_set_tma_wait), the final waits for a leaving block's own copies by
+// that default. A block that gives up sets DevState::err, waits for its
+// copies still in flight and returns; the host reports FLBM_E_TIMEOUT.
 #pragma once
 
 #include <cuda.h>
@@ -57,12 +59,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Waits for phase `parity` of the mbarrier for at most kTmaWaitCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+// Waits for phase `parity` of the mbarrier for at most `limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit = kTmaWaitCycles)
 {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kTmaWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -104,7 +106,7 @@ __device__ __forceinline__ void tile_coords(long long t, const KParams& P, int& 
 template <bool NOISE, bool TAU1>
 static __global__ void __launch_bounds__(kThreadsStep, 2)
     k_collide_bulk_tma(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_psi,
-                       float* __restrict__ fout, DevState* __restrict__ st, KParams P)
+                       float* __restrict__ fout, DevState* __restrict__ st, KParams P, long long wait_cycles)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -161,7 +163,7 @@ static __global__ void __launch_bounds__(kThreadsStep, 2)
 
     for (int k = 0; t < ntiles; ++k) {
         const int s = k & 1;
-        const bool ready = mbar_wait_bounded(bar + 8 * s, (uint32_t)(k >> 1) & 1u);
+        const bool ready = mbar_wait_bounded(bar + 8 * s, (uint32_t)(k >> 1) & 1u, wait_cycles);
         if (__syncthreads_or(!ready)) {  // the whole block leaves together
             if (leader) atomicExch(&st->err, 1);
             // Let the copies this block issued land before its shared memory is released.

@@ -116,3 +116,31 @@ def test_legacy_default_stream_equals_another_stream(flbm):
     b.step(9)
     torch.cuda.synchronize()
     _same_state(a, b, p)
+
+
+def test_restore_refuses_a_corrupt_particle_record(flbm, tmp_path):
+    """A checkpoint whose particle record is corrupt (a non-finite centre, a
+    mask index other than 0 or 1) is refused with FLBM_E_INVAL before any of
+    it reaches the device; the handle still restores a good file afterwards
+    and continues bit for bit."""
+    import ctypes
+    import struct
+
+    p = W.channel_small(kT=1e-5, g=1e-4)
+    a = flbm.Sim(p)
+    a.step(5)
+    path = tmp_path / "good.ckpt"
+    a.checkpoint(path)
+    raw = bytearray(path.read_bytes())
+    head = 80  # the file's fixed header
+    state = head + ctypes.sizeof(flbm.Params)  # the particle record starts with X[3]
+    bad = bytearray(raw)
+    bad[state:state + 8] = struct.pack("<d", float("nan"))
+    (tmp_path / "nan.ckpt").write_bytes(bytes(bad))
+    b = flbm.Sim(p)
+    with pytest.raises(flbm.FLBMError, match="FLBM_E_INVAL"):
+        b.restore(tmp_path / "nan.ckpt")
+    b.restore(path)
+    a.step(4)
+    b.step(4)
+    _same_state(a, b, p)

@@ -101,3 +101,31 @@ def test_tma_refused_where_rows_do_not_allow_it(flbm):
         s.use_tma(False)
         s.step(2)
         assert s.observables()["nonfinite"] == 0
+
+
+def test_a_wait_that_runs_out_reports_a_timeout_and_the_context_stays_usable(flbm):
+    """Failure detection of the bounded waits, without a fault. The TMA-staged
+    collide's waits for its tensor copies are given a limit of one SM cycle,
+    so they give up before the copies land. Each block that gives up flags
+    the error, waits (with the default limit) for its own copies still in
+    flight, and returns. The host must then report FLBM_E_TIMEOUT from
+    flbm_particle_state and flbm_observables. The lattice has no particle,
+    so no kernel of the step indexes memory by values the skipped tiles
+    left behind. Afterwards the context is still usable: a new handle with
+    the default limit steps bit for bit as the direct kernel does."""
+    p = W.params(lx=32, ly=32, lz=32, radius=0.0, kT=1e-5)
+    broken = flbm.Sim(p)
+    broken.use_tma(True)
+    broken.set_tma_wait(1)
+    broken.step(2)
+    with pytest.raises(flbm.FLBMError, match="FLBM_E_TIMEOUT"):
+        broken.particle()
+    with pytest.raises(flbm.FLBMError, match="FLBM_E_TIMEOUT"):
+        broken.observables(allow_nonfinite=True)
+    broken.close()
+    a, b = flbm.Sim(p), flbm.Sim(p)
+    a.use_tma(True)
+    a.step(6)
+    b.step(6)
+    a.particle()  # no error flagged
+    assert np.array_equal(a.read_f(), b.read_f())

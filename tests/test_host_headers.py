@@ -18,7 +18,11 @@ brute-force scan of the lattice:
   counters, and the exact uniform map;
 * tests/host_modes.cu (to_modes, from_modes, bnorm): the collision's
   hand-factored transforms against the D3Q19 mode basis written out from its
-  polynomials, exactly, and their round trip.
+  polynomials, exactly, and their round trip;
+* tests/host_restore.cu (check_restored_state): a particle record read from
+  a checkpoint passes when it is one the library wrote, and is refused when
+  its mask index, centre, velocities, box origin, fluid count, step or mass
+  correction is corrupt, before any of it reaches the device.
 """
 import os
 import subprocess
@@ -59,3 +63,10 @@ def test_cuda_philox_matches_the_published_known_answers(tmp_path):
 def test_collision_mode_transforms_match_the_basis_polynomials(tmp_path):
     out = _build_and_run(tmp_path, "host_modes", "")
     assert "failed 0" in out, out
+
+
+def test_restored_particle_records_are_checked(tmp_path):
+    out = _build_and_run(tmp_path, "host_restore", "")
+    words = out.split()
+    configs, refused, failed = (int(words[words.index(w) + 1]) for w in ("configurations", "refused", "failed"))
+    assert failed == 0 and configs > 300 and refused > 6 * configs, out
