@@ -195,9 +195,12 @@ int flbm_set_particle(flbm_t* h, const double X[3], const double V[3], const dou
  * FLBM_E_CUDA. */
 int flbm_run_host(flbm_t* h, const float* host_f_in, int64_t nsteps, float* host_f_out, flbm_particle* traj);
 
-/* Kernel classes of one step, in launch order. */
+/* Kernel classes of one step. Two-pass steps launch them in this order;
+ * fused steps (flbm_set_density_mode) launch the collide first, then the
+ * particle kernels, the completion of the densities and the shell. */
 enum {
-    FLBM_K_DENSITY = 0,  /* densities of fluid nodes (Eq. (density)) */
+    FLBM_K_DENSITY = 0,  /* densities of fluid nodes (Eq. (density)): the density pass (two-pass), or
+                            the completion of the densities the collide summed (fused) */
     FLBM_K_SHELL = 1,    /* periodic copies and neutral wall ghosts of the density field, and the
                             virtual wetting layer on particle surface nodes (one launch) */
     FLBM_K_COLLIDE = 2,  /* force, MRT collision, noise, streaming, bounce-back, exchange; with a
@@ -260,6 +263,31 @@ int flbm_use_graphs(flbm_t* h, int enable);
  * FLBM_E_TIMEOUT. Errors: FLBM_E_INVAL, FLBM_E_UNSUPPORTED (enable = 1 on a
  * lattice that does not allow it), FLBM_E_CUDA. */
 int flbm_use_tma(flbm_t* h, int enable);
+
+/* How each step forms the densities of Eq. (density) that the Shan-Chen force
+ * of Eq. (sc-force) reads at the next step.
+ *   mode 0 (two-pass): a density pass re-reads every population at the start
+ *     of each step (152 B per node of extra HBM traffic);
+ *   mode 1 (fused, the default where the lattice allows it): the collide-stream
+ *     sums the populations it pushes into each node as it writes them, and a
+ *     small completion kernel adds the partial sums across tile and chunk
+ *     boundaries and recomputes the densities next to the particle after
+ *     cover/uncover. The densities are then carried from step to step (and
+ *     saved by flbm_checkpoint).
+ * The two modes compute the same sums in different orders: they agree to
+ * float32 rounding, and each is bit-reproducible. planes_per_block (fused
+ * only) is how many consecutive z-planes one block of the fused collide walks;
+ * 0 chooses about two waves of blocks for this GPU. The TMA-staged collide
+ * (flbm_use_tma) always runs two-pass. Captured step graphs are dropped.
+ * Errors: FLBM_E_INVAL (mode not 0 or 1, planes_per_block < 0 or > lz),
+ * FLBM_E_UNSUPPORTED (mode 1 on a lattice whose tiles are narrower than 8
+ * nodes, or with fewer than 3 tiles along a periodic x or y), FLBM_E_NOMEM,
+ * FLBM_E_CUDA. */
+int flbm_set_density_mode(flbm_t* h, int32_t mode, int32_t planes_per_block);
+
+/* The density mode the next step takes (host memory, caller-owned outputs):
+ * mode 1 with its planes per block, or mode 0 with 0. Errors: FLBM_E_INVAL. */
+int flbm_get_density_mode(const flbm_t* h, int32_t* mode, int32_t* planes_per_block);
 
 /* Limit, in SM clock cycles, of each wait of the TMA-staged collide for a
  * tile's tensor copies (cycles = 0 restores the default of 2^31, about a

@@ -25,6 +25,7 @@ EXPORTS = (
     "flbm_last_launch_count", "flbm_destroy", "flbm_error_string", "flbm_last_error",
     "flbm_step_timed", "flbm_kernel_name", "flbm_observables_noalloc",
     "flbm_checkpoint", "flbm_restore", "flbm_use_graphs", "flbm_use_tma", "flbm_set_tma_wait", "flbm_adjoint_run",
+    "flbm_set_density_mode", "flbm_get_density_mode",
     "flbm_ensemble_create", "flbm_ensemble_step", "flbm_ensemble_tune", "flbm_ensemble_config",
     "flbm_ensemble_particles", "flbm_ensemble_read_fields", "flbm_ensemble_observables", "flbm_ensemble_nodes",
     "flbm_ensemble_last_launch_count", "flbm_ensemble_last_error", "flbm_ensemble_destroy",
@@ -111,6 +112,8 @@ def load(build_if_missing: bool = True):
         lib.flbm_use_graphs.argtypes = [vp, ctypes.c_int]
         lib.flbm_use_tma.argtypes = [vp, ctypes.c_int]
         lib.flbm_set_tma_wait.argtypes = [vp, ctypes.c_int64]
+        lib.flbm_set_density_mode.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+        lib.flbm_get_density_mode.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         lib.flbm_adjoint_run.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(AdjResult)]
         ens_p = ctypes.POINTER(EnsConfig)
         lib.flbm_ensemble_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, ens_p, vp,
@@ -262,6 +265,18 @@ class Sim:
         """Limit of the TMA-staged collide's waits for its tensor copies, in SM
         cycles (0: the default); a limit near 0 exercises the timeout path."""
         self._check(self.lib.flbm_set_tma_wait(self.h, int(cycles)), "flbm_set_tma_wait")
+
+    def set_density_mode(self, mode: int, planes_per_block: int = 0) -> None:
+        """0: density pass every step; 1: densities summed by the collide
+        (fused), planes_per_block z-planes per block (0: automatic)."""
+        self._check(self.lib.flbm_set_density_mode(self.h, int(mode), int(planes_per_block)),
+                    "flbm_set_density_mode")
+
+    def density_mode(self) -> tuple:
+        """(mode, planes per block) the next step takes."""
+        m, k = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.flbm_get_density_mode(self.h, ctypes.byref(m), ctypes.byref(k)), "flbm_get_density_mode")
+        return m.value, k.value
 
     def checkpoint(self, path) -> None:
         self._check(self.lib.flbm_checkpoint(self.h, os.fsencode(path)), "flbm_checkpoint")

@@ -105,11 +105,11 @@ void setup_tma(flbm_sim* h)
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return;
     }
-    {
+    for (int c = 0; c < 2; ++c) {
         const cuuint64_t dims[4] = {(cuuint64_t)k.px, (cuuint64_t)k.py, (cuuint64_t)k.pz, 2};
         const cuuint64_t strides[3] = {(cuuint64_t)k.px * 4, (cuuint64_t)k.px * k.py * 4, (cuuint64_t)k.padn * 4};
         const cuuint32_t box[4] = {kTmaPX, kTmaPY, 3, 2};
-        if (enc(&h->tm_psi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->psi, dims, strides, box, one,
+        if (enc(&h->tm_psi[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->psibuf[c], dims, strides, box, one,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return;
@@ -132,52 +132,75 @@ void setup_tma(flbm_sim* h)
     h->tma_ok = true;  // available; flbm_use_tma switches it on
 }
 
-// Densities, then the psi shell and the virtual layer (one launch), for the
-// current state. With ev, events ev[0..2] bracket the two kernels.
-int launch_psi(flbm_sim* h, const float* f, cudaEvent_t* ev = nullptr)
+// Densities, then the psi shell and the virtual layer (one launch), of the
+// current state into psibuf[cur]. With ev, events ev[0..2] bracket the two
+// kernels.
+int launch_psi(flbm_sim* h, cudaEvent_t* ev = nullptr)
 {
     const KParams& k = h->kp;
+    float* psi = psi_cur(h);
     record(h, ev, 0);
-    k_density<<<h->grid, h->block, 0, h->stream>>>(f, h->psi, h->st, h->masks, k);
+    k_density<<<h->grid, h->block, 0, h->stream>>>(h->fbuf[h->cur], psi, h->st, h->masks, k);
     if (int rc = launch_check(h, "k_density")) return rc;
     record(h, ev, 1);
     const int nbs = (int)((shell_count(k) + kThreads - 1) / kThreads);
     const int nbv = k.has_particle ? (k.B * k.B * k.B + kThreads - 1) / kThreads : 0;
-    k_shell_virtual<<<nbs + nbv, kThreads, 0, h->stream>>>(h->psi, h->st, h->masks, k, nbs);
+    k_shell_virtual<<<nbs + nbv, kThreads, 0, h->stream>>>(psi, h->st, h->masks, k, nbs);
     if (int rc = launch_check(h, "k_shell_virtual")) return rc;
     record(h, ev, 2);
+    h->psi_valid = true;
     return FLBM_OK;
 }
 
-// One time step. With ev, events ev[0..4] bracket its four kernel classes.
-int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
+// Does the next step take the fused path (densities as a by-product)?
+bool use_fused(const flbm_sim* h) { return h->density_mode == 1 && h->fused_allowed && !h->tma; }
+
+// The current state's densities, if the next step needs them and they are stale.
+int ensure_psi(flbm_sim* h)
+{
+    return h->psi_valid ? FLBM_OK : launch_psi(h);
+}
+
+// Kernel classes in the order each step launches them; step_timed assigns
+// the time between consecutive events to these classes.
+constexpr int kTwoPassOrder[FLBM_NKERNELS] = {FLBM_K_DENSITY, FLBM_K_SHELL, FLBM_K_COLLIDE, FLBM_K_PARTICLE};
+constexpr int kFusedOrder[FLBM_NKERNELS] = {FLBM_K_COLLIDE, FLBM_K_PARTICLE, FLBM_K_DENSITY, FLBM_K_SHELL};
+
+// Collide-stream of the current state: the near-particle tiles on the side
+// stream (higher priority, so its few blocks start first), the bulk tiles on
+// the handle's stream, joined before the particle kernels (the near launch
+// and its particle update overlap the bulk launch). Fused: the bulk launch
+// also writes the next state's densities (psibuf[1 - cur], ring, seams).
+int launch_collide(flbm_sim* h, bool fused)
 {
     const KParams& k = h->kp;
     const float* fin = h->fbuf[h->cur];
     float* fout = h->fbuf[1 - h->cur];
-    if (int rc = launch_psi(h, fin, ev)) return rc;
+    const float* psi = psi_cur(h);
     const bool noise = k.kT > 0.0f;
     const bool part = k.has_particle != 0;
     const dim3 gnear(k.ncx, k.ncy, k.ncz);
-    // Near tiles on the side stream (higher priority, so its few blocks start
-    // first), bulk tiles on the handle's stream, joined before the particle
-    // kernels: the near launch and its particle update overlap the bulk launch.
+    const dim3 gfused(k.gx, k.gy, h->fg.nchunk);
 #define FLBM_COLLIDE(NZ, T1)                                                                                  \
     do {                                                                                                      \
         if (part) {                                                                                           \
             CK(h, cudaEventRecord(h->fork_ev, h->stream));                                                    \
             CK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));                                               \
-            k_collide_near<NZ, T1><<<gnear, h->block, 0, h->side>>>(fin, fout, h->psi, h->st, h->masks,       \
+            k_collide_near<NZ, T1><<<gnear, h->block, 0, h->side>>>(fin, fout, psi, h->st, h->masks,          \
                                                                     h->partials, k);                          \
             if (int rc = launch_check(h, "k_collide_near")) return rc;                                        \
             CK(h, cudaEventRecord(h->join_ev, h->side));                                                      \
         }                                                                                                     \
-        if (h->tma) {                                                                                         \
+        if (fused) {                                                                                          \
+            k_collide_bulk_fused<NZ, T1><<<gfused, h->block, 0, h->stream>>>(                                  \
+                fin, fout, psi, h->psibuf[1 - h->cur], h->ring, h->seam, h->st, k, h->fg);                    \
+            if (int rc = launch_check(h, "k_collide_bulk_fused")) return rc;                                  \
+        } else if (h->tma) {                                                                                  \
             k_collide_bulk_tma<NZ, T1><<<h->tma_grid, h->block, kTmaSmemBytes, h->stream>>>(                   \
-                h->tm_f[h->cur], h->tm_psi, fout, h->st, k, h->tma_wait);                                     \
+                h->tm_f[h->cur], h->tm_psi[h->cur], fout, h->st, k, h->tma_wait);                             \
             if (int rc = launch_check(h, "k_collide_bulk_tma")) return rc;                                    \
         } else {                                                                                              \
-            k_collide_bulk<NZ, T1><<<h->grid, h->block, 0, h->stream>>>(fin, fout, h->psi, h->st, k);         \
+            k_collide_bulk<NZ, T1><<<h->grid, h->block, 0, h->stream>>>(fin, fout, psi, h->st, k);            \
             if (int rc = launch_check(h, "k_collide_bulk")) return rc;                                        \
         }                                                                                                     \
         if (part) CK(h, cudaStreamWaitEvent(h->stream, h->join_ev, 0));                                      \
@@ -187,19 +210,113 @@ int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
     else if (k.tau1) FLBM_COLLIDE(false, true);
     else FLBM_COLLIDE(false, false);
 #undef FLBM_COLLIDE
-    record(h, ev, 3);
-    if (part) {
-        // The particle update ran in the near kernel's last block.
+    return FLBM_OK;
+}
+
+// Particle kernels after the collide (the particle update ran in the near
+// kernel's last block): next-position masks, cover/uncover and the step's
+// bookkeeping; without a particle only the bookkeeping.
+int launch_particle(flbm_sim* h)
+{
+    const KParams& k = h->kp;
+    if (k.has_particle) {
         k_mark_next<<<h->box_blocks, 256, 0, h->stream>>>(h->st, h->masks, h->box_counts, k);
         if (int rc = launch_check(h, "k_mark_next")) return rc;
-        k_cover<<<h->box_blocks, 256, 0, h->stream>>>(fout, h->st, h->masks, h->box_parts, h->box_counts, k);
+        k_cover<<<h->box_blocks, 256, 0, h->stream>>>(h->fbuf[1 - h->cur], h->st, h->masks, h->box_parts,
+                                                       h->box_counts, k);
         if (int rc = launch_check(h, "k_cover")) return rc;
     } else {
         k_finish<<<1, 256, 0, h->stream>>>(h->st, h->box_counts, h->box_parts, h->box_blocks, k);
         if (int rc = launch_check(h, "k_finish")) return rc;
     }
+    return FLBM_OK;
+}
+
+// One time step. With ev, events ev[0..4] bracket its four kernel classes
+// (in the order kTwoPassOrder or kFusedOrder).
+int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
+{
+    const KParams& k = h->kp;
+    if (!use_fused(h)) {
+        if (int rc = launch_psi(h, ev)) return rc;
+        if (int rc = launch_collide(h, false)) return rc;
+        record(h, ev, 3);
+        if (int rc = launch_particle(h)) return rc;
+        record(h, ev, 4);
+        h->cur = 1 - h->cur;
+        h->psi_valid = false;  // psibuf[cur] belongs to an older state
+        return FLBM_OK;
+    }
+    if (int rc = ensure_psi(h)) return rc;
+    record(h, ev, 0);
+    if (int rc = launch_collide(h, true)) return rc;
+    record(h, ev, 1);
+    if (int rc = launch_particle(h)) return rc;
+    record(h, ev, 2);
+    float* psi_next = h->psibuf[1 - h->cur];
+    const int nB = k.gx * k.gy * h->fg.nchunk;
+    const int nA = (int)((near_box_nodes(k) + kThreadsStep - 1) / kThreadsStep);
+    k_psi_finish<<<nB + nA, kThreadsStep, 0, h->stream>>>(h->fbuf[1 - h->cur], psi_next, h->ring, h->seam, h->st,
+                                                          h->masks, k, h->fg, nB);
+    if (int rc = launch_check(h, "k_psi_finish")) return rc;
+    record(h, ev, 3);
+    const int nbs = (int)((shell_count(k) + kThreads - 1) / kThreads);
+    const int nbv = k.has_particle ? (k.B * k.B * k.B + kThreads - 1) / kThreads : 0;
+    k_shell_virtual<<<nbs + nbv, kThreads, 0, h->stream>>>(psi_next, h->st, h->masks, k, nbs);
+    if (int rc = launch_check(h, "k_shell_virtual")) return rc;
     record(h, ev, 4);
     h->cur = 1 - h->cur;
+    h->psi_valid = true;
+    return FLBM_OK;
+}
+
+// Planes per block of the fused collide by default: enough chunks for about
+// two waves of resident blocks (4 per SM) over the lattice's tiles.
+int auto_chunk(const KParams& k)
+{
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 148;
+    const long long tiles = (long long)k.gx * k.gy;
+    const long long target = 2LL * sms * FLBM_BULK_MINBLOCKS;
+    const long long nch = std::max(1LL, std::min<long long>(k.lz, target / tiles));
+    return (int)((k.lz + nch - 1) / nch);
+}
+
+// Fused geometry for K planes per block; the seam buffer grows if needed.
+int set_fused_geometry(flbm_sim* h, int K)
+{
+    const KParams& k = h->kp;
+    K = std::max(K, (k.lz + 65534) / 65535);  // grid z limit
+    FusedGeom g;
+    g.K = K;
+    g.nchunk = (k.lz + K - 1) / K;
+    g.ring = 2 * (k.tx + 2) + 2 * k.ty;
+    g.fp = (k.tx + 2) * (k.ty + 2);
+    const size_t need = (size_t)k.gx * k.gy * g.nchunk * 2 * g.fp;
+    if (need > h->seam_cap) {
+        if (h->seam) cudaFree(h->seam);
+        h->seam = nullptr;
+        h->seam_cap = 0;
+        if (cudaMalloc(&h->seam, sizeof(float2) * need) != cudaSuccess) return fail(h, FLBM_E_NOMEM, "seam buffer");
+        h->seam_cap = need;
+    }
+    h->fg = g;
+    return FLBM_OK;
+}
+
+// Captured graphs replay the kernels and parameters of their capture; drop them.
+int drop_graphs(flbm_sim* h)
+{
+    bool any = false;
+    for (int c = 0; c < 2; ++c) any = any || h->graph[c];
+    if (!any) return FLBM_OK;
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < 2; ++c)
+        if (h->graph[c]) {
+            cudaGraphExecDestroy(h->graph[c]);
+            h->graph[c] = nullptr;
+        }
     return FLBM_OK;
 }
 
@@ -235,7 +352,9 @@ int ensure_graph(flbm_sim* h, int c)
 }
 
 // Fixed-size head of a checkpoint file, followed by flbm_params, DevState,
-// the two particle masks and the current populations.
+// the two particle masks, the current populations and (version 2) the padded
+// density field of the current state, which the fused step carries from one
+// step to the next.
 struct CkptHeader {
     char magic[8];
     uint32_t version;
@@ -248,7 +367,7 @@ void fill_header(const flbm_sim* h, CkptHeader* hd)
 {
     std::memset(hd, 0, sizeof(*hd));
     std::memcpy(hd->magic, "FLBMCKP", 8);
-    hd->version = 1;
+    hd->version = 2;
     hd->lx = h->p.lx; hd->ly = h->p.ly; hd->lz = h->p.lz;
     hd->wall[0] = h->p.wall_x; hd->wall[1] = h->p.wall_y; hd->wall[2] = h->p.wall_z;
     hd->B = h->kp.B;
@@ -264,6 +383,7 @@ void fill_header(const flbm_sim* h, CkptHeader* hd)
 namespace flbm {
 int sim_step(flbm_sim* h, cudaEvent_t* ev) { return launch_step(h, ev); }
 int sim_fail(flbm_sim* h, int code, const std::string& msg) { return fail(h, code, msg); }
+int sim_ensure_psi(flbm_sim* h) { return ensure_psi(h); }
 }  // namespace flbm
 
 extern "C" {
@@ -306,7 +426,8 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
     }
     h->fbuf[1] = h->fbuf[0] + (size_t)2 * 19 * k.N;
     const size_t B3 = (size_t)k.B * k.B * k.B;
-    if (cudaMalloc(&h->psi, sizeof(float) * 2 * k.padn) != cudaSuccess ||
+    if (cudaMalloc(&h->psibuf[0], sizeof(float) * 2 * k.padn) != cudaSuccess ||
+        cudaMalloc(&h->psibuf[1], sizeof(float) * 2 * k.padn) != cudaSuccess ||
         cudaMalloc(&h->st, sizeof(DevState)) != cudaSuccess ||
         cudaMalloc(&h->masks, 2 * B3) != cudaSuccess ||
         cudaMalloc(&h->partials, sizeof(double) * 8 * h->ncand) != cudaSuccess ||
@@ -332,7 +453,9 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
     if (cudaMemcpyAsync(h->st, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         return bail(FLBM_E_CUDA);
     if (cudaMemsetAsync(h->masks, 0, 2 * B3, h->stream) != cudaSuccess) return bail(FLBM_E_CUDA);
-    if (cudaMemsetAsync(h->psi, 0, sizeof(float) * 2 * k.padn, h->stream) != cudaSuccess) return bail(FLBM_E_CUDA);
+    for (int c = 0; c < 2; ++c)
+        if (cudaMemsetAsync(h->psibuf[c], 0, sizeof(float) * 2 * k.padn, h->stream) != cudaSuccess)
+            return bail(FLBM_E_CUDA);
     if (cudaMemsetAsync(h->partials, 0, sizeof(double) * 8 * h->ncand, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->box_counts, 0, sizeof(int) * h->box_blocks, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->box_parts, 0, sizeof(double) * 8 * h->box_blocks, h->stream) != cudaSuccess)
@@ -347,8 +470,22 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
         k_mark<<<1, 1024, 0, h->stream>>>(h->st, h->masks, k);
         if (launch_check(h, "k_mark")) return bail(FLBM_E_CUDA);
     }
+    // The densities of the initial state; later steps keep them (fused) or
+    // recompute them (two-pass).
+    if (launch_psi(h)) return bail(FLBM_E_CUDA);
+    // Fused collide where the lattice allows it: ring buffer for every plane,
+    // seams for the default chunking.
+    h->fused_allowed = fused_ok(k);
+    if (h->fused_allowed) {
+        const FusedGeom g{1, 1, 2 * (k.tx + 2) + 2 * k.ty, (k.tx + 2) * (k.ty + 2)};
+        if (cudaMalloc(&h->ring, sizeof(float2) * (size_t)k.gx * k.gy * k.lz * g.ring) != cudaSuccess)
+            return bail(FLBM_E_NOMEM);
+        if (set_fused_geometry(h, auto_chunk(k))) return bail(FLBM_E_NOMEM);
+        h->density_mode = 1;
+    }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(FLBM_E_CUDA);
     setup_tma(h);
+    h->launches = 0;
     *out = h;
     return FLBM_OK;
 }
@@ -359,6 +496,9 @@ int flbm_step(flbm_t* h, int64_t nsteps)
     h->launches = 0;
     int64_t s = 0;
     if (h->use_graphs) {
+        // A graph captures steps that start from valid densities.
+        if (use_fused(h) && nsteps >= kGraphSteps)
+            if (int rc = ensure_psi(h)) return rc;
         for (; s + kGraphSteps <= nsteps; s += kGraphSteps) {
             if (int rc = ensure_graph(h, h->cur)) return rc;
             CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
@@ -375,16 +515,32 @@ int flbm_use_tma(flbm_t* h, int enable)
     if (!h || (enable != 0 && enable != 1)) return fail(h, FLBM_E_INVAL, "invalid argument");
     if (enable && !h->tma_ok)
         return fail(h, FLBM_E_UNSUPPORTED, "TMA-staged collide needs lx % 4 == 0 and lx >= 32");
-    if (h->tma != (enable != 0)) {
-        // Captured graphs hold the other bulk kernel.
-        CK(h, cudaStreamSynchronize(h->stream));
-        for (int c = 0; c < 2; ++c)
-            if (h->graph[c]) {
-                cudaGraphExecDestroy(h->graph[c]);
-                h->graph[c] = nullptr;
-            }
-    }
+    if (h->tma != (enable != 0))
+        if (int rc = drop_graphs(h)) return rc;  // captured graphs hold the other bulk kernel
     h->tma = enable != 0;
+    return FLBM_OK;
+}
+
+int flbm_set_density_mode(flbm_t* h, int32_t mode, int32_t planes_per_block)
+{
+    if (!h || (mode != 0 && mode != 1) || planes_per_block < 0 || planes_per_block > h->kp.lz)
+        return fail(h, FLBM_E_INVAL, "invalid argument");
+    if (mode == 1 && !h->fused_allowed)
+        return fail(h, FLBM_E_UNSUPPORTED,
+                    "fused densities need tiles at least 8 wide and 3 tiles along a periodic x or y");
+    if (int rc = drop_graphs(h)) return rc;
+    if (mode == 1) {
+        if (int rc = set_fused_geometry(h, planes_per_block ? planes_per_block : auto_chunk(h->kp))) return rc;
+    }
+    h->density_mode = mode;
+    return FLBM_OK;
+}
+
+int flbm_get_density_mode(const flbm_t* h, int32_t* mode, int32_t* planes_per_block)
+{
+    if (!h || !mode || !planes_per_block) return FLBM_E_INVAL;
+    *mode = use_fused(h) ? 1 : 0;
+    *planes_per_block = *mode ? h->fg.K : 0;
     return FLBM_OK;
 }
 
@@ -392,15 +548,8 @@ int flbm_set_tma_wait(flbm_t* h, int64_t cycles)
 {
     if (!h || cycles < 0) return fail(h, FLBM_E_INVAL, "invalid argument");
     if (cycles == 0) cycles = kTmaWaitCycles;
-    if (h->tma_wait != cycles) {
-        // Captured graphs hold the old limit.
-        CK(h, cudaStreamSynchronize(h->stream));
-        for (int c = 0; c < 2; ++c)
-            if (h->graph[c]) {
-                cudaGraphExecDestroy(h->graph[c]);
-                h->graph[c] = nullptr;
-            }
-    }
+    if (h->tma_wait != cycles)
+        if (int rc = drop_graphs(h)) return rc;  // captured graphs hold the old limit
     h->tma_wait = cycles;
     return FLBM_OK;
 }
@@ -422,17 +571,21 @@ int flbm_checkpoint(flbm_t* h, const char* path)
     fill_header(h, &hd);
     std::vector<unsigned char> masks(hd.mask_bytes);
     std::vector<float> f((size_t)2 * 19 * k.N);
+    std::vector<float> psi((size_t)2 * k.padn);
     DevState st;
+    if (int rc = ensure_psi(h)) return rc;
     CK(h, cudaMemcpyAsync(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemcpyAsync(masks.data(), h->masks, hd.mask_bytes, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemcpyAsync(f.data(), h->fbuf[h->cur], hd.f_bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(psi.data(), psi_cur(h), sizeof(float) * psi.size(), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     FILE* fp = std::fopen(path, "wb");
     if (!fp) return fail(h, FLBM_E_INVAL, std::string("cannot open ") + path + " for writing");
     bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1 && std::fwrite(&h->p, sizeof(h->p), 1, fp) == 1 &&
               std::fwrite(&st, sizeof(st), 1, fp) == 1 &&
               std::fwrite(masks.data(), 1, hd.mask_bytes, fp) == hd.mask_bytes &&
-              std::fwrite(f.data(), 1, hd.f_bytes, fp) == hd.f_bytes;
+              std::fwrite(f.data(), 1, hd.f_bytes, fp) == hd.f_bytes &&
+              std::fwrite(psi.data(), sizeof(float), psi.size(), fp) == psi.size();
     ok = (std::fclose(fp) == 0) && ok;
     return ok ? FLBM_OK : fail(h, FLBM_E_INVAL, std::string("write to ") + path + " failed");
 }
@@ -449,7 +602,8 @@ int flbm_restore(flbm_t* h, const char* path)
     std::vector<unsigned char> masks(want.mask_bytes);
     std::vector<float> f((size_t)2 * 19 * h->kp.N);
     bool ok = std::fread(&got, sizeof(got), 1, fp) == 1;
-    if (ok && (std::memcmp(got.magic, want.magic, sizeof(got.magic)) != 0 || got.version != want.version ||
+    if (ok && (std::memcmp(got.magic, want.magic, sizeof(got.magic)) != 0 || got.version < 1 ||
+               got.version > want.version ||
                got.params_bytes != want.params_bytes || got.state_bytes != want.state_bytes)) {
         std::fclose(fp);
         return fail(h, FLBM_E_INVAL, std::string(path) + ": not a checkpoint of this library version");
@@ -463,6 +617,9 @@ int flbm_restore(flbm_t* h, const char* path)
     ok = ok && std::fread(&fp_params, sizeof(fp_params), 1, fp) == 1 && std::fread(&st, sizeof(st), 1, fp) == 1 &&
          std::fread(masks.data(), 1, want.mask_bytes, fp) == want.mask_bytes &&
          std::fread(f.data(), 1, want.f_bytes, fp) == want.f_bytes;
+    // Version 2 carries the state's densities; version 1 files get them recomputed.
+    std::vector<float> psi(got.version >= 2 ? (size_t)2 * h->kp.padn : 0);
+    ok = ok && (psi.empty() || std::fread(psi.data(), sizeof(float), psi.size(), fp) == psi.size());
     std::fclose(fp);
     if (!ok) return fail(h, FLBM_E_INVAL, std::string(path) + ": truncated checkpoint");
     const std::string bad = check_restored_state(st, h->kp);
@@ -483,6 +640,12 @@ int flbm_restore(flbm_t* h, const char* path)
     CK(h, cudaMemcpyAsync(h->st, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->masks, masks.data(), want.mask_bytes, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->fbuf[h->cur], f.data(), want.f_bytes, cudaMemcpyHostToDevice, h->stream));
+    if (!psi.empty()) {
+        CK(h, cudaMemcpyAsync(psi_cur(h), psi.data(), sizeof(float) * psi.size(), cudaMemcpyHostToDevice, h->stream));
+        h->psi_valid = true;
+    } else if (int rc = launch_psi(h)) {
+        return rc;
+    }
     CK(h, cudaStreamSynchronize(h->stream));
     return FLBM_OK;
 }
@@ -530,8 +693,8 @@ int flbm_read_fields(flbm_t* h, float* host_f, float* host_rho)
                               h->stream));
     if (host_rho) {
         if (!h->scratch_rho) CK(h, cudaMalloc(&h->scratch_rho, sizeof(float) * 2 * k.N));
-        if (int rc = launch_psi(h, h->fbuf[h->cur])) return rc;
-        k_unpad<<<h->grid, h->block, 0, h->stream>>>(h->psi, h->scratch_rho, k);
+        if (int rc = ensure_psi(h)) return rc;
+        k_unpad<<<h->grid, h->block, 0, h->stream>>>(psi_cur(h), h->scratch_rho, k);
         if (int rc = launch_check(h, "k_unpad")) return rc;
         CK(h, cudaMemcpyAsync(host_rho, h->scratch_rho, sizeof(float) * 2 * k.N, cudaMemcpyDeviceToHost,
                               h->stream));
@@ -545,6 +708,7 @@ int flbm_write_fields(flbm_t* h, const float* host_f)
     if (!h || !host_f) return fail(h, FLBM_E_INVAL, "NULL argument");
     CK(h, cudaMemcpyAsync(h->fbuf[h->cur], host_f, sizeof(float) * 2 * 19 * h->kp.N, cudaMemcpyHostToDevice,
                           h->stream));
+    if (int rc = launch_psi(h)) return rc;
     CK(h, cudaStreamSynchronize(h->stream));
     return FLBM_OK;
 }
@@ -577,6 +741,7 @@ int flbm_set_particle(flbm_t* h, const double X[3], const double V[3], const dou
     CK(h, cudaMemcpyAsync(h->st, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
     k_mark<<<1, 1024, 0, h->stream>>>(h->st, h->masks, h->kp);
     if (int rc = launch_check(h, "k_mark")) return rc;
+    if (int rc = launch_psi(h)) return rc;  // particle nodes and virtual layer moved
     CK(h, cudaStreamSynchronize(h->stream));
     return FLBM_OK;
 }
@@ -594,7 +759,9 @@ int flbm_run_host(flbm_t* h, const float* host_f_in, int64_t nsteps, float* host
         h->traj_cap = (size_t)nsteps;
     }
     CK(h, cudaMemcpyAsync(h->fbuf[h->cur], host_f_in, fbytes, cudaMemcpyHostToDevice, h->stream));
-    int64_t launches = 0;
+    h->launches = 0;
+    if (int rc = launch_psi(h)) return rc;
+    int64_t launches = h->launches;
     for (int64_t s = 0; s < nsteps; ++s) {
         h->launches = 0;
         if (int rc = launch_step(h)) return rc;
@@ -634,6 +801,7 @@ int flbm_step_timed(flbm_t* h, int64_t nsteps, double* ms)
         h->events.push_back(e);
     }
     h->launches = 0;
+    const int* order = use_fused(h) ? kFusedOrder : kTwoPassOrder;
     for (int64_t s = 0; s < nsteps; ++s)
         if (int rc = launch_step(h, h->events.data() + (FLBM_NKERNELS + 1) * s)) return rc;
     CK(h, cudaStreamSynchronize(h->stream));
@@ -643,7 +811,7 @@ int flbm_step_timed(flbm_t* h, int64_t nsteps, double* ms)
         for (int k = 0; k < FLBM_NKERNELS; ++k) {
             float t = 0.0f;
             CK(h, cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
-            ms[k] += t;
+            ms[order[k]] += t;
         }
     }
     return FLBM_OK;
@@ -663,7 +831,10 @@ void flbm_destroy(flbm_t* h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     cudaFree(h->f_owned);
-    cudaFree(h->psi);
+    cudaFree(h->psibuf[0]);
+    cudaFree(h->psibuf[1]);
+    cudaFree(h->ring);
+    cudaFree(h->seam);
     cudaFree(h->st);
     cudaFree(h->masks);
     cudaFree(h->partials);

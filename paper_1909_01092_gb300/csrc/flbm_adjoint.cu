@@ -1024,6 +1024,7 @@ struct AdjBuffers {
     float* ck_f = nullptr;     // checkpoints: populations (current copy)
     DevState* ck_st = nullptr; // checkpoints: particle record
     uint8_t* ck_m = nullptr;   // checkpoints: both particle masks
+    float* ck_psi = nullptr;   // checkpoints: density field of the state (the fused step carries it)
     float* tape = nullptr;     // K+1 moment fields
     DevState* tape_st = nullptr;
     uint8_t* tape_m = nullptr;
@@ -1067,21 +1068,28 @@ int acheck(flbm_sim* h, const char* what)
     } while (0)
 
 // Copy the handle's state (current populations, particle record, masks) to or from a slot.
-int save_state(flbm_sim* h, float* f, DevState* st, uint8_t* m, size_t mbytes)
+// The state a step reads: populations, particle record, masks and the
+// density field (so that a recomputed segment repeats the forward run bit
+// for bit whichever way the step forms its densities).
+int save_state(flbm_sim* h, float* f, DevState* st, uint8_t* m, size_t mbytes, float* psi)
 {
     const size_t fbytes = sizeof(float) * 2 * 19 * h->kp.N;
+    if (int rc = sim_ensure_psi(h)) return rc;
     ACK(h, cudaMemcpyAsync(f, h->fbuf[h->cur], fbytes, cudaMemcpyDeviceToDevice, h->stream));
     ACK(h, cudaMemcpyAsync(st, h->st, sizeof(DevState), cudaMemcpyDeviceToDevice, h->stream));
     ACK(h, cudaMemcpyAsync(m, h->masks, mbytes, cudaMemcpyDeviceToDevice, h->stream));
+    ACK(h, cudaMemcpyAsync(psi, psi_cur(h), sizeof(float) * 2 * h->kp.padn, cudaMemcpyDeviceToDevice, h->stream));
     return FLBM_OK;
 }
 
-int load_state(flbm_sim* h, const float* f, const DevState* st, const uint8_t* m, size_t mbytes)
+int load_state(flbm_sim* h, const float* f, const DevState* st, const uint8_t* m, size_t mbytes, const float* psi)
 {
     const size_t fbytes = sizeof(float) * 2 * 19 * h->kp.N;
     ACK(h, cudaMemcpyAsync(h->fbuf[h->cur], f, fbytes, cudaMemcpyDeviceToDevice, h->stream));
     ACK(h, cudaMemcpyAsync(h->st, st, sizeof(DevState), cudaMemcpyDeviceToDevice, h->stream));
     ACK(h, cudaMemcpyAsync(h->masks, m, mbytes, cudaMemcpyDeviceToDevice, h->stream));
+    ACK(h, cudaMemcpyAsync(psi_cur(h), psi, sizeof(float) * 2 * h->kp.padn, cudaMemcpyDeviceToDevice, h->stream));
+    h->psi_valid = true;
     return FLBM_OK;
 }
 
@@ -1097,15 +1105,18 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     const uint8_t* m0 = b.tape_m + (size_t)kk * mbytes;
     const uint8_t* m1 = m0 + mbytes;
     cudaStream_t st = h->stream;
+    // The reverse step rebuilds its densities from the tape in the density
+    // buffer the current state does not use.
+    float* psi_scr = h->psibuf[1 - h->cur];
     // The step's density field from the tape (side stream) does not depend on
     // the particle adjoint (handle's stream); the two join before the node kernels.
     ACK(h, cudaEventRecord(h->fork_ev, st));
     ACK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
-    ka_psi_tape<<<h->grid, h->block, 0, h->side>>>(tn, h->psi, s0, m0, k);
+    ka_psi_tape<<<h->grid, h->block, 0, h->side>>>(tn, psi_scr, s0, m0, k);
     if (int rc = acheck(h, "ka_psi_tape")) return rc;
     const unsigned nbs = (unsigned)((shell_count(k) + kThreads - 1) / kThreads);
     const unsigned nbv = (unsigned)((B3 + kThreads - 1) / kThreads);
-    k_shell_virtual<<<nbs + nbv, kThreads, 0, h->side>>>(h->psi, s0, m0, k, (int)nbs);
+    k_shell_virtual<<<nbs + nbv, kThreads, 0, h->side>>>(psi_scr, s0, m0, k, (int)nbs);
     if (int rc = acheck(h, "k_shell_virtual")) return rc;
     ACK(h, cudaEventRecord(h->join_ev, h->side));
     ka_pre<<<1, 1, 0, st>>>(b.adj, s1);
@@ -1122,18 +1133,18 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     // (disjoint nodes and partials), joined before the psi adjoint.
     ACK(h, cudaEventRecord(h->fork_ev, st));
     ACK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
-    ka_node_near<<<dim3(k.ncx, k.ncy, k.ncz), h->block, 0, h->side>>>(tn, h->psi, L1, L0, b.lgf, s0, m0, b.adj,
+    ka_node_near<<<dim3(k.ncx, k.ncy, k.ncz), h->block, 0, h->side>>>(tn, psi_scr, L1, L0, b.lgf, s0, m0, b.adj,
                                                                        b.parts, k);
     if (int rc = acheck(h, "ka_node_near")) return rc;
     ACK(h, cudaEventRecord(h->join_ev, h->side));
-    ka_node_bulk<<<h->grid, h->block, 0, st>>>(tn, h->psi, L1, L0, b.lgf, s0, m0, b.adj, b.parts, k);
+    ka_node_bulk<<<h->grid, h->block, 0, st>>>(tn, psi_scr, L1, L0, b.lgf, s0, m0, b.adj, b.parts, k);
     if (int rc = acheck(h, "ka_node_bulk")) return rc;
     ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
     // psi adjoint at particle nodes (side) and at wall ghosts (handle's
     // stream): disjoint points of lpsi, joined before ka_final.
     ACK(h, cudaEventRecord(h->fork_ev, st));
     ACK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
-    ka_lpsi<<<h->box_blocks, kT, 0, h->side>>>(b.lgf, h->psi, b.lpsi, s0, m0, b.adj, b.parts2, k);
+    ka_lpsi<<<h->box_blocks, kT, 0, h->side>>>(b.lgf, psi_scr, b.lpsi, s0, m0, b.adj, b.parts2, k);
     if (int rc = acheck(h, "ka_lpsi")) return rc;
     ACK(h, cudaEventRecord(h->join_ev, h->side));
     ka_lpsi_shell<<<nbs, kT, 0, st>>>(b.lgf, b.lpsi, s0, m0, k);
@@ -1170,7 +1181,8 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
     const size_t fN = 2 * 19 * N;
     AdjBuffers b;
     if (!b.alloc(b.ck_f, (size_t)(nck + 1) * fN) || !b.alloc(b.ck_st, (size_t)(nck + 1)) ||
-        !b.alloc(b.ck_m, (size_t)(nck + 1) * mbytes) || !b.alloc(b.tape, (size_t)(K + 1) * 8 * N) ||
+        !b.alloc(b.ck_m, (size_t)(nck + 1) * mbytes) || !b.alloc(b.ck_psi, (size_t)(nck + 1) * 2 * k.padn) ||
+        !b.alloc(b.tape, (size_t)(K + 1) * 8 * N) ||
         !b.alloc(b.tape_st, (size_t)(K + 1)) || !b.alloc(b.tape_m, (size_t)(K + 1) * mbytes) ||
         !b.alloc(b.lam[0], 8 * N) || !b.alloc(b.lam[1], 8 * N) || !b.alloc(b.lgf, 6 * N) ||
         !b.alloc(b.lpsi, (size_t)(2 * k.padn)) || !b.alloc(b.uv, 2 * B3) ||
@@ -1195,13 +1207,17 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
     for (int64_t s = 0; s < T; ++s) {
         if (s % K == 0) {
             const int64_t c = s / K;
-            if (int rc = save_state(h, b.ck_f + c * fN, b.ck_st + c, b.ck_m + c * mbytes, mbytes)) return rc;
+            if (int rc = save_state(h, b.ck_f + c * fN, b.ck_st + c, b.ck_m + c * mbytes, mbytes,
+                                    b.ck_psi + c * 2 * k.padn))
+                return rc;
         }
         if (int rc = sim_step(h)) return rc;
         ka_accJ<<<1, 1, 0, st>>>(h->st, b.adj);
         if (int rc = acheck(h, "ka_accJ")) return rc;
     }
-    if (int rc = save_state(h, b.ck_f + nck * fN, b.ck_st + nck, b.ck_m + nck * mbytes, mbytes)) return rc;
+    if (int rc = save_state(h, b.ck_f + nck * fN, b.ck_st + nck, b.ck_m + nck * mbytes, mbytes,
+                            b.ck_psi + nck * 2 * k.padn))
+        return rc;
     cudaEventRecord(ev[1], st);
     // Reverse sweep, segment by segment from the last.
     const double vol = 4.0 / 3.0 * M_PI * p.radius * p.radius * p.radius;
@@ -1211,7 +1227,9 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
     for (int64_t c = nck - 1; c >= 0; --c) {
         const int64_t s0 = c * K;
         const int Ls = (int)std::min<int64_t>(K, T - s0);
-        if (int rc = load_state(h, b.ck_f + c * fN, b.ck_st + c, b.ck_m + c * mbytes, mbytes)) return rc;
+        if (int rc = load_state(h, b.ck_f + c * fN, b.ck_st + c, b.ck_m + c * mbytes, mbytes,
+                                b.ck_psi + c * 2 * k.padn))
+            return rc;
         for (int kk = 0; kk <= Ls; ++kk) {
             ka_tape<<<h->grid, h->block, 0, st>>>(h->fbuf[h->cur], b.tape + (size_t)kk * 8 * N, k);
             if (int rc = acheck(h, "ka_tape")) return rc;
@@ -1225,7 +1243,9 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
             lcur = 1 - lcur;
         }
     }
-    if (int rc = load_state(h, b.ck_f + nck * fN, b.ck_st + nck, b.ck_m + nck * mbytes, mbytes)) return rc;
+    if (int rc = load_state(h, b.ck_f + nck * fN, b.ck_st + nck, b.ck_m + nck * mbytes, mbytes,
+                            b.ck_psi + nck * 2 * k.padn))
+        return rc;
     cudaEventRecord(ev[2], st);
     AdjState a;
     ACK(h, cudaMemcpyAsync(&a, b.adj, sizeof(a), cudaMemcpyDeviceToHost, st));

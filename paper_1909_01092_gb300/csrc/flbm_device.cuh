@@ -221,6 +221,7 @@ struct DevState {
     int cur;               // index of the current mask
     int box0[3];           // origin of the particle box (periodic axes in [0, L))
     int box_next[3];       // origin at the position after this step's update
+    int box_prev[3];       // origin the last step's collide used (its near tiles)
     int err;
     unsigned near_done;    // blocks of the near-collide launch done this step (last one updates)
     unsigned cover_done;   // blocks of the cover launch done this step (last one finishes)

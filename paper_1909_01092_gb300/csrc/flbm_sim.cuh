@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "flbm_fused.cuh"
 #include "flbm_host.cuh"
 
 using flbm::DevState;
@@ -20,7 +21,21 @@ struct flbm_sim {
     float* fbuf[2] = {nullptr, nullptr};
     void* f_owned = nullptr;
     int cur = 0;  // fbuf[cur] holds the current state
-    float* psi = nullptr;
+    // Padded density fields: psibuf[c] holds the densities of the state in
+    // fbuf[c] (Shan-Chen pseudo-potential with its shell and virtual layer).
+    // psi_valid: psibuf[cur] is up to date with fbuf[cur]; the fused step keeps
+    // it so (it writes psibuf[1 - cur] as it streams), the two-pass step
+    // recomputes it at the start of every step.
+    float* psibuf[2] = {nullptr, nullptr};
+    bool psi_valid = false;
+    // Density mode: 0 two-pass (density pass every step), 1 fused (densities
+    // as a by-product of the collide); fused only where fused_ok allows it.
+    int density_mode = 0;
+    bool fused_allowed = false;
+    flbm::FusedGeom fg{};
+    float2* ring = nullptr;        // ring partials: tiles x lz x fg.ring
+    float2* seam = nullptr;        // seam partials: tiles x nchunk x 2 x fg.fp
+    size_t seam_cap = 0;           // float2 slots allocated for seam
     DevState* st = nullptr;
     uint8_t* masks = nullptr;
     double* partials = nullptr;    // per candidate near tile: force, torque, ledger
@@ -46,7 +61,7 @@ struct flbm_sim {
     // the two population copies and of the padded densities; tma_ok when the
     // lattice allows it, tma when it is in use; persistent grid size.
     CUtensorMap tm_f[2];
-    CUtensorMap tm_psi;
+    CUtensorMap tm_psi[2];
     bool tma_ok = false;
     bool tma = false;
     int tma_grid = 0;
@@ -63,11 +78,18 @@ struct flbm_sim {
 
 namespace flbm {
 
+// Densities of the current state.
+inline float* psi_cur(flbm_sim* h) { return h->psibuf[h->cur]; }
+
 // Launch one time step on h's stream (h->cur flips). With ev, events
 // ev[0..5] are recorded between its kernel classes.
 int sim_step(flbm_sim* h, cudaEvent_t* ev = nullptr);
 
 // Record an error message on h and return code.
 int sim_fail(flbm_sim* h, int code, const std::string& msg);
+
+// Make psibuf[cur] hold the current state's densities (a density pass if
+// they are stale).
+int sim_ensure_psi(flbm_sim* h);
 
 }  // namespace flbm

@@ -120,6 +120,16 @@ struct GlobalInputs {
     __device__ __forceinline__ float psb(int i) const { return __ldg(pA + padn + off(i)); }
 };
 
+// Receiver of the pushed populations for callers that also want the next
+// step's densities (the fused bulk collide); put(l, i, v, bounced) sees every
+// population v = f*_li the node pushes outside the particle, bounced = true
+// when a wall sent it back into the node itself. The default receiver does
+// nothing and compiles away.
+struct NoSink {
+    static constexpr bool active = false;
+    __device__ __forceinline__ void put(int, int, float, bool) {}
+};
+
 // Collision and push-streaming of one fluid node (Eq. (lbe)). With PARTICLE,
 // solid_nb marks the directions whose neighbour is a particle node; their
 // links take the moving rule and feed acc = (F[3], T[3], ledger[2]). TAU1:
@@ -127,10 +137,11 @@ struct GlobalInputs {
 // input only through rho_l and j_l, and the ghost modes carry noise only.
 // The inputs come from `in` (global memory or a shared-memory tile); the
 // outputs are pushed to fout, population (l, i) of node m at m + P.dirN[19 l + i].
-template <bool NOISE, bool PARTICLE, bool TAU1, class In>
+template <bool NOISE, bool PARTICLE, bool TAU1, class In, class Sink = NoSink>
 __device__ __forceinline__ void collide_core(int x, int y, int z, uint32_t n, const In& in,
                                              float* __restrict__ fout, const DevState* __restrict__ st,
-                                             const KParams& P, uint32_t solid_nb, double* acc)
+                                             const KParams& P, uint32_t solid_nb, double* acc,
+                                             Sink* sink = nullptr)
 {
     float ma[19], mb[19];
     float rhoA, rhoB;
@@ -313,6 +324,7 @@ __device__ __forceinline__ void collide_core(int x, int y, int z, uint32_t n, co
             if (cz) off += cz > 0 ? offp[2] : offm[2];
             const uint32_t push_idx = n + (uint32_t)off + P.dirN[19 * l + i];
             fout[wall ? back_idx : push_idx] = fo[i];
+            if constexpr (Sink::active) sink->put(l, i, fo[i], wall);
         }
     }
     if (PARTICLE && solid_nb) {
@@ -749,6 +761,7 @@ __device__ __forceinline__ void finish_step(DevState* __restrict__ st, const int
     st->delta_f[1] = (float)st->delta[1];
     st->fc = P.counterforce ? -st->Fp / (double)nf : 0.0;
     st->fc_f = (float)st->fc;
+    st->box_prev[0] = st->box0[0]; st->box_prev[1] = st->box0[1]; st->box_prev[2] = st->box0[2];
     st->box0[0] = st->box_next[0]; st->box0[1] = st->box_next[1]; st->box0[2] = st->box_next[2];
     st->cur = 1 - st->cur;
     st->step += 1;

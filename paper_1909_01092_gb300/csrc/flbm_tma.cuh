@@ -59,11 +59,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
+// Non-blocking test of phase `parity` of the mbarrier.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Waits for phase `parity` of the mbarrier for at most `limit` SM cycles.
+// With the default limit the thread waits in try_wait, which the hardware may
+// suspend until the phase completes. A shorter limit polls with test_wait,
+// which returns at once, so that the limit itself decides.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit = kTmaWaitCycles)
 {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
+    if (limit >= kTmaWaitCycles) {
+        while (!mbar_try_wait(bar, parity))
+            if (clock64() - t0 > limit) return false;
+        return true;
+    }
+    while (!mbar_test_wait(bar, parity))
         if (clock64() - t0 > limit) return false;
     return true;
 }

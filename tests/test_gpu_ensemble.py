@@ -48,9 +48,12 @@ def _fluid(p, X):
 
 
 def _singles(flbm, plist, steps):
+    """Single simulations in the ensemble's density mode (a density pass each
+    step), so that members and singles do the same arithmetic."""
     out = []
     for p in plist:
         s = flbm.Sim(p)
+        s.set_density_mode(0)
         s.step(steps)
         out.append((s.read_f(), s.particle()))
         s.close()

@@ -49,6 +49,7 @@ def test_tma_equals_direct_kernel_bit_for_bit(flbm, case):
     a, b = flbm.Sim(p), flbm.Sim(p)
     a.use_tma(True)
     b.use_tma(False)
+    b.set_density_mode(0)  # the TMA-staged kernel runs with a density pass
     a.step(17)
     b.step(17)
     pa, pb = a.particle(), b.particle()
@@ -125,6 +126,7 @@ def test_a_wait_that_runs_out_reports_a_timeout_and_the_context_stays_usable(flb
     broken.close()
     a, b = flbm.Sim(p), flbm.Sim(p)
     a.use_tma(True)
+    b.set_density_mode(0)
     a.step(6)
     b.step(6)
     a.particle()  # no error flagged

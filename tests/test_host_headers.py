@@ -19,6 +19,12 @@ brute-force scan of the lattice:
 * tests/host_modes.cu (to_modes, from_modes, bnorm): the collision's
   hand-factored transforms against the D3Q19 mode basis written out from its
   polynomials, exactly, and their round trip;
+* tests/host_fused.cu (DensitySink, gather_column, roll_update, put_density,
+  FinishItems, finish_node, near_dilated, near_box_axis): the fused collide's
+  data flow replayed block by block on random lattices, planes per block and
+  particle boxes gives every node outside the near-particle region the direct
+  sum of the 19 values pushed into it, each such node completed once, and the
+  near-particle region lies in the box its recompute walks;
 * tests/host_restore.cu (check_restored_state): a particle record read from
   a checkpoint passes when it is one the library wrote, and is refused when
   its mask index, centre, velocities, box origin, fluid count, step or mass
@@ -70,3 +76,10 @@ def test_restored_particle_records_are_checked(tmp_path):
     words = out.split()
     configs, refused, failed = (int(words[words.index(w) + 1]) for w in ("configurations", "refused", "failed"))
     assert failed == 0 and configs > 300 and refused > 6 * configs, out
+
+
+def test_fused_density_bookkeeping_gives_the_direct_sums(tmp_path):
+    out = _build_and_run(tmp_path, "host_fused", 300)
+    words = out.split()
+    run, failed, with_particle = (int(words[words.index(w) + 1]) for w in ("configurations", "failed", "with_particle"))
+    assert failed == 0 and run == 300 and with_particle > 100, out
