@@ -268,14 +268,17 @@ int flbm_use_tma(flbm_t* h, int enable);
  * of Eq. (sc-force) reads at the next step.
  *   mode 0 (two-pass): a density pass re-reads every population at the start
  *     of each step (152 B per node of extra HBM traffic);
- *   mode 1 (fused, the default where the lattice allows it): the collide-stream
+ *   mode 1 (fused): the collide-stream
  *     sums the populations it pushes into each node as it writes them, and a
  *     small completion kernel adds the partial sums across tile and chunk
  *     boundaries and recomputes the densities next to the particle after
  *     cover/uncover. The densities are then carried from step to step (and
  *     saved by flbm_checkpoint).
  * The two modes compute the same sums in different orders: they agree to
- * float32 rounding, and each is bit-reproducible. planes_per_block (fused
+ * float32 rounding, and each is bit-reproducible. Mode 0 is the default: on
+ * GB300 the fused collide's exchange of pushed values between the threads of
+ * a block (two barriers per plane, about 600 more instructions per node)
+ * costs more than the density pass it removes. planes_per_block (fused
  * only) is how many consecutive z-planes one block of the fused collide walks;
  * 0 chooses about two waves of blocks for this GPU. The TMA-staged collide
  * (flbm_use_tma) always runs two-pass. Captured step graphs are dropped.

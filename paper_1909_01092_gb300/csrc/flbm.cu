@@ -192,7 +192,7 @@ int launch_collide(flbm_sim* h, bool fused)
             CK(h, cudaEventRecord(h->join_ev, h->side));                                                      \
         }                                                                                                     \
         if (fused) {                                                                                          \
-            k_collide_bulk_fused<NZ, T1><<<gfused, h->block, 0, h->stream>>>(                                  \
+            k_collide_bulk_fused<NZ, T1><<<gfused, h->block, fused_smem_bytes(k), h->stream>>>(                \
                 fin, fout, psi, h->psibuf[1 - h->cur], h->ring, h->seam, h->st, k, h->fg);                    \
             if (int rc = launch_check(h, "k_collide_bulk_fused")) return rc;                                  \
         } else if (h->tma) {                                                                                  \
@@ -473,15 +473,24 @@ int flbm_create(const flbm_params* p, void* f_dev, size_t f_dev_bytes, void* str
     // The densities of the initial state; later steps keep them (fused) or
     // recompute them (two-pass).
     if (launch_psi(h)) return bail(FLBM_E_CUDA);
-    // Fused collide where the lattice allows it: ring buffer for every plane,
-    // seams for the default chunking.
+    // The fused collide is available where the lattice allows it (ring buffer
+    // for every plane, seams for the default chunking); steps are two-pass
+    // until flbm_set_density_mode selects it.
     h->fused_allowed = fused_ok(k);
     if (h->fused_allowed) {
+        // Exchange arrays and rolling sums in dynamic shared memory (above the
+        // 48 KB default for 32 x 8 tiles).
+        void (*fused_kern[4])(const float*, float*, const float*, float*, float2*, float2*, const DevState*, KParams,
+                              FusedGeom) = {k_collide_bulk_fused<false, false>, k_collide_bulk_fused<false, true>,
+                                            k_collide_bulk_fused<true, false>, k_collide_bulk_fused<true, true>};
+        for (auto* fk : fused_kern)
+            if (cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes(k)) !=
+                cudaSuccess)
+                return bail(FLBM_E_CUDA);
         const FusedGeom g{1, 1, 2 * (k.tx + 2) + 2 * k.ty, (k.tx + 2) * (k.ty + 2)};
         if (cudaMalloc(&h->ring, sizeof(float2) * (size_t)k.gx * k.gy * k.lz * g.ring) != cudaSuccess)
             return bail(FLBM_E_NOMEM);
         if (set_fused_geometry(h, auto_chunk(k))) return bail(FLBM_E_NOMEM);
-        h->density_mode = 1;
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(FLBM_E_CUDA);
     setup_tma(h);

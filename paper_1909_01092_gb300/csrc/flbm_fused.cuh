@@ -163,89 +163,156 @@ __host__ __device__ __forceinline__ void near_box_axis(int o, int T, int nc, int
     if (!wall && len > L) len = L;
 }
 
+// Shared-memory exchange of the values that leave a node's column: per
+// direction one float2 (A, B) array over the tile padded by two columns on
+// either side and one row above and below, (TX + 4) x (TY + 2). The padding
+// and the cells of a ragged tile's missing nodes are zero and stay zero, so
+// a column (or a ring position) gathers its incoming values at fixed offsets
+// without tests: values from outside the tile read as 0.
+__host__ __device__ __forceinline__ int xch_pitch(const KParams& P) { return P.tx + 4; }
+__host__ __device__ __forceinline__ int xch_size(const KParams& P) { return (P.tx + 4) * (P.ty + 2); }
+__host__ __device__ __forceinline__ int xch_pos(int fx, int fy, const KParams& P) { return (fx + 2) + (P.tx + 4) * (fy + 1); }
+__host__ __device__ __forceinline__ size_t fused_smem_bytes(const KParams& P)
+{
+    return sizeof(float2) * (size_t)(kXchDirs * xch_size(P) + 2 * kThreadsStep + 2 * kRingMax);
+}
+
 // Receiver of one node's pushed populations (see collide_core): the own
-// column's contributions per component to the planes z - 1, z, z + 1, and the
-// 16 values leaving the column into shared memory.
+// column's contributions per component to the planes z - 1, z, z + 1
+// (everything a wall bounced back counts for plane z), and the 16 values
+// leaving the column into the exchange arrays (component l in .x or .y).
 struct DensitySink {
     static constexpr bool active = true;
-    float* xch;  // [2][16][256]
-    int tid;
+    float* xch;  // float2 [16][xch_size], viewed as floats
+    int pos;     // xch_pos of the node
+    int size;    // xch_size
     float own[2][3];
-    __host__ __device__ __forceinline__ DensitySink(float* x, int t) : xch(x), tid(t)
+    __host__ __device__ __forceinline__ DensitySink(float* x, int p, int sz) : xch(x), pos(p), size(sz)
     {
 #pragma unroll
         for (int l = 0; l < 2; ++l) own[l][0] = own[l][1] = own[l][2] = 0.0f;
     }
     __host__ __device__ __forceinline__ void put(int l, int i, float v, bool bounced)
     {
-        if (bounced) {  // back into this node at this plane
+        if (i == 0) {
             own[l][1] += v;
             return;
         }
-        if (i == 0) own[l][1] += v;
-        else if (i == 5) own[l][2] += v;
-        else if (i == 6) own[l][0] += v;
-        else xch[(l * kXchDirs + xch_slot(i)) * kThreadsStep + tid] = v;
+        if (bounced) own[l][1] += v;
+        if (i == 5) {
+            if (!bounced) own[l][2] += v;
+        } else if (i == 6) {
+            if (!bounced) own[l][0] += v;
+        } else {
+            // A bounced value is stored too: its target lies across the wall,
+            // where no node and no ring position gathers it.
+            xch[2 * (xch_slot(i) * size + pos) + l] = v;
+        }
     }
 };
 
-// Values pushed into column (fx, fy) of the tile from inside the tile at the
-// plane just pushed, per destination plane (index cz + 1) and component.
-__host__ __device__ __forceinline__ void gather_column(int fx, int fy, int w, int h, const float* xch,
-                                                       const KParams& P, float inc[3][2])
+// Values pushed into the column at exchange position p from the tile's
+// nodes at the plane just pushed, per destination plane (index cz + 1). For
+// a node of the tile all 16 directions; the missing ones read as 0.
+__host__ __device__ __forceinline__ void gather_column(int p, const float2* xch, const KParams& P, float2 inc[3])
 {
+    const int pitch = xch_pitch(P), size = xch_size(P);
 #pragma unroll
     for (int s = 0; s < kXchDirs; ++s) {
         const int d = xch_dir(s);
-        const int sx = fx - cxv(d), sy = fy - cyv(d);
-        if ((unsigned)sx < (unsigned)w && (unsigned)sy < (unsigned)h) {
-            const int src = sx + P.tx * sy;
-            inc[czv(d) + 1][0] += xch[s * kThreadsStep + src];
-            inc[czv(d) + 1][1] += xch[(kXchDirs + s) * kThreadsStep + src];
-        }
+        const float2 v = xch[s * size + p - cxv(d) - pitch * cyv(d)];
+        inc[czv(d) + 1].x += v.x;
+        inc[czv(d) + 1].y += v.y;
     }
+}
+
+// The same for a ring position on side `side` (0 south row, 1 north row, 2
+// west column, 3 east column): only the five directions that cross that side
+// can bring values from the tile (corners lie in the rows and read zeros
+// for the directions that miss the tile).
+__host__ __device__ __forceinline__ void gather_ring(int side, int p, const float2* xch, const KParams& P,
+                                                     float2 inc[3])
+{
+    const int pitch = xch_pitch(P), size = xch_size(P);
+#pragma unroll
+    for (int s = 0; s < kXchDirs; ++s) {
+        const int d = xch_dir(s);
+        const bool take = side == 0 ? cyv(d) < 0 : side == 1 ? cyv(d) > 0 : side == 2 ? cxv(d) < 0 : cxv(d) > 0;
+        if (!take) continue;
+        const float2 v = xch[s * size + p - cxv(d) - pitch * cyv(d)];
+        inc[czv(d) + 1].x += v.x;
+        inc[czv(d) + 1].y += v.y;
+    }
+}
+
+// Side of ring slot r (see ring_pos).
+__host__ __device__ __forceinline__ int ring_side(int r, const KParams& P)
+{
+    const int R = P.tx + 2;
+    return r < R ? 0 : r < 2 * R ? 1 : r < 2 * R + P.ty ? 2 : 3;
 }
 
 // Stores a density (both components) of destination plane zd for footprint
 // position (fx, fy) of the block's tile: the tile's own nodes into psi_next
 // (zd inside the chunk), ring positions into the ring buffer, and the planes
 // just outside the chunk into the seams. Planes across a z wall are skipped.
-__host__ __device__ __forceinline__ void put_density(int zd, int fx, int fy, bool in_tile, int slot, float a, float b,
-                                            int tile, int bx, int by, int c, int z0, int z1,
-                                            float* __restrict__ psi_next, float2* __restrict__ ring,
-                                            float2* __restrict__ seam, const KParams& P, const FusedGeom& G)
+__host__ __device__ __forceinline__ void put_density(int zd, int fx, int fy, bool in_tile, int slot, float2 v,
+                                                     int tile, int bx, int by, int c, int z0, int z1,
+                                                     float* __restrict__ psi_next, float2* __restrict__ ring,
+                                                     float2* __restrict__ seam, const KParams& P,
+                                                     const FusedGeom& G)
 {
     if (zd >= z0 && zd < z1) {
         if (in_tile) {
             const long long q = pad_index(bx * P.tx + fx, by * P.ty + fy, zd, P);
-            psi_next[q] = a;
-            psi_next[P.padn + q] = b;
+            psi_next[q] = v.x;
+            psi_next[P.padn + q] = v.y;
         } else {
-            ring[ring_index(tile, zd, slot, P, G)] = make_float2(a, b);
+            ring[ring_index(tile, zd, slot, P, G)] = v;
         }
         return;
     }
     if ((zd < 0 || zd >= P.lz) && P.wall[2]) return;
     const int side = zd < z0 ? 0 : 1;
-    seam[seam_index(tile, c, side, fp_index(fx, fy, P), G)] = make_float2(a, b);
+    seam[seam_index(tile, c, side, fp_index(fx, fy, P), G)] = v;
 }
 
 // One plane's update of a column's rolling sums, for the plane z just
-// pushed. Before, roll holds the partial densities (A, B) of planes z - 1 and
-// z; after, those of planes z and z + 1, and r the complete densities of
-// plane z - 1. own: the column's own contributions to planes z - 1, z, z + 1
-// (none for ring positions); inc: what neighbours in the tile pushed into the
-// column, per destination plane.
-__host__ __device__ __forceinline__ void roll_update(float roll[4], const float own[2][3], const float inc[3][2],
-                                                     float r[2])
+// pushed. Before, roll[0] and roll[1] hold the partial densities (A, B) of
+// planes z - 1 and z; after, those of planes z and z + 1, and the result is
+// the complete density of plane z - 1. own: the column's own contributions
+// to planes z - 1, z, z + 1 (none for ring positions); inc: what the tile's
+// other nodes pushed into the column, per destination plane.
+__host__ __device__ __forceinline__ float2 roll_update(float2 roll[2], const float own[2][3], const float2 inc[3])
 {
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-        r[l] = roll[l] + own[l][0] + inc[0][l];
-        roll[l] = roll[2 + l] + own[l][1] + inc[1][l];
-        roll[2 + l] = own[l][2] + inc[2][l];
-    }
+    const float2 r = make_float2(roll[0].x + own[0][0] + inc[0].x, roll[0].y + own[1][0] + inc[0].y);
+    roll[0] = make_float2(roll[1].x + own[0][1] + inc[1].x, roll[1].y + own[1][1] + inc[1].y);
+    roll[1] = make_float2(own[0][2] + inc[2].x, own[1][2] + inc[2].y);
+    return r;
 }
+
+// Does tile (bx, by) meet the particle box grown by one node in x and y
+// (tile_near without its z test)?
+__host__ __device__ __forceinline__ bool tile_near_xy(int bx, int by, const int o[3], const KParams& P)
+{
+    const int B2 = P.B + 2;
+    return ranges_meet(bx * P.tx, min(P.tx, P.lx - bx * P.tx), o[0] - 1, B2, P.lx, P.wall[0]) &&
+           ranges_meet(by * P.ty, min(P.ty, P.ly - by * P.ty), o[1] - 1, B2, P.ly, P.wall[1]);
+}
+
+// The ring position a thread gathers for (threads below the tile's ring
+// length, when the position is a node of the lattice).
+struct RingDuty {
+    bool on;
+    int fx, fy, side, pos;
+    __device__ __forceinline__ RingDuty(int tid, int bx, int by, int w, int h, const KParams& P, const FusedGeom& G)
+    {
+        fx = fy = 0;
+        on = tid < G.ring && ring_pos(tid, w, h, P, fx, fy) && fp_node(bx, by, fx, fy, P);
+        side = ring_side(tid, P);
+        pos = xch_pos(fx, fy, P);
+    }
+};
 
 template <bool NOISE, bool TAU1>
 static __global__ void __launch_bounds__(kThreadsStep, FLBM_BULK_MINBLOCKS)
@@ -253,85 +320,95 @@ static __global__ void __launch_bounds__(kThreadsStep, FLBM_BULK_MINBLOCKS)
                          float* __restrict__ psi_next, float2* __restrict__ ring, float2* __restrict__ seam,
                          const DevState* __restrict__ st, KParams P, FusedGeom G)
 {
-    __shared__ float s_xch[2 * kXchDirs * kThreadsStep];
-    __shared__ float s_roll[4][kThreadsStep];  // per node column: rolling sums of roll_update
-    __shared__ float s_rollr[4][kRingMax];     // the same per ring position
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = tx + P.tx * ty;
-    const int bx = blockIdx.x, by = blockIdx.y, c = blockIdx.z;
-    const int tile = bx + P.gx * by;
-    const int w = tile_w(bx, P), h = tile_h(by, P);
-    const bool node = tx < w && ty < h;
-    const int x = bx * P.tx + tx, y = by * P.ty + ty;
-    const int z0 = c * G.K, z1 = min(z0 + G.K, P.lz);
-    int fxr = 0, fyr = 0;
-    const bool rduty = tid < G.ring && ring_pos(tid, w, h, P, fxr, fyr) && fp_node(bx, by, fxr, fyr, P);
-    int o[3] = {0, 0, 0};
+    extern __shared__ float2 s_fused[];
+    const int xsize = xch_size(P);
+    float2* s_xch = s_fused;                           // [16][xsize]
+    float2* s_roll = s_fused + kXchDirs * xsize;       // [2][256]: rolling sums of the tile's columns
+    float2* s_rollr = s_roll + 2 * kThreadsStep;       // [2][kRingMax]: the same for ring positions
+    const int tid = threadIdx.x + P.tx * threadIdx.y;
+    const float2 zero = make_float2(0.f, 0.f);
+    const int z0 = blockIdx.z * G.K, z1 = min(z0 + G.K, P.lz);
+    // Planes of this tile that belong to the near launch: [zn0, zn0 + nzn)
+    // (periodic along z), none without a particle or when the tile is not
+    // next to it in x and y.
+    int zn0 = 0, nzn = 0;
     if (P.has_particle) {
-        o[0] = st->box0[0];
-        o[1] = st->box0[1];
-        o[2] = st->box0[2];
-    }
-    auto reset = [&] {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) s_roll[k][tid] = 0.0f;
-        if (tid < kRingMax) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) s_rollr[k][tid] = 0.0f;
+        const int o[3] = {st->box0[0], st->box0[1], st->box0[2]};
+        if (tile_near_xy(blockIdx.x, blockIdx.y, o, P)) {
+            zn0 = o[2] - 1;
+            nzn = P.B + 2;
         }
+    }
+    for (int k = tid; k < kXchDirs * xsize; k += kThreadsStep) s_xch[k] = zero;
+    auto reset = [&] {
+        s_roll[tid] = s_roll[kThreadsStep + tid] = zero;
+        if (tid < kRingMax) s_rollr[tid] = s_rollr[kRingMax + tid] = zero;
     };
     reset();
+    __syncthreads();
     for (int z = z0; z < z1; ++z) {
         // Tiles next to the particle belong to the near launch: the densities
         // around them are recomputed after cover/uncover (part A of
         // k_psi_finish), so the partial sums just restart.
-        if (P.has_particle && tile_near(bx, by, z, o, P)) {
+        if (nzn && ranges_meet(z, 1, zn0, nzn, P.lz, P.wall[2])) {
             reset();
             continue;
         }
-        DensitySink sink(s_xch, tid);
+        const int w = tile_w(blockIdx.x, P), h = tile_h(blockIdx.y, P);
+        const bool node = (int)threadIdx.x < w && (int)threadIdx.y < h;
+        DensitySink sink(reinterpret_cast<float*>(s_xch), xch_pos(threadIdx.x, threadIdx.y, P), xsize);
         if (node) {
+            const int x = blockIdx.x * P.tx + threadIdx.x, y = blockIdx.y * P.ty + threadIdx.y;
             const uint32_t n = (uint32_t)x + (uint32_t)P.lx * ((uint32_t)y + (uint32_t)P.ly * (uint32_t)z);
             const GlobalInputs in(fin, psi, x, y, z, n, P);
             collide_core<NOISE, false, TAU1>(x, y, z, n, in, fout, st, P, 0u, nullptr, &sink);
         }
         __syncthreads();
+        const int tile = blockIdx.x + P.gx * blockIdx.y;
         if (node) {
-            float inc[3][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            gather_column(tx, ty, w, h, s_xch, P, inc);
-            float roll[4] = {s_roll[0][tid], s_roll[1][tid], s_roll[2][tid], s_roll[3][tid]};
-            float r[2];
-            roll_update(roll, sink.own, inc, r);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) s_roll[k][tid] = roll[k];
-            put_density(z - 1, tx, ty, true, -1, r[0], r[1], tile, bx, by, c, z0, z1, psi_next, ring, seam, P, G);
+            float2 inc[3] = {zero, zero, zero};
+            gather_column(sink.pos, s_xch, P, inc);
+            float2 roll[2] = {s_roll[tid], s_roll[kThreadsStep + tid]};
+            const float2 r = roll_update(roll, sink.own, inc);
+            s_roll[tid] = roll[0];
+            s_roll[kThreadsStep + tid] = roll[1];
+            put_density(z - 1, threadIdx.x, threadIdx.y, true, -1, r, tile, blockIdx.x, blockIdx.y, blockIdx.z, z0,
+                        z1, psi_next, ring, seam, P, G);
         }
-        if (rduty) {
-            float inc[3][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-            gather_column(fxr, fyr, w, h, s_xch, P, inc);
-            const float none[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-            float roll[4] = {s_rollr[0][tid], s_rollr[1][tid], s_rollr[2][tid], s_rollr[3][tid]};
-            float r[2];
-            roll_update(roll, none, inc, r);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) s_rollr[k][tid] = roll[k];
-            put_density(z - 1, fxr, fyr, false, tid, r[0], r[1], tile, bx, by, c, z0, z1, psi_next, ring, seam, P, G);
+        if (tid < G.ring) {
+            const RingDuty rd(tid, blockIdx.x, blockIdx.y, w, h, P, G);
+            if (rd.on) {
+                float2 inc[3] = {zero, zero, zero};
+                gather_ring(rd.side, rd.pos, s_xch, P, inc);
+                const float none[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+                float2 roll[2] = {s_rollr[tid], s_rollr[kRingMax + tid]};
+                const float2 r = roll_update(roll, none, inc);
+                s_rollr[tid] = roll[0];
+                s_rollr[kRingMax + tid] = roll[1];
+                put_density(z - 1, rd.fx, rd.fy, false, tid, r, tile, blockIdx.x, blockIdx.y, blockIdx.z, z0, z1,
+                            psi_next, ring, seam, P, G);
+            }
         }
-        __syncthreads();  // the next plane overwrites s_xch
+        __syncthreads();  // the next plane overwrites the exchange arrays
     }
     // The chunk's last plane still lacks what the plane above pushes down,
     // and the plane above the chunk has only this chunk's share.
-    if (node) {
-        put_density(z1 - 1, tx, ty, true, -1, s_roll[0][tid], s_roll[1][tid], tile, bx, by, c, z0, z1, psi_next, ring,
-                    seam, P, G);
-        put_density(z1, tx, ty, true, -1, s_roll[2][tid], s_roll[3][tid], tile, bx, by, c, z0, z1, psi_next, ring,
-                    seam, P, G);
+    const int tile = blockIdx.x + P.gx * blockIdx.y;
+    const int w = tile_w(blockIdx.x, P), h = tile_h(blockIdx.y, P);
+    if ((int)threadIdx.x < w && (int)threadIdx.y < h) {
+        put_density(z1 - 1, threadIdx.x, threadIdx.y, true, -1, s_roll[tid], tile, blockIdx.x, blockIdx.y, blockIdx.z,
+                    z0, z1, psi_next, ring, seam, P, G);
+        put_density(z1, threadIdx.x, threadIdx.y, true, -1, s_roll[kThreadsStep + tid], tile, blockIdx.x, blockIdx.y,
+                    blockIdx.z, z0, z1, psi_next, ring, seam, P, G);
     }
-    if (rduty) {
-        put_density(z1 - 1, fxr, fyr, false, tid, s_rollr[0][tid], s_rollr[1][tid], tile, bx, by, c, z0, z1, psi_next,
-                    ring, seam, P, G);
-        put_density(z1, fxr, fyr, false, tid, s_rollr[2][tid], s_rollr[3][tid], tile, bx, by, c, z0, z1, psi_next,
-                    ring, seam, P, G);
+    if (tid < G.ring) {
+        const RingDuty rd(tid, blockIdx.x, blockIdx.y, w, h, P, G);
+        if (rd.on) {
+            put_density(z1 - 1, rd.fx, rd.fy, false, tid, s_rollr[tid], tile, blockIdx.x, blockIdx.y, blockIdx.z, z0,
+                        z1, psi_next, ring, seam, P, G);
+            put_density(z1, rd.fx, rd.fy, false, tid, s_rollr[kRingMax + tid], tile, blockIdx.x, blockIdx.y,
+                        blockIdx.z, z0, z1, psi_next, ring, seam, P, G);
+        }
     }
 }
 
@@ -391,61 +468,78 @@ struct FinishItems {
     }
 };
 
-// Density of node (x, y, z), home tile (bx, by), chunk c, from its home
-// partial (psi_next) and the ring and seam partials of the blocks whose
-// footprint holds it: the 3 x 3 tiles around it, each with the ring of the
-// node's plane (other tiles only) and the seams of the chunks below and
-// above, in this fixed order.
-__host__ __device__ __forceinline__ void finish_node(int x, int y, int z, int bx, int by, int c,
+// The tiles around tile (bx, by) that part B reads: index, extent, and
+// whether it exists (not across a wall). Slot k = (dbx + 1) + 3 (dby + 1).
+struct TileRing {
+    int t[9], w[9], h[9];
+    bool ok[9];
+    __host__ __device__ __forceinline__ TileRing(int bx, int by, const KParams& P)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            int tbx = bx + k % 3 - 1, tby = by + k / 3 - 1;
+            ok[k] = true;
+            if (tbx < 0 || tbx >= P.gx) {
+                if (P.wall[0]) ok[k] = false;
+                tbx += tbx < 0 ? P.gx : -P.gx;
+            }
+            if (tby < 0 || tby >= P.gy) {
+                if (P.wall[1]) ok[k] = false;
+                tby += tby < 0 ? P.gy : -P.gy;
+            }
+            t[k] = ok[k] ? tbx + P.gx * tby : 0;
+            w[k] = ok[k] ? tile_w(tbx, P) : 0;
+            h[k] = ok[k] ? tile_h(tby, P) : 0;
+        }
+    }
+};
+
+// Density of node (fx, fy) of tile (bx, by) (ring R of its tiles), plane z,
+// chunk c, from its home partial (psi_next) and the partials of the blocks
+// whose footprint holds it: for each tile k of the 3 x 3 block around it (in
+// slot order) whose ring or footprint contains the node, the ring partial of
+// plane z (other tiles only) and the seams of the chunks below and above
+// when z is the chunk's first or last plane. A node on a tile edge sits on
+// the ring of one side tile, a corner node on the rings of three tiles.
+__host__ __device__ __forceinline__ void finish_node(int fx, int fy, int z, int bx, int by, int c, const TileRing& R,
                                                     float* __restrict__ psi_next, const float2* __restrict__ ring,
                                                     const float2* __restrict__ seam, const KParams& P,
                                                     const FusedGeom& G)
 {
+    const int w = R.w[4], h = R.h[4];
     const int z0 = c * G.K, z1 = min(z0 + G.K, P.lz);
     const bool lo = z == z0 && (z0 > 0 || !P.wall[2]);
     const bool hi = z == z1 - 1 && (z1 < P.lz || !P.wall[2]);
     const int cb = c == 0 ? G.nchunk - 1 : c - 1;
     const int ca = c == G.nchunk - 1 ? 0 : c + 1;
-    const long long q = pad_index(x, y, z, P);
+    const long long q = pad_index(bx * P.tx + fx, by * P.ty + fy, z, P);
     float a = psi_next[q], b = psi_next[P.padn + q];
-    for (int dby = -1; dby <= 1; ++dby) {
-        int tby = by + dby;
-        if (tby < 0 || tby >= P.gy) {
-            if (P.wall[1]) continue;
-            tby += tby < 0 ? P.gy : -P.gy;
-        }
-        for (int dbx = -1; dbx <= 1; ++dbx) {
-            int tbx = bx + dbx;
-            if (tbx < 0 || tbx >= P.gx) {
-                if (P.wall[0]) continue;
-                tbx += tbx < 0 ? P.gx : -P.gx;
-            }
-            const int w = tile_w(tbx, P), h = tile_h(tby, P);
-            int fx = x - tbx * P.tx, fy = y - tby * P.ty;
-            if (!P.wall[0]) {
-                if (fx < -1) fx += P.lx;
-                else if (fx > w) fx -= P.lx;
-            }
-            if (!P.wall[1]) {
-                if (fy < -1) fy += P.ly;
-                else if (fy > h) fy -= P.ly;
-            }
-            if (fx < -1 || fx > w || fy < -1 || fy > h) continue;
-            const int t = tbx + P.gx * tby;
-            const int slot = ring_slot(fx, fy, w, h, P);
-            if (slot >= 0) {
-                const float2 v = ring[ring_index(t, z, slot, P, G)];
+    const int dxs[3] = {fx == 0 ? -1 : 0, 0, fx == w - 1 ? 1 : 0};  // candidate side columns
+    const int dys[3] = {fy == 0 ? -1 : 0, 0, fy == h - 1 ? 1 : 0};
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+            const int dbx = kx - 1, dby = ky - 1;
+            if ((dbx != 0 && dxs[kx] != dbx) || (dby != 0 && dys[ky] != dby)) continue;
+            const int k = kx + 3 * ky;
+            if (!R.ok[k]) continue;
+            // Position of the node relative to tile k.
+            const int fxk = dbx < 0 ? R.w[k] : (dbx > 0 ? -1 : fx);
+            const int fyk = dby < 0 ? R.h[k] : (dby > 0 ? -1 : fy);
+            if (k != 4) {
+                const float2 v = ring[ring_index(R.t[k], z, ring_slot(fxk, fyk, R.w[k], R.h[k], P), P, G)];
                 a += v.x;
                 b += v.y;
             }
-            const int pos = fp_index(fx, fy, P);
+            const int p = fp_index(fxk, fyk, P);
             if (lo) {
-                const float2 v = seam[seam_index(t, cb, 1, pos, G)];
+                const float2 v = seam[seam_index(R.t[k], cb, 1, p, G)];
                 a += v.x;
                 b += v.y;
             }
             if (hi) {
-                const float2 v = seam[seam_index(t, ca, 0, pos, G)];
+                const float2 v = seam[seam_index(R.t[k], ca, 0, p, G)];
                 a += v.x;
                 b += v.y;
             }
@@ -453,6 +547,35 @@ __host__ __device__ __forceinline__ void finish_node(int x, int y, int z, int bx
     }
     psi_next[q] = a;
     psi_next[P.padn + q] = b;
+}
+
+// Can the dilated near-particle region meet tile (bx, by) over planes
+// [z0, z1)? Only then do part B's nodes of that block need the per-node test.
+__host__ __device__ __forceinline__ bool block_meets_near(int bx, int by, int z0, int z1, const int o[3],
+                                                          const KParams& P)
+{
+    bool nx = false, ny = false;
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+        int b = bx + d;
+        if (b < 0 || b >= P.gx) {
+            if (P.wall[0]) continue;
+            b += b < 0 ? P.gx : -P.gx;
+        }
+        nx = nx || ranges_meet(b * P.tx, min(P.tx, P.lx - b * P.tx), o[0] - 1, P.B + 2, P.lx, P.wall[0]);
+    }
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+        int b = by + d;
+        if (b < 0 || b >= P.gy) {
+            if (P.wall[1]) continue;
+            b += b < 0 ? P.gy : -P.gy;
+        }
+        ny = ny || ranges_meet(b * P.ty, min(P.ty, P.ly - b * P.ty), o[1] - 1, P.B + 2, P.ly, P.wall[1]);
+    }
+    const int zl = min(z1 - z0 + 2, P.lz);
+    const int zs = (z0 == 0 && !P.wall[2]) ? P.lz - 1 : max(z0 - 1, 0);
+    return nx && ny && ranges_meet(zs, zl, o[2] - 1, P.B + 2, P.lz, P.wall[2]);
 }
 
 // Completes psi_next after the fused collide and the particle kernels.
@@ -480,16 +603,16 @@ static __global__ void __launch_bounds__(kThreadsStep) k_psi_finish(const float*
         const int ntile = P.gx * P.gy;
         const int tile = blockIdx.x % ntile, c = blockIdx.x / ntile;
         const int bx = tile % P.gx, by = tile / P.gx;
-        const int w = tile_w(bx, P), h = tile_h(by, P);
+        const TileRing R(bx, by, P);
         const int z0 = c * G.K, z1 = min(z0 + G.K, P.lz);
-        const FinishItems items(z0, z1, w, h, P);
+        const bool check = P.has_particle && block_meets_near(bx, by, z0, z1, o, P);
+        const FinishItems items(z0, z1, R.w[4], R.h[4], P);
         const long long total = items.count();
         for (long long it = threadIdx.x; it < total; it += blockDim.x) {
             int z, fx, fy;
             items.item(it, z, fx, fy);
-            const int x = bx * P.tx + fx, y = by * P.ty + fy;
-            if (P.has_particle && near_dilated(x, y, z, o, P)) continue;
-            finish_node(x, y, z, bx, by, c, psi_next, ring, seam, P, G);
+            if (check && near_dilated(bx * P.tx + fx, by * P.ty + fy, z, o, P)) continue;
+            finish_node(fx, fy, z, bx, by, c, R, psi_next, ring, seam, P, G);
         }
         return;
     }

@@ -1,7 +1,7 @@
 // Host check (no GPU) of the bookkeeping of the fused collide's densities,
 // built from the header functions the kernels call (DensitySink, gather_column,
-// roll_update, put_density, finish_node, edge_count/edge_node, ring_pos,
-// near_dilated, tile_near, near_box_axis).
+// gather_ring, roll_update, put_density, TileRing, finish_node, FinishItems,
+// ring_pos, tile_near_xy, block_meets_near, near_dilated, near_box_axis).
 //
 // For random lattices (sizes, walls, ragged tiles), planes per block and
 // particle boxes, every node pushes random values for its 19 directions, with
@@ -119,25 +119,34 @@ int main(int argc, char** argv)
         std::vector<float> psi((size_t)2 * P.padn, NAN);
         std::vector<float2> ring((size_t)P.gx * P.gy * P.lz * G.ring, make_float2(NAN, NAN));
         std::vector<float2> seam((size_t)P.gx * P.gy * G.nchunk * 2 * G.fp, make_float2(NAN, NAN));
-        std::vector<float> xch(2 * kXchDirs * kThreadsStep);
+        std::vector<float2> xch((size_t)kXchDirs * xch_size(P));
         for (int ch = 0; ch < G.nchunk; ++ch)
             for (int by = 0; by < P.gy; ++by)
                 for (int bx = 0; bx < P.gx; ++bx) {
                     const int tile = bx + P.gx * by;
                     const int w = tile_w(bx, P), h = tile_h(by, P);
                     const int z0 = ch * G.K, z1 = std::min(z0 + G.K, P.lz);
-                    std::vector<float> roll((size_t)4 * kThreadsStep, 0.0f), rollr((size_t)4 * kRingMax, 0.0f);
+                    const float2 zero = make_float2(0.0f, 0.0f);
+                    std::vector<float2> roll((size_t)2 * kThreadsStep, zero), rollr((size_t)2 * kRingMax, zero);
+                    std::fill(xch.begin(), xch.end(), zero);
                     std::vector<DensitySink> sinks;
-                    for (int tid = 0; tid < kThreadsStep; ++tid) sinks.emplace_back(xch.data(), tid);
+                    for (int tid = 0; tid < kThreadsStep; ++tid)
+                        sinks.emplace_back(reinterpret_cast<float*>(xch.data()), 0, xch_size(P));
+                    const bool nxy = P.has_particle && tile_near_xy(bx, by, o, P);
                     for (int z = z0; z < z1; ++z) {
+                        if (P.has_particle && tile_near(bx, by, z, o, P) != (nxy && ranges_meet(z, 1, o[2] - 1, P.B + 2, P.lz, P.wall[2]))) {
+                            std::printf("hoisted near test differs\n");
+                            return 1;
+                        }
                         if (P.has_particle && tile_near(bx, by, z, o, P)) {
-                            std::fill(roll.begin(), roll.end(), 0.0f);
-                            std::fill(rollr.begin(), rollr.end(), 0.0f);
+                            std::fill(roll.begin(), roll.end(), zero);
+                            std::fill(rollr.begin(), rollr.end(), zero);
                             continue;
                         }
                         for (int tid = 0; tid < kThreadsStep; ++tid) {
-                            sinks[tid] = DensitySink(xch.data(), tid);
                             const int tx = tid % P.tx, ty = tid / P.tx;
+                            sinks[tid] = DensitySink(reinterpret_cast<float*>(xch.data()), xch_pos(tx, ty, P),
+                                                     xch_size(P));
                             if (tx >= w || ty >= h) continue;
                             const int x = bx * P.tx + tx, y = by * P.ty + ty;
                             const long long n = x + (long long)P.lx * (y + (long long)P.ly * z);
@@ -148,27 +157,25 @@ int main(int argc, char** argv)
                         for (int tid = 0; tid < kThreadsStep; ++tid) {
                             const int tx = tid % P.tx, ty = tid / P.tx;
                             if (tx < w && ty < h) {
-                                float inc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-                                gather_column(tx, ty, w, h, xch.data(), P, inc);
-                                float rl[4] = {roll[tid], roll[kThreadsStep + tid], roll[2 * kThreadsStep + tid],
-                                               roll[3 * kThreadsStep + tid]};
-                                float r[2];
-                                roll_update(rl, sinks[tid].own, inc, r);
-                                for (int k = 0; k < 4; ++k) roll[(size_t)k * kThreadsStep + tid] = rl[k];
-                                put_density(z - 1, tx, ty, true, -1, r[0], r[1], tile, bx, by, ch, z0, z1, psi.data(),
+                                float2 inc[3] = {zero, zero, zero};
+                                gather_column(xch_pos(tx, ty, P), xch.data(), P, inc);
+                                float2 rl[2] = {roll[tid], roll[kThreadsStep + tid]};
+                                const float2 r = roll_update(rl, sinks[tid].own, inc);
+                                roll[tid] = rl[0];
+                                roll[kThreadsStep + tid] = rl[1];
+                                put_density(z - 1, tx, ty, true, -1, r, tile, bx, by, ch, z0, z1, psi.data(),
                                             ring.data(), seam.data(), P, G);
                             }
                             int fx, fy;
                             if (tid < G.ring && ring_pos(tid, w, h, P, fx, fy) && fp_node(bx, by, fx, fy, P)) {
-                                float inc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-                                gather_column(fx, fy, w, h, xch.data(), P, inc);
+                                float2 inc[3] = {zero, zero, zero};
+                                gather_ring(ring_side(tid, P), xch_pos(fx, fy, P), xch.data(), P, inc);
                                 const float none[2][3] = {{0, 0, 0}, {0, 0, 0}};
-                                float rl[4] = {rollr[tid], rollr[kRingMax + tid], rollr[2 * kRingMax + tid],
-                                               rollr[3 * kRingMax + tid]};
-                                float r[2];
-                                roll_update(rl, none, inc, r);
-                                for (int k = 0; k < 4; ++k) rollr[(size_t)k * kRingMax + tid] = rl[k];
-                                put_density(z - 1, fx, fy, false, tid, r[0], r[1], tile, bx, by, ch, z0, z1, psi.data(),
+                                float2 rl[2] = {rollr[tid], rollr[kRingMax + tid]};
+                                const float2 r = roll_update(rl, none, inc);
+                                rollr[tid] = rl[0];
+                                rollr[kRingMax + tid] = rl[1];
+                                put_density(z - 1, fx, fy, false, tid, r, tile, bx, by, ch, z0, z1, psi.data(),
                                             ring.data(), seam.data(), P, G);
                             }
                         }
@@ -176,18 +183,17 @@ int main(int argc, char** argv)
                     for (int tid = 0; tid < kThreadsStep; ++tid) {
                         const int tx = tid % P.tx, ty = tid / P.tx;
                         if (tx < w && ty < h) {
-                            put_density(z1 - 1, tx, ty, true, -1, roll[tid], roll[kThreadsStep + tid], tile, bx, by, ch,
-                                        z0, z1, psi.data(), ring.data(), seam.data(), P, G);
-                            put_density(z1, tx, ty, true, -1, roll[2 * kThreadsStep + tid],
-                                        roll[3 * kThreadsStep + tid], tile, bx, by, ch, z0, z1, psi.data(), ring.data(),
-                                        seam.data(), P, G);
+                            put_density(z1 - 1, tx, ty, true, -1, roll[tid], tile, bx, by, ch, z0, z1, psi.data(),
+                                        ring.data(), seam.data(), P, G);
+                            put_density(z1, tx, ty, true, -1, roll[kThreadsStep + tid], tile, bx, by, ch, z0, z1,
+                                        psi.data(), ring.data(), seam.data(), P, G);
                         }
                         int fx, fy;
                         if (tid < G.ring && ring_pos(tid, w, h, P, fx, fy) && fp_node(bx, by, fx, fy, P)) {
-                            put_density(z1 - 1, fx, fy, false, tid, rollr[tid], rollr[kRingMax + tid], tile, bx, by,
-                                        ch, z0, z1, psi.data(), ring.data(), seam.data(), P, G);
-                            put_density(z1, fx, fy, false, tid, rollr[2 * kRingMax + tid], rollr[3 * kRingMax + tid],
-                                        tile, bx, by, ch, z0, z1, psi.data(), ring.data(), seam.data(), P, G);
+                            put_density(z1 - 1, fx, fy, false, tid, rollr[tid], tile, bx, by, ch, z0, z1, psi.data(),
+                                        ring.data(), seam.data(), P, G);
+                            put_density(z1, fx, fy, false, tid, rollr[kRingMax + tid], tile, bx, by, ch, z0, z1,
+                                        psi.data(), ring.data(), seam.data(), P, G);
                         }
                     }
                 }
@@ -199,6 +205,8 @@ int main(int argc, char** argv)
             const int bx = tile % P.gx, by = tile / P.gx;
             const int w = tile_w(bx, P), h = tile_h(by, P);
             const int z0 = ch * G.K, z1 = std::min(z0 + G.K, P.lz);
+            const TileRing TR(bx, by, P);
+            const bool check = P.has_particle && block_meets_near(bx, by, z0, z1, o, P);
             const FinishItems items(z0, z1, w, h, P);
             const long long total = items.count();
             for (long long it = 0; it < total; ++it) {
@@ -206,8 +214,13 @@ int main(int argc, char** argv)
                 items.item(it, z, fx, fy);
                 const int x = bx * P.tx + fx, y = by * P.ty + fy;
                 visits[x + (long long)P.lx * (y + (long long)P.ly * z)] += 1;
-                if (P.has_particle && near_dilated(x, y, z, o, P)) continue;
-                finish_node(x, y, z, bx, by, ch, psi.data(), ring.data(), seam.data(), P, G);
+                const bool nd = P.has_particle && near_dilated(x, y, z, o, P);
+                if (nd && !check) {
+                    std::printf("block_meets_near missed a near node\n");
+                    return 1;
+                }
+                if (nd) continue;
+                finish_node(fx, fy, z, bx, by, ch, TR, psi.data(), ring.data(), seam.data(), P, G);
             }
         }
         // Part A's box must hold the dilated near region.

@@ -126,12 +126,15 @@ def test_fused_and_two_pass_steps_agree(flbm, name, p, K, part):
 
 
 def test_density_mode_choice(flbm):
-    """Fused by default where the lattice allows it; lattices with tiles
-    narrower than 8 nodes or fewer than 3 tiles along a periodic axis refuse
-    it; the TMA-staged collide runs two-pass."""
+    """Two-pass by default; fused where the lattice allows it and it is asked
+    for; lattices with tiles narrower than 8 nodes or fewer than 3 tiles
+    along a periodic axis refuse it; the TMA-staged collide runs two-pass."""
     s = flbm.Sim(W.channel_small())
+    assert s.density_mode() == (0, 0)
+    s.set_density_mode(1)
     assert s.density_mode()[0] == 1
-    s.use_tma(False)
+    s.set_density_mode(1, 5)
+    assert s.density_mode() == (1, 5)
     narrow = flbm.Sim(W.params(lx=4, ly=8, lz=8, wall=(1, 1, 0)))
     assert narrow.density_mode() == (0, 0)
     with pytest.raises(flbm.FLBMError, match="UNSUPPORTED"):
@@ -140,6 +143,7 @@ def test_density_mode_choice(flbm):
     with pytest.raises(flbm.FLBMError, match="UNSUPPORTED"):
         few.set_density_mode(1)
     t = flbm.Sim(W.params(lx=64, ly=32, lz=8))
+    t.set_density_mode(1)
     t.use_tma(True)
     assert t.density_mode() == (0, 0)
     t.use_tma(False)
@@ -149,8 +153,8 @@ def test_density_mode_choice(flbm):
 
 
 def test_benchmarked_channel_carries_the_densities_of_its_state(flbm):
-    """The 128x128x512 fluctuating channel with the R = 12 sphere, in the
-    benchmark's launch configuration (default planes per block): after 6
+    """The 128x128x512 fluctuating channel with the R = 12 sphere in fused
+    mode with the default planes per block: after 6
     fused steps the densities the step carries equal, on every fluid node,
     a fresh density pass over the same populations (a second handle given
     those populations) within 1e-6 relative. The two sum the same values in
@@ -160,6 +164,7 @@ def test_benchmarked_channel_carries_the_densities_of_its_state(flbm):
 
     p = W.channel_large()
     sim = flbm.Sim(p, stream=torch.cuda.Stream())
+    sim.set_density_mode(1)
     assert sim.density_mode()[0] == 1
     for steps, graphs in ((6, False), (8, True)):
         sim.use_graphs(graphs)
