@@ -83,7 +83,9 @@ def settling_sweep(plist: list[dict], burn: int, samples: int, every: int = 10, 
     out = []
     for r, p in enumerate(plist):
         ufl = obs[r]["momentum"][2] / float(np.sum(obs[r]["mass"]))
-        out.append(settling_row(p, rec[:, r], ufl, parts[r]["mp"], parts[r]["Fp"], intervals))
+        row = settling_row(p, rec[:, r], ufl, parts[r]["mp"], parts[r]["Fp"], intervals)
+        row["nonfinite"] = int(obs[r]["nonfinite"])
+        out.append(row)
     return out
 
 
