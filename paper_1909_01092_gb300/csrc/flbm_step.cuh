@@ -120,6 +120,66 @@ struct GlobalInputs {
     __device__ __forceinline__ float psb(int i) const { return __ldg(pA + padn + off(i)); }
 };
 
+// Push targets of the populations of node n = (x, y, z). Population (l, i)
+// goes to the same direction's slot of node x + c_i (periodic axes wrap),
+// unless c_i crosses a wall: then halfway bounce-back sends it to slot
+// (l, opp(i)) of the node itself. PushFrame holds the per-node part: the
+// offsets one step up and down each axis (with wrap) and which of those
+// steps cross a wall.
+struct PushFrame {
+    int offp[3], offm[3];
+    uint32_t wallp = 0, wallm = 0;
+    __host__ __device__ __forceinline__ PushFrame(int x, int y, int z, const KParams& P)
+    {
+        const int L[3] = {P.lx, P.ly, P.lz};
+        const int crd[3] = {x, y, z};
+        const int stride[3] = {1, P.lx, P.lx * P.ly};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            offp[a] = stride[a];
+            offm[a] = -stride[a];
+            if (crd[a] + 1 >= L[a]) {
+                if (P.wall[a]) wallp |= 1u << a;
+                else offp[a] = stride[a] * (1 - L[a]);
+            }
+            if (crd[a] - 1 < 0) {
+                if (P.wall[a]) wallm |= 1u << a;
+                else offm[a] = stride[a] * (L[a] - 1);
+            }
+        }
+    }
+    // Target of (l, i) and whether a wall bounced it.
+    __host__ __device__ __forceinline__ uint32_t target(uint32_t n, int l, int i, const KParams& P, bool& wall) const
+    {
+        const int cx = cxv(i), cy = cyv(i), cz = czv(i);
+        const uint32_t need_p = (cx > 0 ? 1u : 0u) | (cy > 0 ? 2u : 0u) | (cz > 0 ? 4u : 0u);
+        const uint32_t need_m = (cx < 0 ? 1u : 0u) | (cy < 0 ? 2u : 0u) | (cz < 0 ? 4u : 0u);
+        wall = ((wallp & need_p) | (wallm & need_m)) != 0u;
+        if (wall) return n + P.dirN[19 * l + oppv(i)];
+        int off = 0;
+        if (cx) off += cx > 0 ? offp[0] : offm[0];
+        if (cy) off += cy > 0 ? offp[1] : offm[1];
+        if (cz) off += cz > 0 ? offp[2] : offm[2];
+        return n + (uint32_t)off + P.dirN[19 * l + i];
+    }
+};
+
+// The same targets for a node whose neighbours along y and z are all inside
+// the lattice (1 <= y <= ly - 2, 1 <= z <= lz - 2): the precomputed offset
+// n + pushoff, with only the x edge to handle (x = 0 or lx - 1: bounce-back
+// at an x wall, wrap on a periodic x).
+__host__ __device__ __forceinline__ uint32_t push_target_yz_inside(uint32_t n, int x, int l, int i, const KParams& P,
+                                                                  bool& wall)
+{
+    const int cx = cxv(i);
+    const bool edge = (cx > 0 && x == P.lx - 1) || (cx < 0 && x == 0);
+    wall = edge && P.wall[0];
+    if (wall) return n + P.dirN[19 * l + oppv(i)];
+    uint32_t t = n + P.pushoff[19 * l + i];
+    if (edge) t += cx > 0 ? (uint32_t)(-P.lx) : (uint32_t)P.lx;
+    return t;
+}
+
 // Receiver of the pushed populations for callers that also want the next
 // step's densities (the fused bulk collide); put(l, i, v, bounced) sees every
 // population v = f*_li the node pushes outside the particle, bounced = true
@@ -269,25 +329,10 @@ __device__ __forceinline__ void collide_core(int x, int y, int z, uint32_t n, co
         }
     }
 
-    // Destination offsets along each axis (periodic wrap), and wall flags.
-    const int L[3] = {P.lx, P.ly, P.lz};
-    const int crd[3] = {x, y, z};
-    const int stride[3] = {1, P.lx, P.lx * P.ly};
-    int offp[3], offm[3];
-    uint32_t wallp = 0, wallm = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        offp[a] = stride[a];
-        offm[a] = -stride[a];
-        if (crd[a] + 1 >= L[a]) {
-            if (P.wall[a]) wallp |= 1u << a;
-            else offp[a] = stride[a] * (1 - L[a]);
-        }
-        if (crd[a] - 1 < 0) {
-            if (P.wall[a]) wallm |= 1u << a;
-            else offm[a] = stride[a] * (L[a] - 1);
-        }
-    }
+    // Push targets: away from the y and z boundaries, the precomputed
+    // offsets (the common case); elsewhere the general wall and wrap logic.
+    const bool yz_inside = !PARTICLE && y >= 1 && y + 2 <= P.ly && z >= 1 && z + 2 <= P.lz;
+    const PushFrame frame(x, y, z, P);
 
     // Back-transform and push each component (Eq. (lbe) streaming; halfway
     // bounce-back at walls; moving link rule at the particle).
@@ -296,15 +341,22 @@ __device__ __forceinline__ void collide_core(int x, int y, int z, uint32_t n, co
         float fo[19];
         from_modes(l == 0 ? ma : mb, fo);
         const float rl = l == 0 ? rhoA : rhoB;
+        if (yz_inside) {
+#pragma unroll
+            for (int i = 0; i < 19; ++i) {
+                bool wall;
+                const uint32_t idx = push_target_yz_inside(n, x, l, i, P, wall);
+                fout[idx] = fo[i];
+                if constexpr (Sink::active) sink->put(l, i, fo[i], wall);
+            }
+            continue;
+        }
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             const int cx = cxv(i), cy = cyv(i), cz = czv(i);
-            const uint32_t need_p = (cx > 0 ? 1u : 0u) | (cy > 0 ? 2u : 0u) | (cz > 0 ? 4u : 0u);
-            const uint32_t need_m = (cx < 0 ? 1u : 0u) | (cy < 0 ? 2u : 0u) | (cz < 0 ? 4u : 0u);
-            const bool wall = ((wallp & need_p) | (wallm & need_m)) != 0u;
-            const uint32_t back_idx = n + P.dirN[19 * l + oppv(i)];
             if (PARTICLE && (solid_nb >> i & 1u)) {
                 // f_{-i}(x, t+1) = f*_i(x) - 6 w_i rho_l (u_b . c_i), u_b at the link midpoint.
+                const uint32_t back_idx = n + P.dirN[19 * l + oppv(i)];
                 const float r[3] = {rnf[0] + 0.5f * cx, rnf[1] + 0.5f * cy, rnf[2] + 0.5f * cz};
                 const float* V = st->Vf;
                 const float* Om = st->Omf;
@@ -318,12 +370,9 @@ __device__ __forceinline__ void collide_core(int x, int y, int z, uint32_t n, co
                 lk.led[l] += corr;
                 continue;
             }
-            int off = 0;
-            if (cx) off += cx > 0 ? offp[0] : offm[0];
-            if (cy) off += cy > 0 ? offp[1] : offm[1];
-            if (cz) off += cz > 0 ? offp[2] : offm[2];
-            const uint32_t push_idx = n + (uint32_t)off + P.dirN[19 * l + i];
-            fout[wall ? back_idx : push_idx] = fo[i];
+            bool wall;
+            const uint32_t idx = frame.target(n, l, i, P, wall);
+            fout[idx] = fo[i];
             if constexpr (Sink::active) sink->put(l, i, fo[i], wall);
         }
     }
