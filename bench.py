@@ -38,13 +38,13 @@ STEP_BYTES_PER_NODE = 2 * 19 * 4 * 2
 COLLIDE_BYTES_PER_NODE = STEP_BYTES_PER_NODE + 2 * 4
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes of the collide class (bulk + near launches) per step of the
-# 128x128x512 channel, from an ncu capture of the same kernels at 128x128x128
-# scaled by bulk nodes (profiles/k_collide_bulk_channel_128x128x128.md):
-# 289.6 B per bulk node x 8,331,264 bulk nodes + 9.9 MB for the near tiles.
-COLLIDE_TRAFFIC_BYTES = (329398784 + 261222912) / 2039808 * 8331264 + 9.9e6
-# Thread instructions per node of the noisy bulk collide kernel (same capture:
-# 107.6 M warp instructions over 2,039,808 nodes).
-COLLIDE_INST_PER_NODE = 107604480 * 32 / 2039808
+# 128x128x512 channel, from an ncu capture of the bulk kernel on the
+# 128x128x32 slab of the same channel, scaled by bulk nodes: B per bulk node
+# x 8,331,264 bulk nodes + 9.9 MB for the near tiles.
+COLLIDE_TRAFFIC_PER_BULK_NODE = 289.6
+COLLIDE_TRAFFIC_BYTES = COLLIDE_TRAFFIC_PER_BULK_NODE * 8331264 + 9.9e6
+# Thread instructions per node of the noisy bulk collide kernel (same capture).
+COLLIDE_INST_PER_NODE = 1688.0
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 
@@ -246,6 +246,32 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def fused_bench(binding, W, steps: int = 50) -> dict:
+    """The same channel with the densities summed by the collide-stream
+    (flbm_set_density_mode 1) instead of the density pass: milliseconds per
+    step and per kernel class, for comparison with the default two-pass
+    step."""
+    import torch
+
+    p = W.channel_large()
+    sim = binding.Sim(p, stream=torch.cuda.Stream())
+    sim.set_density_mode(1)
+    sim.step(5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(sim.stream)
+    kms = sim.step_timed(steps)
+    e1.record(sim.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    mode = sim.density_mode()
+    sim.close()
+    n = p["lx"] * p["ly"] * p["lz"]
+    return {"workload": WORKLOAD, "density_mode": mode[0], "planes_per_block": mode[1], "steps": steps,
+            "ms_per_step": ms, "mlups": n / (ms * 1e-3) / 1e6,
+            "kernel_ms_per_step": {k: v / steps for k, v in kms.items()}}
+
+
 def ensemble_bench(binding, W, steps: int = 100) -> dict:
     """The 128-replica ensemble (uneven channels, radii and kT): tuned
     batched launches replayed as CUDA graphs, against the same replicas
@@ -426,9 +452,10 @@ def run_ours(args):
         cpu = cpu_baseline()
         cpu["configs"] = oracle_configs()
     nfluid = sim.particle()["nfluid"]
-    ens = adj = small = None
+    ens = adj = small = fused = None
     if rank == 0 and world == 1 and not args.no_ensemble:
         sim.close()
+        fused = fused_bench(binding, W)
         ens = ensemble_bench(binding, W)
         adj = adjoint_bench(binding, W)
         small = small_bench(binding, W)
@@ -441,7 +468,7 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (2.55 GB of populations), no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches,
                 "fluid_only_mlups": aggregate_mlups(nfluid, args.steps, world, ms_max),
-                "ensemble": ens, "adjoint": adj, "small_configs": small}
+                "fused_densities": fused, "ensemble": ens, "adjoint": adj, "small_configs": small}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:

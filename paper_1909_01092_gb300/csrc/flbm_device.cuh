@@ -198,7 +198,6 @@ struct KParams {
     int ncx, ncy, ncz;     // candidate tiles per axis around the particle box
     int tau1;              // every relaxation time equals 1
     uint32_t dirN[38];     // (19 l + i) * N: offset of population (l, i) in one copy
-    uint32_t pushoff[38];  // dirN + c_i . (1, lx, lx ly): offset of the push target of (l, i) when no wall or wrap intervenes
     int has_particle;
     int B;                 // side of the particle box
     double R;              // sphere radius

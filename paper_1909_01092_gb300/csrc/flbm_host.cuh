@@ -111,11 +111,7 @@ inline void make_kparams(const flbm_params& p, int tile_policy, KParams& k)
     k.ncy = std::min(k.gy, (k.B + 2 + k.ty - 1) / k.ty + 2);
     k.ncz = std::min(p.lz, k.B + 2);
     k.tau1 = (p.tau_s == 1.0 && p.tau_d == 1.0 && p.tau_g == 1.0) ? 1 : 0;
-    for (int q = 0; q < 38; ++q) {
-        const int i = q % 19;
-        k.dirN[q] = (uint32_t)((long long)q * k.N);
-        k.pushoff[q] = k.dirN[q] + (uint32_t)(cxv(i) + (long long)p.lx * cyv(i) + (long long)p.lx * p.ly * czv(i));
-    }
+    for (int q = 0; q < 38; ++q) k.dirN[q] = (uint32_t)((long long)q * k.N);
 }
 
 

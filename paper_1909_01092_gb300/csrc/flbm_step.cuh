@@ -148,37 +148,23 @@ struct PushFrame {
             }
         }
     }
-    // Target of (l, i) and whether a wall bounced it.
+    // Target of (l, i) and whether a wall bounced it: both candidate
+    // indices, then a select (no branch).
     __host__ __device__ __forceinline__ uint32_t target(uint32_t n, int l, int i, const KParams& P, bool& wall) const
     {
         const int cx = cxv(i), cy = cyv(i), cz = czv(i);
         const uint32_t need_p = (cx > 0 ? 1u : 0u) | (cy > 0 ? 2u : 0u) | (cz > 0 ? 4u : 0u);
         const uint32_t need_m = (cx < 0 ? 1u : 0u) | (cy < 0 ? 2u : 0u) | (cz < 0 ? 4u : 0u);
         wall = ((wallp & need_p) | (wallm & need_m)) != 0u;
-        if (wall) return n + P.dirN[19 * l + oppv(i)];
+        const uint32_t back_idx = n + P.dirN[19 * l + oppv(i)];
         int off = 0;
         if (cx) off += cx > 0 ? offp[0] : offm[0];
         if (cy) off += cy > 0 ? offp[1] : offm[1];
         if (cz) off += cz > 0 ? offp[2] : offm[2];
-        return n + (uint32_t)off + P.dirN[19 * l + i];
+        const uint32_t push_idx = n + (uint32_t)off + P.dirN[19 * l + i];
+        return wall ? back_idx : push_idx;
     }
 };
-
-// The same targets for a node whose neighbours along y and z are all inside
-// the lattice (1 <= y <= ly - 2, 1 <= z <= lz - 2): the precomputed offset
-// n + pushoff, with only the x edge to handle (x = 0 or lx - 1: bounce-back
-// at an x wall, wrap on a periodic x).
-__host__ __device__ __forceinline__ uint32_t push_target_yz_inside(uint32_t n, int x, int l, int i, const KParams& P,
-                                                                  bool& wall)
-{
-    const int cx = cxv(i);
-    const bool edge = (cx > 0 && x == P.lx - 1) || (cx < 0 && x == 0);
-    wall = edge && P.wall[0];
-    if (wall) return n + P.dirN[19 * l + oppv(i)];
-    uint32_t t = n + P.pushoff[19 * l + i];
-    if (edge) t += cx > 0 ? (uint32_t)(-P.lx) : (uint32_t)P.lx;
-    return t;
-}
 
 // Receiver of the pushed populations for callers that also want the next
 // step's densities (the fused bulk collide); put(l, i, v, bounced) sees every
@@ -329,9 +315,7 @@ __device__ __forceinline__ void collide_core(int x, int y, int z, uint32_t n, co
         }
     }
 
-    // Push targets: away from the y and z boundaries, the precomputed
-    // offsets (the common case); elsewhere the general wall and wrap logic.
-    const bool yz_inside = !PARTICLE && y >= 1 && y + 2 <= P.ly && z >= 1 && z + 2 <= P.lz;
+    // Per-node offsets and wall flags of the push targets.
     const PushFrame frame(x, y, z, P);
 
     // Back-transform and push each component (Eq. (lbe) streaming; halfway
@@ -341,16 +325,6 @@ __device__ __forceinline__ void collide_core(int x, int y, int z, uint32_t n, co
         float fo[19];
         from_modes(l == 0 ? ma : mb, fo);
         const float rl = l == 0 ? rhoA : rhoB;
-        if (yz_inside) {
-#pragma unroll
-            for (int i = 0; i < 19; ++i) {
-                bool wall;
-                const uint32_t idx = push_target_yz_inside(n, x, l, i, P, wall);
-                fout[idx] = fo[i];
-                if constexpr (Sink::active) sink->put(l, i, fo[i], wall);
-            }
-            continue;
-        }
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             const int cx = cxv(i), cy = cyv(i), cz = czv(i);

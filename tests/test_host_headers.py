@@ -25,11 +25,10 @@ brute-force scan of the lattice:
   particle boxes gives every node outside the near-particle region the direct
   sum of the 19 values pushed into it, each such node completed once, and the
   near-particle region lies in the box its recompute walks;
-* tests/host_push.cu (PushFrame::target, push_target_yz_inside): the push
-  target of every population of every node, by the general wall-and-wrap
-  rule and by the fast rule for nodes inside y and z, equals the target
-  taken from the definition (x + c_i with wrap, or the node itself in the
-  opposite direction across a wall);
+* tests/host_push.cu (PushFrame::target): the push target of every
+  population of every node equals the target taken from the definition
+  (x + c_i with wrap, or the node itself in the opposite direction across a
+  wall);
 * tests/host_restore.cu (check_restored_state): a particle record read from
   a checkpoint passes when it is one the library wrote, and is refused when
   its mask index, centre, velocities, box origin, fluid count, step or mass
@@ -93,5 +92,5 @@ def test_fused_density_bookkeeping_gives_the_direct_sums(tmp_path):
 def test_push_targets_follow_streaming_and_bounce_back(tmp_path):
     out = _build_and_run(tmp_path, "host_push", "")
     words = out.split()
-    configs, fast, failed = (int(words[words.index(w) + 1]) for w in ("configurations", "fast", "failed"))
-    assert failed == 0 and configs > 250 and fast > 10 ** 6, out
+    configs, targets, failed = (int(words[words.index(w) + 1]) for w in ("configurations", "targets", "failed"))
+    assert failed == 0 and configs > 250 and targets > 10 ** 6, out
