@@ -38,13 +38,13 @@ STEP_BYTES_PER_NODE = 2 * 19 * 4 * 2
 COLLIDE_BYTES_PER_NODE = STEP_BYTES_PER_NODE + 2 * 4
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes of the collide class (bulk + near launches) per step of the
-# 128x128x512 channel, from an ncu capture of the bulk kernel on the
-# 128x128x32 slab of the same channel, scaled by bulk nodes: B per bulk node
-# x 8,331,264 bulk nodes + 9.9 MB for the near tiles.
-COLLIDE_TRAFFIC_PER_BULK_NODE = 289.6
-COLLIDE_TRAFFIC_BYTES = COLLIDE_TRAFFIC_PER_BULK_NODE * 8331264 + 9.9e6
+# 128x128x512 channel, from an ncu capture of one bulk-kernel launch on the
+# 128x128x128 channel (populations larger than L2), scaled by bulk nodes:
+# B per bulk node x 8,331,264 bulk nodes + 9.8 MB read by the near launch.
+COLLIDE_TRAFFIC_PER_BULK_NODE = 289.4
+COLLIDE_TRAFFIC_BYTES = COLLIDE_TRAFFIC_PER_BULK_NODE * 8331264 + 9.8e6
 # Thread instructions per node of the noisy bulk collide kernel (same capture).
-COLLIDE_INST_PER_NODE = 1688.0
+COLLIDE_INST_PER_NODE = 1688.1
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 
