@@ -254,6 +254,42 @@ __host__ __device__ __forceinline__ bool is_solid(int x, int y, int z, const int
     return in_box(x, y, z, o, P, bi) && mask[bi];
 }
 
+// Directions i = 1..18 whose neighbour x + c_i is a particle node of the box
+// at origin o with node mask `mask`, as bits 1 << i. The neighbour wraps on a
+// periodic axis; across a wall there is none. The neighbour's box
+// coordinates are the node's own plus c_i, taken modulo L on periodic axes.
+__host__ __device__ __forceinline__ uint32_t solid_neighbours(int x, int y, int z, const int o[3],
+                                                              const uint8_t* mask, const KParams& P)
+{
+    const int c[3] = {x, y, z};
+    const int L[3] = {P.lx, P.ly, P.lz};
+    int d[3];
+    bool lo[3], hi[3];  // a step down / up this axis leaves through a wall
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        d[a] = box_rel(c[a], o[a], L[a], P.wall[a]);
+        lo[a] = P.wall[a] && c[a] == 0;
+        hi[a] = P.wall[a] && c[a] == L[a] - 1;
+    }
+    const unsigned B = (unsigned)P.B;
+    uint32_t bits = 0u;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const int s[3] = {cxv(i), cyv(i), czv(i)};
+        bool ok = true;
+        unsigned e[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if ((s[a] < 0 && lo[a]) || (s[a] > 0 && hi[a])) ok = false;
+            int t = d[a] + s[a];
+            if (!P.wall[a]) t = t >= L[a] ? t - L[a] : (t < 0 ? t + L[a] : t);
+            e[a] = (unsigned)t;
+        }
+        if (ok && e[0] < B && e[1] < B && e[2] < B && mask[e[0] + B * (e[1] + B * e[2])]) bits |= 1u << i;
+    }
+    return bits;
+}
+
 // Does [a0, a0+la) meet [b0, b0+lb) on an axis of length L (periodic: modulo L)?
 __host__ __device__ __forceinline__ bool ranges_meet(int a0, int la, int b0, int lb, int L, int wall)
 {

@@ -446,26 +446,15 @@ __device__ __forceinline__ void near_tile_work(int cx, int cy, int cz, int tx, i
     const int z = bz;
     const bool inside = x < P.lx && y < P.ly;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint32_t links = 0;
-    if (inside && !is_solid(x, y, z, o, mask, P)) {
-        const int L[3] = {P.lx, P.ly, P.lz};
-        uint32_t solid_nb = 0;
-#pragma unroll
-        for (int i = 1; i < 19; ++i) {
-            int q[3] = {x + cxv(i), y + cyv(i), z + czv(i)};
-            bool ok = true;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (q[a] < 0 || q[a] >= L[a]) {
-                    if (P.wall[a]) ok = false;
-                    else q[a] += (q[a] < 0) ? L[a] : -L[a];
-                }
-            }
-            if (ok && is_solid(q[0], q[1], q[2], o, mask, P)) solid_nb |= 1u << i;
-        }
+    const bool fluid = inside && !is_solid(x, y, z, o, mask, P);
+    const uint32_t links = fluid ? solid_neighbours(x, y, z, o, mask, P) : 0u;
+    // A warp none of whose nodes has a particle link takes the update of the
+    // bulk tiles. Every lane of the block's full warps reaches the vote.
+    const bool warp_links = __any_sync(0xffffffffu, links != 0u);
+    if (fluid) {
         const uint32_t n = (uint32_t)x + (uint32_t)P.lx * ((uint32_t)y + (uint32_t)P.ly * (uint32_t)z);
-        collide_node<NOISE, true, TAU1>(x, y, z, n, fin, fout, psi, st, P, solid_nb, acc);
-        links = solid_nb;
+        if (warp_links) collide_node<NOISE, true, TAU1>(x, y, z, n, fin, fout, psi, st, P, links, acc);
+        else collide_node<NOISE, false, TAU1>(x, y, z, n, fin, fout, psi, st, P, 0u, nullptr);
     }
     if (!__syncthreads_or(links != 0)) {  // no particle link in this tile
         if (tid < 8) partials[cand * 8 + tid] = 0.0;

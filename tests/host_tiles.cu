@@ -9,7 +9,10 @@
 //     layer density or bounces a population off the particle;
 //  3. the candidate grid of the near launch reaches every near tile exactly
 //     once, so each near node is updated once and each tile's force partial
-//     is summed once.
+//     is summed once;
+//  4. solid_neighbours gives, for every fluid node, exactly the directions
+//     whose neighbour (wrapped on periodic axes, none across a wall) is a
+//     particle node.
 // Prints one line and returns 0 when every configuration passes.
 #include <cstdio>
 #include <cstdint>
@@ -97,6 +100,31 @@ int check(const flbm_params& p, int policy, long long* near_tiles, long long* to
                 if (!touch) continue;
                 ++*touch_nodes;
                 if (!tile_near(x / k.tx, y / k.ty, z, o, k)) ++fails;
+            }
+
+    // 4. the links found from box coordinates against the lattice scan
+    std::vector<uint8_t> mask((size_t)B * B * B);
+    for (int t = 0; t < B * B * B; ++t) mask[t] = box_node_inside(t, o, X, k) ? 1 : 0;
+    for (int z = 0; z < L[2]; ++z)
+        for (int y = 0; y < L[1]; ++y)
+            for (int x = 0; x < L[0]; ++x) {
+                if (scan[idx(x, y, z)]) continue;
+                uint32_t want = 0;
+                for (int i = 1; i < 19; ++i) {
+                    int q[3] = {x + cxv(i), y + cyv(i), z + czv(i)};
+                    bool ok = true;
+                    for (int a = 0; a < 3; ++a)
+                        if (q[a] < 0 || q[a] >= L[a]) {
+                            if (W[a]) ok = false;
+                            else q[a] = (q[a] + L[a]) % L[a];
+                        }
+                    if (ok && scan[idx(q[0], q[1], q[2])]) want |= 1u << i;
+                }
+                if (solid_neighbours(x, y, z, o, mask.data(), k) != want) {
+                    ++fails;
+                    z = L[2];
+                    break;
+                }
             }
 
     // 3. the candidate grid reaches every near tile exactly once
