@@ -3,7 +3,8 @@
 // The paper's statistics of the settling velocity (Section 3) are averages
 // over noise realisations and channel geometries. An ensemble advances all
 // its replicas with one set of batched launches per step: every launch walks
-// a flat list of work items (replica, block of that replica), and its blocks
+// a flat list of work items (replica and block of that replica, with the
+// block's tile coordinates decoded on the host), and its blocks
 // are persistent (a fixed number per SM, striding over the list). A block
 // stages the descriptor of its current replica (kernel parameters and device
 // pointers) in shared memory and runs the same device bodies as the
@@ -57,44 +58,48 @@ __device__ __forceinline__ void stage_rep(const RepDesc* __restrict__ reps, int 
     have = r;
 }
 
-// Tile b of a replica -> tile coordinates and this thread's place in it.
+// Work item of a batched launch: x the replica; for tile lists (density,
+// bulk collide) y, z, w the tile (bx, by, bz), for near lists the candidate
+// (cx, cy, cz); for the others y the block of the replica.
+using Item = int4;
+
+// This thread's place (tx, ty) in a tile: the tile width is a power of two.
 struct TileCoord {
     int bx, by, bz, tx, ty;
 };
-__device__ __forceinline__ TileCoord tile_of(int b, const KParams& P)
+__device__ __forceinline__ TileCoord tile_of(const Item& it, const KParams& P)
 {
     TileCoord c;
-    c.bx = b % P.gx;
-    const int r = b / P.gx;
-    c.by = r % P.gy;
-    c.bz = r / P.gy;
-    c.tx = threadIdx.x % P.tx;
-    c.ty = threadIdx.x / P.tx;
+    c.bx = it.y;
+    c.by = it.z;
+    c.bz = it.w;
+    c.tx = threadIdx.x & (P.tx - 1);
+    c.ty = threadIdx.x >> (__ffs(P.tx) - 1);
     return c;
 }
 
-// Every batched kernel: 256 threads, items[i] = (replica, block of replica).
+// Every batched kernel: 256 threads, items[i] as above.
 #define FLBM_FOR_ITEMS                                                     \
     __shared__ RepDesc sR;                                                 \
     int have = -1;                                                         \
     for (int i = blockIdx.x; i < nitems; i += gridDim.x) {                 \
-        const int2 it = items[i];                                          \
+        const Item it = items[i];                                          \
         stage_rep(reps, it.x, sR, have);                                   \
         const KParams& P = sR.P;
 #define FLBM_END_ITEMS }
 
 static __global__ void __launch_bounds__(256) kb_density(const RepDesc* __restrict__ reps,
-                                                         const int2* __restrict__ items, int nitems, int par)
+                                                         const Item* __restrict__ items, int nitems, int par)
 {
     FLBM_FOR_ITEMS
-    const TileCoord c = tile_of(it.y, P);
+    const TileCoord c = tile_of(it, P);
     density_node(c.bx * P.tx + c.tx, c.by * P.ty + c.ty, c.bz, sR.f[par], sR.psi, sR.st, sR.masks, P);
     FLBM_END_ITEMS
 }
 
 // Shell blocks of the replica first, then the blocks of its particle box.
 static __global__ void __launch_bounds__(256) kb_shell(const RepDesc* __restrict__ reps,
-                                                       const int2* __restrict__ items, int nitems)
+                                                       const Item* __restrict__ items, int nitems)
 {
     FLBM_FOR_ITEMS
     const int nbs = (int)((shell_count(P) + 255) / 256);
@@ -107,29 +112,27 @@ static __global__ void __launch_bounds__(256) kb_shell(const RepDesc* __restrict
 
 template <bool NOISE, bool TAU1>
 static __global__ void __launch_bounds__(256, 3)
-    kb_bulk(const RepDesc* __restrict__ reps, const int2* __restrict__ items, int nitems, int par)
+    kb_bulk(const RepDesc* __restrict__ reps, const Item* __restrict__ items, int nitems, int par)
 {
     FLBM_FOR_ITEMS
-    const TileCoord c = tile_of(it.y, P);
+    const TileCoord c = tile_of(it, P);
     bulk_tile<NOISE, TAU1>(c.bx, c.by, c.bz, c.tx, c.ty, sR.f[par], sR.f[1 - par], sR.psi, sR.st, P);
     FLBM_END_ITEMS
 }
 
 template <bool NOISE, bool TAU1>
 static __global__ void __launch_bounds__(256, 2)
-    kb_near(const RepDesc* __restrict__ reps, const int2* __restrict__ items, int nitems, int par)
+    kb_near(const RepDesc* __restrict__ reps, const Item* __restrict__ items, int nitems, int par)
 {
     FLBM_FOR_ITEMS
-    const int cx = it.y % P.ncx;
-    const int cy = (it.y / P.ncx) % P.ncy;
-    const int cz = it.y / (P.ncx * P.ncy);
-    near_tile<NOISE, TAU1>(cx, cy, cz, threadIdx.x % P.tx, threadIdx.x / P.tx, threadIdx.x, sR.f[par],
+    const TileCoord c = tile_of(it, P);
+    near_tile<NOISE, TAU1>(c.bx, c.by, c.bz, c.tx, c.ty, threadIdx.x, sR.f[par],
                            sR.f[1 - par], sR.psi, sR.st, sR.masks, sR.partials, P);
     FLBM_END_ITEMS
 }
 
 static __global__ void __launch_bounds__(256) kb_mark_next(const RepDesc* __restrict__ reps,
-                                                           const int2* __restrict__ items, int nitems)
+                                                           const Item* __restrict__ items, int nitems)
 {
     FLBM_FOR_ITEMS
     mark_next_block(it.y, sR.st, sR.masks, sR.box_counts, P);
@@ -137,7 +140,7 @@ static __global__ void __launch_bounds__(256) kb_mark_next(const RepDesc* __rest
 }
 
 static __global__ void __launch_bounds__(256) kb_cover(const RepDesc* __restrict__ reps,
-                                                       const int2* __restrict__ items, int nitems, int par)
+                                                       const Item* __restrict__ items, int nitems, int par)
 {
     FLBM_FOR_ITEMS
     cover_then_finish(it.y, sR.f[1 - par], sR.st, sR.masks, sR.box_parts, sR.box_counts, P);
@@ -145,7 +148,7 @@ static __global__ void __launch_bounds__(256) kb_cover(const RepDesc* __restrict
 }
 
 static __global__ void __launch_bounds__(256) kb_finish(const RepDesc* __restrict__ reps,
-                                                        const int2* __restrict__ items, int nitems)
+                                                        const Item* __restrict__ items, int nitems)
 {
     FLBM_FOR_ITEMS
     finish_step(sR.st, sR.box_counts, sR.box_parts, sR.box_blocks, P);
@@ -188,7 +191,7 @@ struct flbm_ens {
     void* arena = nullptr;
     RepDesc* d_reps = nullptr;
     DevState* d_states = nullptr;  // n records, contiguous
-    int2* d_items = nullptr;
+    Item* d_items = nullptr;
     size_t items_cap = 0;
     long long off[W_COUNT + 1] = {};  // work list k = d_items[off[k] .. off[k+1])
     double* obs_tiles = nullptr;
@@ -261,7 +264,16 @@ int apply_config(flbm_ens* e)
     std::iota(order.begin(), order.end(), 0);
     if (e->cfg.packing == 2)
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return e->kp[a].N > e->kp[b].N; });
-    std::vector<int2> items;
+    std::vector<Item> items;
+    // Block b of replica r in list w, with its tile or candidate decoded.
+    auto item = [&](int r, long long b, int w) {
+        const KParams& k = e->kp[r];
+        if (w == W_DENSITY || (w >= W_BULK && w < W_BULK + 4))
+            return make_int4(r, (int)(b % k.gx), (int)(b / k.gx % k.gy), (int)(b / ((long long)k.gx * k.gy)));
+        if (w >= W_NEAR && w < W_NEAR + 4)
+            return make_int4(r, (int)(b % k.ncx), (int)(b / k.ncx % k.ncy), (int)(b / ((long long)k.ncx * k.ncy)));
+        return make_int4(r, (int)b, 0, 0);
+    };
     for (int w = 0; w < W_COUNT; ++w) {
         e->off[w] = (long long)items.size();
         if (e->cfg.packing == 1) {
@@ -269,10 +281,10 @@ int apply_config(flbm_ens* e)
             for (int r = 0; r < e->n; ++r) most = std::max(most, blocks_of(e->kp[r], w));
             for (long long b = 0; b < most; ++b)
                 for (int r = 0; r < e->n; ++r)
-                    if (b < blocks_of(e->kp[r], w)) items.push_back(make_int2(r, (int)b));
+                    if (b < blocks_of(e->kp[r], w)) items.push_back(item(r, b, w));
         } else {
             for (int r : order)
-                for (long long b = 0, nb = blocks_of(e->kp[r], w); b < nb; ++b) items.push_back(make_int2(r, (int)b));
+                for (long long b = 0, nb = blocks_of(e->kp[r], w); b < nb; ++b) items.push_back(item(r, b, w));
         }
     }
     e->off[W_COUNT] = (long long)items.size();
@@ -281,11 +293,11 @@ int apply_config(flbm_ens* e)
         cudaFree(e->d_items);
         e->d_items = nullptr;
         e->items_cap = 0;
-        if (cudaMalloc(&e->d_items, sizeof(int2) * items.size()) != cudaSuccess)
+        if (cudaMalloc(&e->d_items, sizeof(Item) * items.size()) != cudaSuccess)
             return efail(e, FLBM_E_NOMEM, "work lists");
         e->items_cap = items.size();
     }
-    ECK(e, cudaMemcpyAsync(e->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, e->stream));
+    ECK(e, cudaMemcpyAsync(e->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, e->stream));
     ECK(e, cudaMemcpyAsync(e->d_reps, e->rd.data(), sizeof(RepDesc) * e->n, cudaMemcpyHostToDevice, e->stream));
     ECK(e, cudaStreamSynchronize(e->stream));  // host vectors go out of scope
     return FLBM_OK;
@@ -379,7 +391,7 @@ namespace {
 
 // Launch work list w of kernel K with its trailing arguments on stream s.
 template <typename... Args>
-int launch_on(flbm_ens* e, cudaStream_t s, int w, void (*kern)(const RepDesc*, const int2*, int, Args...),
+int launch_on(flbm_ens* e, cudaStream_t s, int w, void (*kern)(const RepDesc*, const Item*, int, Args...),
               const char* what, Args... args)
 {
     const long long nitems = e->off[w + 1] - e->off[w];
@@ -391,7 +403,7 @@ int launch_on(flbm_ens* e, cudaStream_t s, int w, void (*kern)(const RepDesc*, c
 }
 
 template <typename... Args>
-int launch_list(flbm_ens* e, int w, void (*kern)(const RepDesc*, const int2*, int, Args...), const char* what,
+int launch_list(flbm_ens* e, int w, void (*kern)(const RepDesc*, const Item*, int, Args...), const char* what,
                 Args... args)
 {
     return launch_on(e, e->stream, w, kern, what, args...);
