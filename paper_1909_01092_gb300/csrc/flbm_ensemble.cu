@@ -120,8 +120,10 @@ static __global__ void __launch_bounds__(256, 3)
     FLBM_END_ITEMS
 }
 
+// Three blocks per SM: the register cap costs some spills, and the extra
+// resident warps hide more of the near tiles' latency (measured faster).
 template <bool NOISE, bool TAU1>
-static __global__ void __launch_bounds__(256, 2)
+static __global__ void __launch_bounds__(256, 3)
     kb_near(const RepDesc* __restrict__ reps, const Item* __restrict__ items, int nitems, int par)
 {
     FLBM_FOR_ITEMS
