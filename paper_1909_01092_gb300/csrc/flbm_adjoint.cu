@@ -67,7 +67,8 @@ struct AdjState {
 // on their large parts, keep 48 significant bits; only the neighbour differences
 // (a(x+c_i) - a(x)) + c_i . (b(x+c_i) - b(x)) go through the float32 mode
 // projection and collision transpose (adj_modes), the large part through
-// adj_modes_ab in double-float arithmetic (flbm_df.h). The adjoint of psi at
+// adj_modes_ab_mixed: double-float arithmetic (flbm_df.h) on the adjoint
+// values, whose coefficients (the forward quantities) are floats. The adjoint of psi at
 // particle nodes and wall ghosts (lpsi) and the reductions are FP64.
 //
 // The 48-bit fields are stored as two floats, v = hi + lo with
@@ -629,27 +630,22 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
             float lrho[2], lj[2][3], lgv[2][3], lG;
             adj_modes<float>(rho, j, g, ext, P.G, lm, lrho, lj, lgv, lG);
             {
-                // Double-float: the inputs are floats, (a_l, b_l) are stored as pairs.
-                df rf[2], jf[2][3], gf[2][3], ef[3], af[2], bf[2][3], lrf[2], ljf[2][3], lgf[2][3], lGf;
+                // Double-float for (a_l, b_l), stored as pairs, and the outputs;
+                // the forward quantities and coefficients in float.
+                df af[2], bf[2][3], lrf[2], ljf[2][3], lgf[2][3], lGf;
                 for (int l = 0; l < 2; ++l) {
-                    rf[l] = df(rho[l]);
                     af[l] = df(asv[l].hi, asv[l].lo);
-                    for (int a = 0; a < 3; ++a) {
-                        jf[l][a] = df(j[l][a]);
-                        gf[l][a] = df(g[l][a]);
-                        bf[l][a] = df(bsv[l][a].hi, bsv[l][a].lo);
-                    }
+                    for (int a = 0; a < 3; ++a) bf[l][a] = df(bsv[l][a].hi, bsv[l][a].lo);
                 }
-                for (int a = 0; a < 3; ++a) ef[a] = df(ext[a]);
-                adj_modes_ab<df>(rf, jf, gf, ef, df(P.G), af, bf, lrf, ljf, lgf, lGf);
+                adj_modes_ab_mixed<df>(rho, j, g, ext, P.G, af, bf, lrf, ljf, lgf, lGf);
                 acc[9] += lGf.value() + (double)lG;
                 for (int l = 0; l < 2; ++l) {
-                    df v = lrf[l] + df(lrho[l]);
+                    df v = lrf[l] + lrho[l];
                     if (PARTICLE) v = v + df(lrx[l]);  // link and reaction terms (FP64 sums)
                     lam0[(size_t)l * N + n] = Split{v.hi, v.lo};
                     for (int a = 0; a < 3; ++a) {
-                        const df vj = ljf[l][a] + df(lj[l][a]);
-                        const df vg = lgf[l][a] + df(lgv[l][a]);
+                        const df vj = ljf[l][a] + lj[l][a];
+                        const df vg = lgf[l][a] + lgv[l][a];
                         lam0[(size_t)(2 + 3 * l + a) * N + n] = Split{vj.hi, vj.lo};
                         lg[(size_t)(3 * l + a) * N + n] = Split{vg.hi, vg.lo};
                     }

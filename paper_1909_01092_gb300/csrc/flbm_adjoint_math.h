@@ -152,4 +152,51 @@ FLBM_HD void adj_modes_ab(const T rho[2], const T j[2][3], const T g[2][3], cons
     }
 }
 
+// adj_modes_ab with the forward quantities (rho, j, g, the external force
+// and G) and the coefficients formed from them (1 / rho_tot, the forces F_l
+// and the velocity u) in float, computed as the forward step computes them,
+// and the adjoint values (a, b and every output) in A: the type of the large
+// parts (flbm::df on the GPU; double for a reference with the same float
+// coefficients). Every product is an adjoint value times a float.
+template <class A>
+FLBM_HD void adj_modes_ab_mixed(const float rho[2], const float j[2][3], const float g[2][3], const float ext[3],
+                                float G, const A a[2], const A b[2][3], A lrho[2], A lj[2][3], A lg[2][3], A& lG)
+{
+    const float rt = rho[0] + rho[1];
+    const float irt = 1.0f / rt;
+    float F[2][3], u[3];
+    for (int l = 0; l < 2; ++l)
+        for (int c = 0; c < 3; ++c) F[l][c] = -G * rho[l] * g[l][c] + rho[l] * irt * ext[c];
+    for (int c = 0; c < 3; ++c) u[c] = (j[0][c] + j[1][c] + 0.5f * (F[0][c] + F[1][c])) * irt;
+    A lu[3] = {A(), A(), A()};
+    A lF[2][3];
+    for (int l = 0; l < 2; ++l) {
+        lrho[l] = a[l] + b[l][0] * u[0] + b[l][1] * u[1] + b[l][2] * u[2];
+        for (int c = 0; c < 3; ++c) {
+            lF[l][c] = b[l][c] * 0.5f;
+            lu[c] += b[l][c] * rho[l];
+        }
+    }
+    const A ul = lu[0] * u[0] + lu[1] * u[1] + lu[2] * u[2];
+    const float hirt = 0.5f * irt;
+    for (int l = 0; l < 2; ++l) {
+        lrho[l] -= ul * irt;
+        for (int c = 0; c < 3; ++c) {
+            lj[l][c] = lu[c] * irt;
+            lF[l][c] += lu[c] * hirt;
+        }
+    }
+    A eF[2];
+    for (int l = 0; l < 2; ++l) eF[l] = lF[l][0] * ext[0] + lF[l][1] * ext[1] + lF[l][2] * ext[2];
+    const A es = (eF[0] * rho[0] + eF[1] * rho[1]) * (irt * irt);
+    lG = A();
+    for (int l = 0; l < 2; ++l) {
+        const A gl = lF[l][0] * g[l][0] + lF[l][1] * g[l][1] + lF[l][2] * g[l][2];
+        const float cg = -G * rho[l];
+        for (int c = 0; c < 3; ++c) lg[l][c] = lF[l][c] * cg;
+        lrho[l] += gl * (-G) + eF[l] * irt - es;
+        lG += gl * (-rho[l]);
+    }
+}
+
 }  // namespace flbm

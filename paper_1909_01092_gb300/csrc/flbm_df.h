@@ -97,6 +97,21 @@ FLBM_DF df operator/(df a, df b)
     return fast_two_sum(q1, q2);
 }
 
+// a + b and a * b for a float b (exact as given).
+FLBM_DF df operator+(df a, float b)
+{
+    df s = two_sum(a.hi, b);
+    s.lo += a.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+
+FLBM_DF df operator*(df a, float b)
+{
+    df p = two_prod(a.hi, b);
+    p.lo = df_fma(a.lo, b, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+
 FLBM_DF df& operator+=(df& a, df b) { return a = a + b; }
 FLBM_DF df& operator-=(df& a, df b) { return a = a - b; }
 

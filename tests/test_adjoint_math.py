@@ -23,7 +23,8 @@ SHIM = r"""
 #include "flbm_df.h"
 extern "C" void df_op(int op, const float* a, const float* b, float* out) {
     const flbm::df x(a[0], a[1]), y(b[0], b[1]);
-    const flbm::df r = op == 0 ? x + y : op == 1 ? x - y : op == 2 ? x * y : x / y;
+    const flbm::df r = op == 0 ? x + y : op == 1 ? x - y : op == 2 ? x * y : op == 3 ? x / y
+                     : op == 4 ? x + b[0] : x * b[0];
     out[0] = r.hi; out[1] = r.lo;
 }
 extern "C" void adj_ab_df(const double* in, double G, const double* ab, double* out) {
@@ -39,6 +40,31 @@ extern "C" void adj_ab_df(const double* in, double G, const double* ab, double* 
     out[0] = lrho[0].value(); out[1] = lrho[1].value();
     for (int l = 0; l < 2; ++l) for (int c = 0; c < 3; ++c) { out[2 + 3 * l + c] = lj[l][c].value(); out[8 + 3 * l + c] = lg[l][c].value(); }
     out[14] = lG.value();
+}
+extern "C" void adj_ab_mixed(const float* in, float G, const double* ab, int use_df, double* out) {
+    using flbm::df;
+    const float rho[2] = {in[0], in[1]};
+    const float j[2][3] = {{in[2], in[3], in[4]}, {in[5], in[6], in[7]}};
+    const float g[2][3] = {{in[8], in[9], in[10]}, {in[11], in[12], in[13]}};
+    const float ext[3] = {in[14], in[15], in[16]};
+    if (use_df) {
+        const df a[2] = {df(ab[0]), df(ab[1])};
+        const df b[2][3] = {{df(ab[2]), df(ab[3]), df(ab[4])}, {df(ab[5]), df(ab[6]), df(ab[7])}};
+        df lrho[2], lj[2][3], lg[2][3], lG;
+        flbm::adj_modes_ab_mixed<df>(rho, j, g, ext, G, a, b, lrho, lj, lg, lG);
+        out[0] = lrho[0].value(); out[1] = lrho[1].value();
+        for (int l = 0; l < 2; ++l) for (int c = 0; c < 3; ++c) { out[2 + 3 * l + c] = lj[l][c].value(); out[8 + 3 * l + c] = lg[l][c].value(); }
+        out[14] = lG.value();
+    } else {
+        const double a[2] = {(double)df(ab[0]).value(), (double)df(ab[1]).value()};
+        double b[2][3];
+        for (int l = 0; l < 2; ++l) for (int c = 0; c < 3; ++c) b[l][c] = df(ab[2 + 3 * l + c]).value();
+        double lrho[2], lj[2][3], lg[2][3], lG;
+        flbm::adj_modes_ab_mixed<double>(rho, j, g, ext, G, a, b, lrho, lj, lg, lG);
+        out[0] = lrho[0]; out[1] = lrho[1];
+        for (int l = 0; l < 2; ++l) for (int c = 0; c < 3; ++c) { out[2 + 3 * l + c] = lj[l][c]; out[8 + 3 * l + c] = lg[l][c]; }
+        out[14] = lG;
+    }
 }
 extern "C" void fwd(const double* in, double G, double* ms) {
     const double rho[2] = {in[0], in[1]};
@@ -94,6 +120,7 @@ def shim(tmp_path_factory):
     L.adj_ab.argtypes = [dp, ctypes.c_double, dp, dp]
     L.adj_ab_df.argtypes = [dp, ctypes.c_double, dp, dp]
     fp = ctypes.POINTER(ctypes.c_float)
+    L.adj_ab_mixed.argtypes = [fp, ctypes.c_float, dp, ctypes.c_int, dp]
     L.df_op.argtypes = [ctypes.c_int, fp, fp, fp]
     return L
 
@@ -159,11 +186,12 @@ def _split(v):
     return np.array([hi, np.float32(v - float(hi))], dtype=np.float32)
 
 
-@pytest.mark.parametrize("op", range(4))
+@pytest.mark.parametrize("op", range(6))
 def test_double_float_operations_against_exact_arithmetic(shim, op):
-    """Sum, difference, product and quotient of double-float numbers agree
-    with the exact rational result of the represented values to 2^-44
-    relative (about 48-bit operands)."""
+    """Sum, difference, product and quotient of double-float numbers, and
+    the sum and product of a double-float and a float, agree with the exact
+    rational result of the represented values to 2^-44 relative (about
+    48-bit operands)."""
     from fractions import Fraction
 
     rng = np.random.default_rng(7 + op)
@@ -174,13 +202,16 @@ def test_double_float_operations_against_exact_arithmetic(shim, op):
         b = _split(rng.standard_normal() * 10.0 ** rng.integers(-3, 4))
         if op == 1:  # differences of close numbers: the adjoint's use
             b = _split(float(a[0]) * (1 + 1e-3 * rng.standard_normal()))
+        if op >= 4:  # the second operand is a float
+            b[1] = np.float32(0.0)
         out = np.zeros(2, dtype=np.float32)
         shim.df_op(op, a.ctypes.data_as(fp), b.ctypes.data_as(fp), out.ctypes.data_as(fp))
         fa = Fraction(float(a[0])) + Fraction(float(a[1]))
         fb = Fraction(float(b[0])) + Fraction(float(b[1]))
-        exact = [fa + fb, fa - fb, fa * fb, fa / fb][op]
+        exact = [fa + fb, fa - fb, fa * fb, fa / fb, fa + fb, fa * fb][op]
         got = Fraction(float(out[0])) + Fraction(float(out[1]))
-        scale = [max(abs(fa), abs(fb)), max(abs(fa), abs(fb)), abs(exact), abs(exact)][op]
+        scale = [max(abs(fa), abs(fb)), max(abs(fa), abs(fb)), abs(exact), abs(exact),
+                 max(abs(fa), abs(fb)), abs(exact)][op]
         worst = max(worst, float(abs(got - exact) / scale))
     assert worst <= 2.0 ** -44, worst
 
@@ -199,3 +230,27 @@ def test_density_momentum_part_in_double_float(shim, seed):
     shim.adj_ab(_p(x), G, _p(ab), _p(o1))
     shim.adj_ab_df(_p(x), G, _p(ab), _p(o2))
     assert np.max(np.abs(o1 - o2)) <= 1e-12 * np.max(np.abs(ab)), np.max(np.abs(o1 - o2))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_mixed_density_momentum_part_in_double_float(shim, seed):
+    """adj_modes_ab_mixed (float coefficients, double-float adjoint values)
+    equals its evaluation with the same float coefficients and double adjoint
+    values to 1e-12 of the largest adjoint input, and the double-float
+    adj_modes_ab with exact coefficients to the float rounding of the
+    coefficients (1e-6 of the largest adjoint input)."""
+    rng = np.random.default_rng(300 + seed)
+    x = np.concatenate([[1.0 + 0.05 * rng.standard_normal(), 0.05 + 0.01 * rng.standard_normal()],
+                        0.02 * rng.standard_normal(6), 0.1 * rng.standard_normal(6), 1e-4 * rng.standard_normal(3)])
+    xf = x.astype(np.float32)
+    x = xf.astype(np.float64)
+    ab = 1e3 * (1.0 + 0.01 * rng.standard_normal(8))
+    G = np.float32(1.2)
+    fp = ctypes.POINTER(ctypes.c_float)
+    o_df, o_d, o_exact = np.zeros(15), np.zeros(15), np.zeros(15)
+    shim.adj_ab_mixed(xf.ctypes.data_as(fp), ctypes.c_float(G), _p(ab), 1, _p(o_df))
+    shim.adj_ab_mixed(xf.ctypes.data_as(fp), ctypes.c_float(G), _p(ab), 0, _p(o_d))
+    shim.adj_ab(_p(x), float(G), _p(ab), _p(o_exact))
+    scale = np.max(np.abs(ab))
+    assert np.max(np.abs(o_df - o_d)) <= 1e-12 * scale, np.max(np.abs(o_df - o_d))
+    assert np.max(np.abs(o_df - o_exact)) <= 1e-6 * scale, np.max(np.abs(o_df - o_exact))
