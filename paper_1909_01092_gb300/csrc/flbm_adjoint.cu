@@ -68,8 +68,11 @@ struct AdjState {
 // (a(x+c_i) - a(x)) + c_i . (b(x+c_i) - b(x)) go through the float32 mode
 // projection and collision transpose (adj_modes), the large part through
 // adj_modes_ab_mixed: double-float arithmetic (flbm_df.h) on the adjoint
-// values, whose coefficients (the forward quantities) are floats. The adjoint of psi at
-// particle nodes and wall ghosts (lpsi) and the reductions are FP64.
+// values, whose coefficients (the forward quantities) are floats. The terms of
+// the moving links and the Shan-Chen reaction take the same form: double-float
+// adjoint values times float coefficients, summed per node and added to the
+// FP64 partials once per node. The adjoint of psi at particle nodes and wall
+// ghosts (lpsi) and the reductions are FP64.
 //
 // The 48-bit fields are stored as two floats, v = hi + lo with
 // lo = fl(v - hi). A node reads its own values as FP64 (sval) and forms its
@@ -536,7 +539,10 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
             }
             const float* lF = adj->lFf;
             const float* lT = adj->lTf;
-            double lrx[2] = {0.0, 0.0};  // extra adjoint of rho_l from links and the reaction
+            df lrx[2];  // extra adjoint of rho_l from links and the reaction
+            // This node's link and reaction terms of partials 0..9, added to acc once.
+            df lk[10];
+            const df lled[2] = {df(adj->lled[0]), df(adj->lled[1])};
             Split asv[2], bsv[2][3];         // a_l, b_l of this node
             float lm[2][10];               // mode adjoint of the neighbour differences
 #pragma unroll
@@ -558,7 +564,12 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                         // bounce-back reads (x, -c_i): a - c_i . b, so dv = -2 c_i . b (float)
                         dv = -2.0f * (cx * bs[0].hi + cy * bs[1].hi + cz * bs[2].hi);
                         if (PARTICLE && (solid_nb >> i & 1u)) {
-                            const double cb = cx * sval(bs[0]) + cy * sval(bs[1]) + cz * sval(bs[2]);
+                            // The large adjoint parts (a_l, b_l and the ledger's) in double-float,
+                            // the forward quantities in float.
+                            df cb;
+                            if (cx) cb += cx > 0 ? df(bs[0].hi, bs[0].lo) : -df(bs[0].hi, bs[0].lo);
+                            if (cy) cb += cy > 0 ? df(bs[1].hi, bs[1].lo) : -df(bs[1].hi, bs[1].lo);
+                            if (cz) cb += cz > 0 ? df(bs[2].hi, bs[2].lo) : -df(bs[2].hi, bs[2].lo);
                             const float d[3] = {rnf[0] + 0.5f * cx, rnf[1] + 0.5f * cy, rnf[2] + 0.5f * cz};
                             const float kap = cx * (lF[0] + lT[1] * d[2] - lT[2] * d[1]) +
                                               cy * (lF[1] + lT[2] * d[0] - lT[0] * d[2]) +
@@ -568,23 +579,26 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                             const float ubc = (V[0] + Om[1] * d[2] - Om[2] * d[1]) * cx +
                                               (V[1] + Om[2] * d[0] - Om[0] * d[2]) * cy +
                                               (V[2] + Om[0] * d[1] - Om[1] * d[0]) * cz;
-                            const double lcorr = -(ax - cb) - (double)kap + adj->lled[l];
-                            lrx[l] += lcorr * (6.0 * wv(i) * ubc);
-                            const double lub = lcorr * 6.0 * wv(i) * rho[l];  // lambda (u_b . c_i)
-                            const double lb[3] = {lub * cx, lub * cy, lub * cz};
-                            acc[3] += lb[0]; acc[4] += lb[1]; acc[5] += lb[2];
-                            acc[6] += d[1] * lb[2] - d[2] * lb[1];
-                            acc[7] += d[2] * lb[0] - d[0] * lb[2];
-                            acc[8] += d[0] * lb[1] - d[1] * lb[0];
-                            acc[0] -= lb[1] * Om[2] - lb[2] * Om[1];
-                            acc[1] -= lb[2] * Om[0] - lb[0] * Om[2];
-                            acc[2] -= lb[0] * Om[1] - lb[1] * Om[0];
-                            // lever of the exchanged momentum (2 f* - corr) c_i
-                            const double dp = 2.0 * fo[l][i] - 6.0 * wv(i) * rho[l] * ubc;
-                            const double fr[3] = {dp * cx, dp * cy, dp * cz};
-                            acc[0] -= fr[1] * lT[2] - fr[2] * lT[1];
-                            acc[1] -= fr[2] * lT[0] - fr[0] * lT[2];
-                            acc[2] -= fr[0] * lT[1] - fr[1] * lT[0];
+                            const df lcorr = (cb - df(as.hi, as.lo)) + (lled[l] + (-kap));
+                            const float w6 = 6.0f * wv(i);
+                            lrx[l] += lcorr * (w6 * ubc);
+                            const df lub = lcorr * (w6 * rho[l]);  // lambda (u_b . c_i)
+                            // With lb = lub c_i: partials 3..5 += lb, 6..8 += d x lb,
+                            // 0..2 -= lb x Omega (the float sums of coefficients exact).
+                            if (cx) lk[3] += cx > 0 ? lub : -lub;
+                            if (cy) lk[4] += cy > 0 ? lub : -lub;
+                            if (cz) lk[5] += cz > 0 ? lub : -lub;
+                            lk[6] += lub * two_sum(d[1] * cz, -d[2] * cy);
+                            lk[7] += lub * two_sum(d[2] * cx, -d[0] * cz);
+                            lk[8] += lub * two_sum(d[0] * cy, -d[1] * cx);
+                            lk[0] += lub * two_sum(cz * Om[1], -cy * Om[2]);
+                            lk[1] += lub * two_sum(cx * Om[2], -cz * Om[0]);
+                            lk[2] += lub * two_sum(cy * Om[0], -cx * Om[1]);
+                            // lever of the exchanged momentum (2 f* - corr) c_i (small: float)
+                            const float dp = 2.0f * fo[l][i] - w6 * rho[l] * ubc;
+                            lk[0] = lk[0] + (-dp * (cy * lT[2] - cz * lT[1]));
+                            lk[1] = lk[1] + (-dp * (cz * lT[0] - cx * lT[2]));
+                            lk[2] = lk[2] + (-dp * (cx * lT[1] - cy * lT[0]));
                             dv += 2.0f * kap;
                         }
                     } else {
@@ -615,16 +629,18 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                                       cy * (lF[1] + lT[2] * d[0] - lT[0] * d[2]) +
                                       cz * (lF[2] + lT[0] * d[1] - lT[1] * d[0]);
                     const float w = wv(i);
-                    acc[9] += (double)kap * w * (rho[0] * pb + rho[1] * pa);
-                    lrx[0] += (double)(kap * P.G * w * pb);
-                    lrx[1] += (double)(kap * P.G * w * pa);
-                    const double mag = (double)P.G * w * (rho[0] * pb + rho[1] * pa);
-                    const double fr[3] = {mag * cx, mag * cy, mag * cz};
-                    acc[0] -= fr[1] * lT[2] - fr[2] * lT[1];
-                    acc[1] -= fr[2] * lT[0] - fr[0] * lT[2];
-                    acc[2] -= fr[0] * lT[1] - fr[1] * lT[0];
+                    const float t = rho[0] * pb + rho[1] * pa;
+                    lk[9] += two_prod(kap * w, t);
+                    lrx[0] = lrx[0] + kap * P.G * w * pb;
+                    lrx[1] = lrx[1] + kap * P.G * w * pa;
+                    const float mag = P.G * w * t;
+                    lk[0] = lk[0] + (-mag * (cy * lT[2] - cz * lT[1]));
+                    lk[1] = lk[1] + (-mag * (cz * lT[0] - cx * lT[2]));
+                    lk[2] = lk[2] + (-mag * (cx * lT[1] - cy * lT[0]));
                 }
             }
+            if (PARTICLE && solid_nb)
+                for (int k = 0; k < 10; ++k) acc[k] += lk[k].value();
             // Transpose of the collision: the float32 part from the differences, the
             // 48-bit part from (a_l, b_l) of this node (modes 0..3 only).
             float lrho[2], lj[2][3], lgv[2][3], lG;
@@ -641,7 +657,7 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
                 acc[9] += lGf.value() + (double)lG;
                 for (int l = 0; l < 2; ++l) {
                     df v = lrf[l] + lrho[l];
-                    if (PARTICLE) v = v + df(lrx[l]);  // link and reaction terms (FP64 sums)
+                    if (PARTICLE) v = v + lrx[l];  // link and reaction terms
                     lam0[(size_t)l * N + n] = Split{v.hi, v.lo};
                     for (int a = 0; a < 3; ++a) {
                         const df vj = ljf[l][a] + lj[l][a];
