@@ -938,19 +938,15 @@ static __global__ void __launch_bounds__(kT) ka_lpsi_shell(const lg_t* __restric
     lpsi[P.padn + dst] = cnt ? lp[1] / double(cnt) : 0.0;
 }
 
-// a_l of fluid nodes: lambda psi of the node (the Shan-Chen stencil
+// a_l of fluid node (x, y, z): lambda psi of the node (the Shan-Chen stencil
 // transposed) plus mu of every particle node and wall ghost among its
-// neighbours (each averaged this node's density).
-static __global__ void __launch_bounds__(kT) ka_final(lam_t* __restrict__ lam0, const lg_t* __restrict__ lg,
-                                                      const double* __restrict__ lpsi, const DevState* __restrict__ s0,
-                                                      const uint8_t* __restrict__ mk0, KParams P)
+// neighbours (each averaged this node's density). Only an edge candidate
+// (adj_edge_candidate) can have such neighbours; the others skip the scan.
+__device__ __forceinline__ void final_node(int x, int y, int z, bool candidate, lam_t* __restrict__ lam0,
+                                           const lg_t* __restrict__ lg, const double* __restrict__ lpsi,
+                                           const DevState* __restrict__ s0, const uint8_t* __restrict__ m0,
+                                           const KParams& P)
 {
-    const int x = blockIdx.x * P.tx + threadIdx.x;
-    const int y = blockIdx.y * P.ty + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= P.lx || y >= P.ly) return;
-    const uint8_t* m0 = cur_mask(s0, mk0, P);
-    if (solid_at(x, y, z, s0, m0, P)) return;
     const uint32_t n = lin(x, y, z, P);
     // Particle nodes and wall ghosts among the neighbours: their mu, and
     // whether the stencil of this node meets any (the neighbours of a node
@@ -958,7 +954,7 @@ static __global__ void __launch_bounds__(kT) ka_final(lam_t* __restrict__ lam0, 
     double add[2] = {0.0, 0.0};
     bool edge = false;
     const int L[3] = {P.lx, P.ly, P.lz};
-    for (int i = 1; i < 19; ++i) {
+    for (int i = 1; candidate && i < 19; ++i) {
         int r[3] = {x + cxv(i), y + cyv(i), z + czv(i)};
         bool ghost = false;
         for (int a = 0; a < 3; ++a) {
@@ -989,6 +985,36 @@ static __global__ void __launch_bounds__(kT) ka_final(lam_t* __restrict__ lam0, 
             lam0[c * P.N + n] = Split{v.hi, v.lo};
         }
     }
+}
+
+// Fluid nodes that are not edge candidates (every warp takes the same path).
+static __global__ void __launch_bounds__(kT) ka_final(lam_t* __restrict__ lam0, const lg_t* __restrict__ lg,
+                                                      const double* __restrict__ lpsi, const DevState* __restrict__ s0,
+                                                      const uint8_t* __restrict__ mk0, KParams P)
+{
+    const int x = blockIdx.x * P.tx + threadIdx.x;
+    const int y = blockIdx.y * P.ty + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= P.lx || y >= P.ly) return;
+    const int c[3] = {x, y, z};
+    const int o[3] = {s0->box0[0], s0->box0[1], s0->box0[2]};
+    if (adj_edge_candidate(c, o, P)) return;  // ka_final_edge's
+    final_node(x, y, z, false, lam0, lg, lpsi, s0, cur_mask(s0, mk0, P), P);
+}
+
+// The edge candidates, each once (adj_edge_node), in nearly uniform warps.
+static __global__ void __launch_bounds__(kT) ka_final_edge(lam_t* __restrict__ lam0, const lg_t* __restrict__ lg,
+                                                           const double* __restrict__ lpsi,
+                                                           const DevState* __restrict__ s0,
+                                                           const uint8_t* __restrict__ mk0, KParams P)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int o[3] = {s0->box0[0], s0->box0[1], s0->box0[2]};
+    int c[3];
+    if (!adj_edge_node(t, o, P, c)) return;
+    const uint8_t* m0 = cur_mask(s0, mk0, P);
+    if (solid_at(c[0], c[1], c[2], s0, m0, P)) return;
+    final_node(c[0], c[1], c[2], true, lam0, lg, lpsi, s0, m0, P);
 }
 
 // Per-tile partials -> adjoint of step n's particle state and the gradient
@@ -1168,6 +1194,14 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     ACK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
     ka_reduce<<<1, kT, 0, h->side>>>(b.adj, b.parts, h->ntiles, b.parts2, h->box_blocks);
     if (int rc = acheck(h, "ka_reduce")) return rc;
+    {
+        // The edge candidates on the side stream after the reduction (disjoint nodes).
+        const long long ne = adj_edge_entries(k);
+        if (ne > 0) {
+            ka_final_edge<<<(unsigned)((ne + kT - 1) / kT), kT, 0, h->side>>>(L0, b.lgf, b.lpsi, s0, m0, k);
+            if (int rc = acheck(h, "ka_final_edge")) return rc;
+        }
+    }
     ACK(h, cudaEventRecord(h->join_ev, h->side));
     ka_final<<<h->grid, h->block, 0, st>>>(L0, b.lgf, b.lpsi, s0, m0, k);
     if (int rc = acheck(h, "ka_final")) return rc;

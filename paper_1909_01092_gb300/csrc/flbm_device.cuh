@@ -312,6 +312,87 @@ __host__ __device__ __forceinline__ bool tile_near(int bx, int by, int bz, const
            ranges_meet(bz, 1, o[2] - 1, B2, P.lz, P.wall[2]);
 }
 
+// Edge candidates of the adjoint's last node pass: the nodes on a walled
+// face (a wall ghost among their neighbours) and the nodes of the particle
+// box at origin o grown by one node (a particle node among their
+// neighbours). No other node has either among its neighbours.
+__host__ __device__ __forceinline__ bool adj_edge_candidate(const int c[3], const int o[3], const KParams& P)
+{
+    const int L[3] = {P.lx, P.ly, P.lz};
+    for (int a = 0; a < 3; ++a)
+        if (P.wall[a] && (c[a] == 0 || c[a] == L[a] - 1)) return true;
+    if (!P.has_particle) return false;
+    bool in_grown = true;
+    for (int a = 0; a < 3; ++a) in_grown = in_grown && ranges_meet(c[a], 1, o[a] - 1, P.B + 2, L[a], P.wall[a]);
+    return in_grown;
+}
+
+// Entries adj_edge_node walks: the particle box grown by one node, then the
+// two faces of each walled axis.
+__host__ __device__ __forceinline__ long long adj_edge_entries(const KParams& P)
+{
+    const long long Bg = P.has_particle ? P.B + 2 : 0;
+    const int L[3] = {P.lx, P.ly, P.lz};
+    long long n = Bg * Bg * Bg;
+    for (int a = 0; a < 3; ++a)
+        if (P.wall[a]) n += 2LL * L[(a + 1) % 3] * L[(a + 2) % 3];
+    return n;
+}
+
+// Node c of entry t, or false: every edge candidate is the node of exactly
+// one entry. The grown box's entries outside the lattice, or repeating a node
+// where the box wraps a periodic axis shorter than it, give none; so do the
+// face entries that lie on a face of an earlier walled axis, repeat a face of
+// an axis of length 1, or lie in the grown box.
+__host__ __device__ __forceinline__ bool adj_edge_node(long long t, const int o[3], const KParams& P, int c[3])
+{
+    if (t < 0 || t >= adj_edge_entries(P)) return false;
+    const int L[3] = {P.lx, P.ly, P.lz};
+    const int Bg = P.B + 2;
+    const long long nbox = P.has_particle ? (long long)Bg * Bg * Bg : 0;
+    if (t < nbox) {
+        const int d[3] = {(int)(t % Bg), (int)(t / Bg % Bg), (int)(t / ((long long)Bg * Bg))};
+        for (int a = 0; a < 3; ++a) {
+            int v = o[a] - 1 + d[a];
+            if (P.wall[a]) {
+                if (v < 0 || v >= L[a]) return false;
+            } else {
+                if (d[a] >= L[a]) return false;
+                v = (v % L[a] + L[a]) % L[a];
+            }
+            c[a] = v;
+        }
+        return true;
+    }
+    t -= nbox;
+    int face = -1;
+    for (int a = 0; a < 3 && face < 0; ++a) {
+        if (!P.wall[a]) continue;
+        const int b = (a + 1) % 3, e = (a + 2) % 3;
+        const long long fsz = (long long)L[b] * L[e];
+        for (int side = 0; side < 2 && face < 0; ++side) {
+            if (t < fsz) {
+                if (side == 1 && L[a] == 1) return false;
+                c[a] = side ? L[a] - 1 : 0;
+                c[b] = (int)(t % L[b]);
+                c[e] = (int)(t / L[b]);
+                face = a;
+            } else {
+                t -= fsz;
+            }
+        }
+    }
+    if (face < 0) return false;
+    for (int a = 0; a < face; ++a)
+        if (P.wall[a] && (c[a] == 0 || c[a] == L[a] - 1)) return false;
+    if (P.has_particle) {
+        bool in_grown = true;
+        for (int a = 0; a < 3; ++a) in_grown = in_grown && ranges_meet(c[a], 1, o[a] - 1, Bg, L[a], P.wall[a]);
+        if (in_grown) return false;
+    }
+    return true;
+}
+
 __host__ __device__ __forceinline__ long long pad_index(int x, int y, int z, const KParams& P)
 {
     return (long long)(x + 1) + (long long)P.px * ((y + 1) + (long long)P.py * (z + 1));

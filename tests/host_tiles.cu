@@ -12,7 +12,10 @@
 //     is summed once;
 //  4. solid_neighbours gives, for every fluid node, exactly the directions
 //     whose neighbour (wrapped on periodic axes, none across a wall) is a
-//     particle node.
+//     particle node;
+//  5. every node with a wall ghost or a particle node among its neighbours is
+//     an edge candidate of the adjoint (adj_edge_candidate), and the entries
+//     of adj_edge_node reach every candidate exactly once and nothing else.
 // Prints one line and returns 0 when every configuration passes.
 #include <cstdio>
 #include <cstdint>
@@ -126,6 +129,40 @@ int check(const flbm_params& p, int policy, long long* near_tiles, long long* to
                     break;
                 }
             }
+
+    // 5. edge candidates of the adjoint and their enumeration
+    {
+        std::vector<int> tally(N, 0);
+        const long long ne = adj_edge_entries(k);
+        for (long long t = 0; t < ne; ++t) {
+            int c[3];
+            if (adj_edge_node(t, o, k, c)) {
+                bool ok = true;
+                for (int a = 0; a < 3; ++a) ok = ok && c[a] >= 0 && c[a] < L[a];
+                if (!ok) { ++fails; break; }
+                tally[idx(c[0], c[1], c[2])] += 1;
+            }
+        }
+        for (int z = 0; z < L[2]; ++z)
+            for (int y = 0; y < L[1]; ++y)
+                for (int x = 0; x < L[0]; ++x) {
+                    const int c[3] = {x, y, z};
+                    const bool cand = adj_edge_candidate(c, o, k);
+                    if (tally[idx(x, y, z)] != (cand ? 1 : 0)) ++fails;
+                    bool needs = false;  // a wall ghost or a particle node among the neighbours
+                    for (int i = 1; i < 19 && !needs; ++i) {
+                        int q[3] = {x + cxv(i), y + cyv(i), z + czv(i)};
+                        bool ghost = false;
+                        for (int a = 0; a < 3; ++a)
+                            if (q[a] < 0 || q[a] >= L[a]) {
+                                if (W[a]) ghost = true;
+                                else q[a] = (q[a] + L[a]) % L[a];
+                            }
+                        needs = ghost || scan[idx(q[0], q[1], q[2])];
+                    }
+                    if (needs && !cand) ++fails;
+                }
+    }
 
     // 3. the candidate grid reaches every near tile exactly once
     std::vector<int> hits((size_t)k.gx * k.gy * k.lz, 0);

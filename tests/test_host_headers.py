@@ -4,7 +4,7 @@ The programs include the library's headers and run the helpers the
 kernels call, on random lattices, wall flags, radii and positions, against a
 brute-force scan of the lattice:
 
-* tests/host_tiles.cu (box_origin, box_node_inside, tile_near,
+* tests/host_tiles.cu (box_origin, box_node_inside, tile_near, adj_edge_candidate, adj_edge_node,
   candidate_tile, make_kparams, both tile policies): the particle box holds
   exactly the sphere's nodes, every fluid node next to the sphere is in a
   near tile, and the near launch reaches every near tile exactly once;
