@@ -1188,14 +1188,12 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     ka_lpsi_shell<<<nbs, kT, 0, st>>>(b.lgf, b.lpsi, s0, m0, k);
     if (int rc = acheck(h, "ka_lpsi_shell")) return rc;
     ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
-    // The particle-adjoint reduction (side) and the a_l of fluid nodes
-    // (handle's stream) read and write disjoint data.
+    // The a_l of the edge candidates (side stream) and of the other fluid
+    // nodes, then the particle-adjoint reduction (handle's stream): disjoint
+    // nodes, and the reduction writes nothing the final passes read.
     ACK(h, cudaEventRecord(h->fork_ev, st));
     ACK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
-    ka_reduce<<<1, kT, 0, h->side>>>(b.adj, b.parts, h->ntiles, b.parts2, h->box_blocks);
-    if (int rc = acheck(h, "ka_reduce")) return rc;
     {
-        // The edge candidates on the side stream after the reduction (disjoint nodes).
         const long long ne = adj_edge_entries(k);
         if (ne > 0) {
             ka_final_edge<<<(unsigned)((ne + kT - 1) / kT), kT, 0, h->side>>>(L0, b.lgf, b.lpsi, s0, m0, k);
@@ -1205,6 +1203,8 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     ACK(h, cudaEventRecord(h->join_ev, h->side));
     ka_final<<<h->grid, h->block, 0, st>>>(L0, b.lgf, b.lpsi, s0, m0, k);
     if (int rc = acheck(h, "ka_final")) return rc;
+    ka_reduce<<<1, kT, 0, st>>>(b.adj, b.parts, h->ntiles, b.parts2, h->box_blocks);
+    if (int rc = acheck(h, "ka_reduce")) return rc;
     ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
     return FLBM_OK;
 }
