@@ -201,6 +201,7 @@ struct KParams {
     int has_particle;
     int B;                 // side of the particle box
     double R;              // sphere radius
+    double inv_mp, inv_Ip; // 1 / m_p and 1 / I_p of the particle (0 without one)
     double rho0[2];        // initial densities (fallback for an uncovered node with no fluid neighbour)
     int counterforce;
 };

@@ -104,6 +104,12 @@ inline void make_kparams(const flbm_params& p, int tile_policy, KParams& k)
     k.has_particle = p.radius > 0.0 ? 1 : 0;
     k.B = k.has_particle ? (int)std::ceil(2.0 * p.radius) + 2 : 1;
     k.R = p.radius;
+    if (k.has_particle) {  // the mass and moment of inertia of initial_state
+        const double vol = 4.0 / 3.0 * M_PI * p.radius * p.radius * p.radius;
+        const double mp = vol * (p.rho_p_ratio * (p.rho_a0 + p.rho_b0));
+        k.inv_mp = 1.0 / mp;
+        k.inv_Ip = 1.0 / (0.4 * mp * p.radius * p.radius);
+    }
     k.rho0[0] = p.rho_a0; k.rho0[1] = p.rho_b0;
     k.counterforce = p.fluid_counterforce;
     // Candidate tiles that can meet the particle box grown by one node.

@@ -546,29 +546,43 @@ __device__ __forceinline__ void update_particle(DevState* __restrict__ st, const
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[k] += __ldcg(partials + c * 8 + k);
     block_sum8<256>(acc, s_red, s_out);
-    if (tid != 0) return;
-    const int L[3] = {P.lx, P.ly, P.lz};
-    for (int a = 0; a < 3; ++a) {
-        st->F[a] = s_out[a] + st->Ppend[a];
-        st->T[a] = s_out[3 + a] + st->Lpend[a];
+    // One thread per axis: the three components are independent. FP64 on a
+    // part whose FP64 is slow, so products with 1 / m_p and 1 / I_p, and the
+    // periodic wrap as a conditional shift (floor only for a longer step).
+    const int a = tid;
+    if (a >= 3) return;
+    const int L = a == 0 ? P.lx : (a == 1 ? P.ly : P.lz);
+    const double F = s_out[a] + st->Ppend[a];
+    const double T = s_out[3 + a] + st->Lpend[a];
+    st->F[a] = F;
+    st->T[a] = T;
+    const double ext = (a == 2) ? st->Fp : 0.0;
+    const double v0 = st->V[a];
+    const double vn = v0 + (F + ext) * P.inv_mp;
+    st->Vavg[a] = 0.5 * (v0 + vn);
+    st->V[a] = vn;
+    const double om = st->Om[a] + T * P.inv_Ip;
+    st->Om[a] = om;
+    st->Vf[a] = (float)vn;
+    st->Omf[a] = (float)om;
+    double xn = st->X[a] + vn;
+    if (!P.wall[a]) {
+        if (xn >= L) xn -= L;
+        else if (xn < 0.0) xn += L;
+        if (xn >= L || xn < 0.0) xn -= L * floor(xn / L);
     }
-    for (int a = 0; a < 3; ++a) {
-        const double ext = (a == 2) ? st->Fp : 0.0;
-        const double vn = st->V[a] + (st->F[a] + ext) / st->mp;
-        st->Vavg[a] = 0.5 * (st->V[a] + vn);
-        st->V[a] = vn;
-        st->Om[a] += st->T[a] / st->Ip;
-        st->Vf[a] = (float)st->V[a];
-        st->Omf[a] = (float)st->Om[a];
-        double xn = st->X[a] + vn;
-        if (!P.wall[a]) xn -= L[a] * floor(xn / L[a]);
-        st->X[a] = xn;
+    st->X[a] = xn;
+    if (a == 0) {
+        st->ledger_bb[0] = s_out[6];
+        st->ledger_bb[1] = s_out[7];
     }
-    st->ledger_bb[0] = s_out[6];
-    st->ledger_bb[1] = s_out[7];
-    int o[3];
-    box_origin(st->X, P, o);
-    st->box_next[0] = o[0]; st->box_next[1] = o[1]; st->box_next[2] = o[2];
+    // box_origin of the new position, this axis.
+    int o = (int)floor(xn - P.R);
+    if (!P.wall[a]) {
+        o %= L;
+        if (o < 0) o += L;
+    }
+    st->box_next[a] = o;
 }
 
 // (2) Particle nodes at the new position -> mask[1 - cur]; per-block counts.
