@@ -619,6 +619,18 @@ static __global__ void __launch_bounds__(256) k_mark_next(const DevState* __rest
 
 // (3) Cover (new box) and uncover (old box) on the post-stream populations f;
 // per-block FP64 partials of impulse, angular impulse and mass ledger.
+// Exact FP64 sum of the 19 float populations of component l at node m
+// (exact: populations are floats of similar magnitude, so every partial sum
+// fits in a double and the order does not matter); four chains to shorten
+// the dependent FP64 additions, which are slow on this part.
+__device__ __forceinline__ double pop_sum(const float* __restrict__ f, int l, long long m, long long N)
+{
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < 19; ++i) s4[i & 3] += (double)f[(long long)(19 * l + i) * N + m];
+    return (s4[0] + s4[1]) + (s4[2] + s4[3]);
+}
+
 __device__ __forceinline__ void cover_block(int blk, float* __restrict__ f, const DevState* __restrict__ st,
                                             const uint8_t* __restrict__ masks, double* __restrict__ parts,
                                             const KParams& P)
@@ -628,6 +640,7 @@ __device__ __forceinline__ void cover_block(int blk, float* __restrict__ f, cons
     const int B = P.B;
     const int B3 = B * B * B;
     const int t = blk * 256 + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const int cur = st->cur;
     const int o_old[3] = {st->box0[0], st->box0[1], st->box0[2]};
     const int o_new[3] = {st->box_next[0], st->box_next[1], st->box_next[2]};
@@ -636,6 +649,8 @@ __device__ __forceinline__ void cover_block(int blk, float* __restrict__ f, cons
     const int L[3] = {P.lx, P.ly, P.lz};
     const long long N = P.N;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    bool uncovered = false;
+    int cu_[3] = {0, 0, 0};  // an uncovered node of this thread
     if (t < B3) {
         const int d[3] = {t % B, (t / B) % B, t / (B * B)};
         if (m_new[t]) {  // covered: particle node now, fluid before
@@ -646,13 +661,19 @@ __device__ __forceinline__ void cover_block(int blk, float* __restrict__ f, cons
             }
             if (!is_solid(c[0], c[1], c[2], o_old, m_old, P)) {
                 const long long n = c[0] + (long long)P.lx * (c[1] + (long long)P.ly * c[2]);
-                double j[3] = {0, 0, 0}, rl[2] = {0, 0};
+                double j4[3][4] = {}, r4[2][4] = {};  // exact sums in four chains
                 for (int l = 0; l < 2; ++l)
+#pragma unroll
                     for (int i = 0; i < 19; ++i) {
                         const double fv = f[(long long)(19 * l + i) * N + n];
-                        rl[l] += fv;
-                        j[0] += fv * cxv(i); j[1] += fv * cyv(i); j[2] += fv * czv(i);
+                        r4[l][i & 3] += fv;
+                        if (cxv(i)) j4[0][i & 3] += cxv(i) > 0 ? fv : -fv;
+                        if (cyv(i)) j4[1][i & 3] += cyv(i) > 0 ? fv : -fv;
+                        if (czv(i)) j4[2][i & 3] += czv(i) > 0 ? fv : -fv;
                     }
+                double j[3], rl[2];
+                for (int a = 0; a < 3; ++a) j[a] = (j4[a][0] + j4[a][1]) + (j4[a][2] + j4[a][3]);
+                for (int l = 0; l < 2; ++l) rl[l] = (r4[l][0] + r4[l][1]) + (r4[l][2] + r4[l][3]);
                 double r[3];
                 for (int a = 0; a < 3; ++a) r[a] = rel_axis((double)c[a], st->X[a], L[a], P.wall[a]);
                 acc[0] += j[0]; acc[1] += j[1]; acc[2] += j[2];
@@ -664,59 +685,73 @@ __device__ __forceinline__ void cover_block(int blk, float* __restrict__ f, cons
             }
         }
         if (m_old[t]) {  // uncovered: particle node before, fluid now
-            int c[3];
             for (int a = 0; a < 3; ++a) {
-                c[a] = o_old[a] + d[a];
-                if (!P.wall[a] && c[a] >= L[a]) c[a] -= L[a];
+                cu_[a] = o_old[a] + d[a];
+                if (!P.wall[a] && cu_[a] >= L[a]) cu_[a] -= L[a];
             }
-            if (!is_solid(c[0], c[1], c[2], o_new, m_new, P)) {
-                double mean[2] = {0.0, 0.0};
-                int cnt = 0;
-                for (int jd = 1; jd < 19; ++jd) {
-                    int q[3] = {c[0] + cxv(jd), c[1] + cyv(jd), c[2] + czv(jd)};
-                    bool ok = true;
-                    for (int a = 0; a < 3; ++a) {
-                        if (q[a] < 0 || q[a] >= L[a]) {
-                            if (P.wall[a]) ok = false;
-                            else q[a] += (q[a] < 0) ? L[a] : -L[a];
-                        }
-                    }
-                    if (!ok) continue;
-                    if (is_solid(q[0], q[1], q[2], o_new, m_new, P)) continue;
-                    if (is_solid(q[0], q[1], q[2], o_old, m_old, P)) continue;  // uncovered too
-                    const long long m = q[0] + (long long)P.lx * (q[1] + (long long)P.ly * q[2]);
-                    for (int l = 0; l < 2; ++l) {
-                        double s = 0.0;
-                        for (int i = 0; i < 19; ++i) s += f[(long long)(19 * l + i) * N + m];
-                        mean[l] += s;
-                    }
-                    ++cnt;
+            uncovered = !is_solid(cu_[0], cu_[1], cu_[2], o_new, m_new, P);
+        }
+    }
+    // Each uncovered node of the warp in turn, by the whole warp: lane j
+    // (1..18) sums the populations of neighbour j, the warp adds them up
+    // (exact sums), and the lanes write the refilled populations.
+    unsigned um = __ballot_sync(0xffffffffu, uncovered);
+    while (um) {
+        const int src = __ffs(um) - 1;
+        um &= um - 1;
+        int c[3];
+        for (int a = 0; a < 3; ++a) c[a] = __shfl_sync(0xffffffffu, cu_[a], src);
+        double m0 = 0.0, m1 = 0.0;
+        int one = 0;
+        if (lane >= 1 && lane <= 18) {
+            int q[3] = {c[0] + cxv(lane), c[1] + cyv(lane), c[2] + czv(lane)};
+            bool ok = true;
+            for (int a = 0; a < 3; ++a) {
+                if (q[a] < 0 || q[a] >= L[a]) {
+                    if (P.wall[a]) ok = false;
+                    else q[a] += (q[a] < 0) ? L[a] : -L[a];
                 }
-                // neighbour-mean densities; the initial densities if no fluid neighbour is left
-                const double rls[2] = {cnt ? mean[0] / cnt : P.rho0[0], cnt ? mean[1] / cnt : P.rho0[1]};
-                double r[3];
-                for (int a = 0; a < 3; ++a) r[a] = rel_axis((double)c[a], st->X[a], L[a], P.wall[a]);
-                const double ub[3] = {st->V[0] + st->Om[1] * r[2] - st->Om[2] * r[1],
-                                      st->V[1] + st->Om[2] * r[0] - st->Om[0] * r[2],
-                                      st->V[2] + st->Om[0] * r[1] - st->Om[1] * r[0]};
-                const long long n = c[0] + (long long)P.lx * (c[1] + (long long)P.ly * c[2]);
-                const double uu = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
-                double pm[3] = {0, 0, 0};
-                for (int l = 0; l < 2; ++l) {
-                    for (int i = 0; i < 19; ++i) {
-                        const double cu = ub[0] * cxv(i) + ub[1] * cyv(i) + ub[2] * czv(i);
-                        f[(long long)(19 * l + i) * N + n] =
-                            (float)(wv(i) * rls[l] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
-                    }
-                    pm[0] += rls[l] * ub[0]; pm[1] += rls[l] * ub[1]; pm[2] += rls[l] * ub[2];
-                }
-                acc[0] -= pm[0]; acc[1] -= pm[1]; acc[2] -= pm[2];
-                acc[3] -= r[1] * pm[2] - r[2] * pm[1];
-                acc[4] -= r[2] * pm[0] - r[0] * pm[2];
-                acc[5] -= r[0] * pm[1] - r[1] * pm[0];
-                acc[6] -= rls[0];
-                acc[7] -= rls[1];
             }
+            // a fluid neighbour that was fluid before as well
+            if (ok && !is_solid(q[0], q[1], q[2], o_new, m_new, P) && !is_solid(q[0], q[1], q[2], o_old, m_old, P)) {
+                const long long m = q[0] + (long long)P.lx * (q[1] + (long long)P.ly * q[2]);
+                m0 = pop_sum(f, 0, m, N);
+                m1 = pop_sum(f, 1, m, N);
+                one = 1;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            m0 += __shfl_xor_sync(0xffffffffu, m0, off);
+            m1 += __shfl_xor_sync(0xffffffffu, m1, off);
+            one += __shfl_xor_sync(0xffffffffu, one, off);
+        }
+        const int cnt = one;
+        // neighbour-mean densities; the initial densities if no fluid neighbour is left
+        const double rls[2] = {cnt ? m0 / cnt : P.rho0[0], cnt ? m1 / cnt : P.rho0[1]};
+        double r[3];
+        for (int a = 0; a < 3; ++a) r[a] = rel_axis((double)c[a], st->X[a], L[a], P.wall[a]);
+        const double ub[3] = {st->V[0] + st->Om[1] * r[2] - st->Om[2] * r[1],
+                              st->V[1] + st->Om[2] * r[0] - st->Om[0] * r[2],
+                              st->V[2] + st->Om[0] * r[1] - st->Om[1] * r[0]};
+        const long long n = c[0] + (long long)P.lx * (c[1] + (long long)P.ly * c[2]);
+        const double uu = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+        for (int q = lane; q < 38; q += 32) {  // population (l, i) = (q / 19, q % 19)
+            const int l = q / 19, i = q % 19;
+            const double cu = ub[0] * cxv(i) + ub[1] * cyv(i) + ub[2] * czv(i);
+            f[(long long)q * N + n] = (float)(wv(i) * rls[l] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+        }
+        if (lane == src) {
+            double pm[3] = {0, 0, 0};
+            for (int l = 0; l < 2; ++l) {
+                pm[0] += rls[l] * ub[0]; pm[1] += rls[l] * ub[1]; pm[2] += rls[l] * ub[2];
+            }
+            acc[0] -= pm[0]; acc[1] -= pm[1]; acc[2] -= pm[2];
+            acc[3] -= r[1] * pm[2] - r[2] * pm[1];
+            acc[4] -= r[2] * pm[0] - r[0] * pm[2];
+            acc[5] -= r[0] * pm[1] - r[1] * pm[0];
+            acc[6] -= rls[0];
+            acc[7] -= rls[1];
         }
     }
     block_sum8<256>(acc, s_red, s_out);
@@ -755,7 +790,7 @@ __device__ __forceinline__ void finish_step(DevState* __restrict__ st, const int
 {
     __shared__ double s_red[(256 / 32) * 8];
     __shared__ double s_out[8];
-    __shared__ long long s_c[256];
+    __shared__ long long s_c[256 / 32];
     if (!P.has_particle) {
         if (threadIdx.x == 0) {
             st->step += 1;
@@ -770,23 +805,31 @@ __device__ __forceinline__ void finish_step(DevState* __restrict__ st, const int
         for (int k = 0; k < 8; ++k) acc[k] += __ldcg(parts + b * 8 + k);
         cnt += __ldcg(counts + b);
     }
-    s_c[threadIdx.x] = cnt;
-    block_sum8<256>(acc, s_red, s_out);
-    if (threadIdx.x != 0) return;
+    // Particle nodes: an integer sum, the same in any order.
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+    if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = cnt;
+    block_sum8<256>(acc, s_red, s_out);  // its barriers also publish s_c
+    // Threads 0, 1, 2 form delta_A, delta_B and the counterforce at once
+    // (FP64 divisions are slow here); thread 0 also the rest.
+    if (threadIdx.x >= 3) return;
     long long solid = 0;
-    for (int k = 0; k < (int)blockDim.x; ++k) solid += s_c[k];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) solid += s_c[w];
+    const long long nf = P.N - solid;
+    if (threadIdx.x < 2) {
+        const int l = threadIdx.x;
+        st->delta[l] = (st->ledger_bb[l] + s_out[6 + l]) / (double)nf;
+        st->delta_f[l] = (float)st->delta[l];
+    } else {
+        st->fc = P.counterforce ? -st->Fp / (double)nf : 0.0;
+        st->fc_f = (float)st->fc;
+    }
+    if (threadIdx.x != 0) return;
     for (int a = 0; a < 3; ++a) {
         st->Ppend[a] = s_out[a];
         st->Lpend[a] = s_out[3 + a];
     }
-    const long long nf = P.N - solid;
     st->nfluid = nf;
-    st->delta[0] = (st->ledger_bb[0] + s_out[6]) / (double)nf;
-    st->delta[1] = (st->ledger_bb[1] + s_out[7]) / (double)nf;
-    st->delta_f[0] = (float)st->delta[0];
-    st->delta_f[1] = (float)st->delta[1];
-    st->fc = P.counterforce ? -st->Fp / (double)nf : 0.0;
-    st->fc_f = (float)st->fc;
     st->box_prev[0] = st->box0[0]; st->box_prev[1] = st->box0[1]; st->box_prev[2] = st->box0[2];
     st->box0[0] = st->box_next[0]; st->box0[1] = st->box_next[1]; st->box0[2] = st->box_next[2];
     st->cur = 1 - st->cur;
