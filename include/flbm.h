@@ -373,6 +373,10 @@ typedef struct flbm_adjoint_result {
  * trajectory. On return h has advanced T steps, exactly as flbm_step(h, T)
  * would leave it. The paper computes no gradients; this differentiates its
  * noise-free method.
+ * The repeated step sequences of the forward run and of the recomputes
+ * are replayed as CUDA graphs (two-pass density mode); on a handle whose
+ * stream is the legacy default stream, which graphs cannot capture, the
+ * call runs on a private stream ordered after and before the handle's.
  * Requires a particle (radius > 0), kT = 0, every relaxation time 1 and
  * fluid_counterforce = 0: FLBM_E_UNSUPPORTED otherwise. Synchronises.
  * Errors: FLBM_E_INVAL, FLBM_E_UNSUPPORTED, FLBM_E_NOMEM, FLBM_E_CUDA. */

@@ -384,6 +384,7 @@ namespace flbm {
 int sim_step(flbm_sim* h, cudaEvent_t* ev) { return launch_step(h, ev); }
 int sim_fail(flbm_sim* h, int code, const std::string& msg) { return fail(h, code, msg); }
 int sim_ensure_psi(flbm_sim* h) { return ensure_psi(h); }
+bool sim_fused(const flbm_sim* h) { return use_fused(h); }
 }  // namespace flbm
 
 extern "C" {

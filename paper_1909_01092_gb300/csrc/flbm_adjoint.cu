@@ -1105,6 +1105,53 @@ int acheck(flbm_sim* h, const char* what)
         if (e_ != cudaSuccess) return sim_fail((h), FLBM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// CUDA graphs of the run's repeated sequences of kAdjGraph steps: forward
+// steps, each followed by the J sum, and recompute steps, each preceded by
+// the tape writes of its slot (slots j kAdjGraph .. (j + 1) kAdjGraph - 1 of
+// the segment). One per starting population copy (cur) and, for the
+// recompute, per chunk j; captured on first use and replayed for every later
+// chunk and segment. kAdjGraph is even, so a replay leaves cur where it was.
+constexpr int kAdjGraph = 8;
+
+struct AdjGraphs {
+    cudaGraphExec_t fwd[2] = {nullptr, nullptr};
+    std::vector<cudaGraphExec_t> rec[2];
+    ~AdjGraphs()
+    {
+        for (int c = 0; c < 2; ++c) {
+            if (fwd[c]) cudaGraphExecDestroy(fwd[c]);
+            for (cudaGraphExec_t g : rec[c])
+                if (g) cudaGraphExecDestroy(g);
+        }
+    }
+};
+
+// Capture what body() launches on h's stream into *out (nothing runs).
+template <class Body>
+int capture_graph(flbm_sim* h, cudaGraphExec_t* out, Body body)
+{
+    const int c = h->cur;
+    const int64_t before = h->launches;
+    ACK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = body();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->launches = before;
+    h->cur = c;
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return sim_fail(h, FLBM_E_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        *out = nullptr;
+        return sim_fail(h, FLBM_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+    }
+    return FLBM_OK;
+}
+
 // Copy the handle's state (current populations, particle record, masks) to or from a slot.
 // The state a step reads: populations, particle record, masks and the
 // density field (so that a recomputed segment repeats the forward run bit
@@ -1235,6 +1282,39 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
         !b.alloc(b.parts, (size_t)h->ntiles * kNodeParts) || !b.alloc(b.parts2, (size_t)h->box_blocks) ||
         !b.alloc(b.cparts, (size_t)h->box_blocks * 9) || !b.alloc(b.adj, 1))
         return sim_fail(h, FLBM_E_NOMEM, "adjoint checkpoints and tape");
+    // The step sequences are replayed as CUDA graphs, which the legacy default
+    // stream cannot capture: on that stream the run takes a private stream,
+    // ordered after the handle's stream on entry and before it on exit.
+    struct StreamSwap {
+        flbm_sim* h;
+        cudaStream_t user = nullptr, priv = nullptr;
+        ~StreamSwap()
+        {
+            if (!priv) return;
+            cudaEvent_t e;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+                cudaEventRecord(e, priv);
+                cudaStreamWaitEvent(user, e, 0);
+                cudaEventDestroy(e);
+            } else {
+                cudaStreamSynchronize(priv);
+            }
+            h->stream = user;
+            cudaStreamDestroy(priv);
+        }
+    } swap{h};
+    if (h->stream == nullptr) {
+        cudaEvent_t e;
+        ACK(h, cudaStreamCreateWithFlags(&swap.priv, cudaStreamNonBlocking));
+        ACK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        const cudaError_t r1 = cudaEventRecord(e, h->stream);
+        const cudaError_t r2 = cudaStreamWaitEvent(swap.priv, e, 0);
+        cudaEventDestroy(e);
+        ACK(h, r1);
+        ACK(h, r2);
+        swap.user = h->stream;
+        h->stream = swap.priv;
+    }
     cudaStream_t st = h->stream;
     ACK(h, cudaMemsetAsync(b.adj, 0, sizeof(AdjState), st));
     ACK(h, cudaMemsetAsync(b.lam[0], 0, sizeof(lam_t) * 8 * N, st));
@@ -1249,17 +1329,41 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
         }
     } guard{ev};
     cudaEventRecord(ev[0], st);
+    // Graphs need a stream that can be captured, and the two-pass step (whose
+    // launches do not depend on host state).
+    AdjGraphs ag;
+    const bool graphs = st != nullptr && !sim_fused(h);
+    auto fwd_step = [&]() -> int {
+        if (int rc = sim_step(h)) return rc;
+        ka_accJ<<<1, 1, 0, st>>>(h->st, b.adj);
+        return acheck(h, "ka_accJ");
+    };
     // Forward run: checkpoints every K steps, the sum of Vavg_z.
-    for (int64_t s = 0; s < T; ++s) {
+    for (int64_t s = 0; s < T;) {
         if (s % K == 0) {
             const int64_t c = s / K;
             if (int rc = save_state(h, b.ck_f + c * fN, b.ck_st + c, b.ck_m + c * mbytes, mbytes,
                                     b.ck_psi + c * 2 * k.padn))
                 return rc;
         }
-        if (int rc = sim_step(h)) return rc;
-        ka_accJ<<<1, 1, 0, st>>>(h->st, b.adj);
-        if (int rc = acheck(h, "ka_accJ")) return rc;
+        const int64_t next = std::min<int64_t>(T, (s / K + 1) * K);  // the next checkpoint
+        while (s < next) {
+            if (graphs && next - s >= kAdjGraph) {
+                cudaGraphExec_t& g = ag.fwd[h->cur];
+                if (!g)
+                    if (int rc = capture_graph(h, &g, [&]() -> int {
+                            for (int i = 0; i < kAdjGraph; ++i)
+                                if (int r = fwd_step()) return r;
+                            return FLBM_OK;
+                        }))
+                        return rc;
+                ACK(h, cudaGraphLaunch(g, st));
+                s += kAdjGraph;
+            } else {
+                if (int rc = fwd_step()) return rc;
+                ++s;
+            }
+        }
     }
     if (int rc = save_state(h, b.ck_f + nck * fN, b.ck_st + nck, b.ck_m + nck * mbytes, mbytes,
                             b.ck_psi + nck * 2 * k.padn))
@@ -1276,13 +1380,34 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
         if (int rc = load_state(h, b.ck_f + c * fN, b.ck_st + c, b.ck_m + c * mbytes, mbytes,
                                 b.ck_psi + c * 2 * k.padn))
             return rc;
-        for (int kk = 0; kk <= Ls; ++kk) {
+        // Tape slot kk (moments, particle record, masks of the state), then a step.
+        auto tape_step = [&](int kk, bool step) -> int {
             ka_tape<<<h->grid, h->block, 0, st>>>(h->fbuf[h->cur], b.tape + (size_t)kk * 8 * N, k);
             if (int rc = acheck(h, "ka_tape")) return rc;
             ACK(h, cudaMemcpyAsync(b.tape_st + kk, h->st, sizeof(DevState), cudaMemcpyDeviceToDevice, st));
             ACK(h, cudaMemcpyAsync(b.tape_m + (size_t)kk * mbytes, h->masks, mbytes, cudaMemcpyDeviceToDevice, st));
-            if (kk < Ls)
-                if (int rc = sim_step(h)) return rc;
+            return step ? sim_step(h) : FLBM_OK;
+        };
+        for (int kk = 0; kk <= Ls;) {
+            if (graphs && kk % kAdjGraph == 0 && kk + kAdjGraph <= Ls) {
+                std::vector<cudaGraphExec_t>& v = ag.rec[h->cur];
+                const size_t j = (size_t)(kk / kAdjGraph);
+                if (v.size() <= j) v.resize(j + 1, nullptr);
+                if (!v[j]) {
+                    const int k0 = kk;
+                    if (int rc = capture_graph(h, &v[j], [&]() -> int {
+                            for (int i = 0; i < kAdjGraph; ++i)
+                                if (int r = tape_step(k0 + i, true)) return r;
+                            return FLBM_OK;
+                        }))
+                        return rc;
+                }
+                ACK(h, cudaGraphLaunch(v[j], st));
+                kk += kAdjGraph;
+            } else {
+                if (int rc = tape_step(kk, kk < Ls)) return rc;
+                ++kk;
+            }
         }
         for (int kk = Ls - 1; kk >= 0; --kk) {
             if (int rc = reverse_step(h, b, kk, b.lam[lcur], b.lam[1 - lcur], inv2T, dFp_dg)) return rc;

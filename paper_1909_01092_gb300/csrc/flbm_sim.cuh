@@ -92,4 +92,7 @@ int sim_fail(flbm_sim* h, int code, const std::string& msg);
 // they are stale).
 int sim_ensure_psi(flbm_sim* h);
 
+// Does the next step take the fused path (densities carried from step to step)?
+bool sim_fused(const flbm_sim* h);
+
 }  // namespace flbm
