@@ -350,13 +350,14 @@ def adjoint_bench(binding, W, steps: int = 2000, every: int = 100) -> dict:
     """Gradient of the time-averaged settling velocity on the 64x64x128
     noise-free channel (R=8, delta_rho=0.3, G=1.2) by the adjoint with
     checkpoints every `every` steps, against the plain forward step of the
-    same channel."""
+    same channel replayed as CUDA graphs."""
     import torch
 
     p = W.channel_adjoint()
     nodes = p["lx"] * p["ly"] * p["lz"]
-    fwd = binding.Sim(p)
-    fwd.step(5)
+    fwd = binding.Sim(p, stream=torch.cuda.Stream())  # the fastest plain step: graph replay
+    fwd.use_graphs(True)
+    fwd.step(16)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(fwd.stream)

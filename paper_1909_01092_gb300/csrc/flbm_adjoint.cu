@@ -1116,12 +1116,15 @@ constexpr int kAdjGraph = 8;
 struct AdjGraphs {
     cudaGraphExec_t fwd[2] = {nullptr, nullptr};
     std::vector<cudaGraphExec_t> rec[2];
+    cudaGraphExec_t rev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [lcur][cur], full segments
     ~AdjGraphs()
     {
         for (int c = 0; c < 2; ++c) {
             if (fwd[c]) cudaGraphExecDestroy(fwd[c]);
             for (cudaGraphExec_t g : rec[c])
                 if (g) cudaGraphExecDestroy(g);
+            for (int d = 0; d < 2; ++d)
+                if (rev[c][d]) cudaGraphExecDestroy(rev[c][d]);
         }
     }
 };
@@ -1409,10 +1412,24 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
                 ++kk;
             }
         }
-        for (int kk = Ls - 1; kk >= 0; --kk) {
-            if (int rc = reverse_step(h, b, kk, b.lam[lcur], b.lam[1 - lcur], inv2T, dFp_dg)) return rc;
-            lcur = 1 - lcur;
+        // The reverse sweep of the segment; a full segment's as one graph,
+        // which depends only on the parities of lcur and cur at its start.
+        auto sweep = [&](int lc) -> int {
+            for (int kk = Ls - 1; kk >= 0; --kk) {
+                if (int rc = reverse_step(h, b, kk, b.lam[lc], b.lam[1 - lc], inv2T, dFp_dg)) return rc;
+                lc = 1 - lc;
+            }
+            return FLBM_OK;
+        };
+        if (graphs && Ls == K) {
+            cudaGraphExec_t& g = ag.rev[lcur][h->cur];
+            if (!g)
+                if (int rc = capture_graph(h, &g, [&]() { return sweep(lcur); })) return rc;
+            ACK(h, cudaGraphLaunch(g, st));
+        } else {
+            if (int rc = sweep(lcur)) return rc;
         }
+        if (Ls & 1) lcur = 1 - lcur;
     }
     if (int rc = load_state(h, b.ck_f + nck * fN, b.ck_st + nck, b.ck_m + nck * mbytes, mbytes,
                             b.ck_psi + nck * 2 * k.padn))
