@@ -211,12 +211,28 @@ __host__ __device__ __forceinline__ void shell_node(long long t, float* __restri
         psi[P.padn + dst] = psi[P.padn + src];
         return;
     }
+    // A fluid neighbour of the ghost lies inward across every wall the ghost
+    // is beyond (only 5 directions for a face ghost, 1 for an edge ghost);
+    // it can be a particle node only if the ghost is within the particle box
+    // grown by one node. Same neighbours, same order as a scan of all 18.
+    bool lo[3], hi[3];
+    bool near = P.has_particle != 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = q[a] < 0;
+        hi[a] = q[a] >= L[a];
+        near = near && ranges_meet(q[a], 1, o[a] - 1, P.B + 2, L[a], P.wall[a]);
+    }
     float sa = 0.0f, sb = 0.0f;
     int cnt = 0;
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
-        int r[3] = {q[0] + cxv(j), q[1] + cyv(j), q[2] + czv(j)};
+        const int c[3] = {cxv(j), cyv(j), czv(j)};
         bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ok = ok && !(lo[a] && c[a] != 1) && !(hi[a] && c[a] != -1);
+        if (!ok) continue;
+        int r[3] = {q[0] + c[0], q[1] + c[1], q[2] + c[2]};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             if (r[a] < 0 || r[a] >= L[a]) {
@@ -225,7 +241,7 @@ __host__ __device__ __forceinline__ void shell_node(long long t, float* __restri
             }
         }
         if (!ok) continue;
-        if (P.has_particle && is_solid(r[0], r[1], r[2], o, mask, P)) continue;
+        if (near && is_solid(r[0], r[1], r[2], o, mask, P)) continue;
         const long long pi = pad_index(r[0], r[1], r[2], P);
         sa += psi[pi];
         sb += psi[P.padn + pi];
