@@ -144,7 +144,7 @@ int launch_psi(flbm_sim* h, cudaEvent_t* ev = nullptr)
     if (int rc = launch_check(h, "k_density")) return rc;
     record(h, ev, 1);
     const int nbs = (int)((shell_count(k) + kThreads - 1) / kThreads);
-    const int nbv = k.has_particle ? (k.B * k.B * k.B + kThreads - 1) / kThreads : 0;
+    const int nbv = virtual_blocks(k);
     k_shell_virtual<<<nbs + nbv, kThreads, 0, h->stream>>>(psi, h->st, h->masks, k, nbs);
     if (int rc = launch_check(h, "k_shell_virtual")) return rc;
     record(h, ev, 2);
@@ -261,7 +261,7 @@ int launch_step(flbm_sim* h, cudaEvent_t* ev = nullptr)
     if (int rc = launch_check(h, "k_psi_finish")) return rc;
     record(h, ev, 3);
     const int nbs = (int)((shell_count(k) + kThreads - 1) / kThreads);
-    const int nbv = k.has_particle ? (k.B * k.B * k.B + kThreads - 1) / kThreads : 0;
+    const int nbv = virtual_blocks(k);
     k_shell_virtual<<<nbs + nbv, kThreads, 0, h->stream>>>(psi_next, h->st, h->masks, k, nbs);
     if (int rc = launch_check(h, "k_shell_virtual")) return rc;
     record(h, ev, 4);

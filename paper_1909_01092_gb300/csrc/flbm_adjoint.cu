@@ -1203,7 +1203,7 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     ka_psi_tape<<<h->grid, h->block, 0, h->side>>>(tn, psi_scr, s0, m0, k);
     if (int rc = acheck(h, "ka_psi_tape")) return rc;
     const unsigned nbs = (unsigned)((shell_count(k) + kThreads - 1) / kThreads);
-    const unsigned nbv = (unsigned)((B3 + kThreads - 1) / kThreads);
+    const unsigned nbv = (unsigned)virtual_blocks(k);
     k_shell_virtual<<<nbs + nbv, kThreads, 0, h->side>>>(psi_scr, s0, m0, k, (int)nbs);
     if (int rc = acheck(h, "k_shell_virtual")) return rc;
     ACK(h, cudaEventRecord(h->join_ev, h->side));

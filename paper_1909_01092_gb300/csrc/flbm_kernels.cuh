@@ -252,8 +252,78 @@ __host__ __device__ __forceinline__ void shell_node(long long t, float* __restri
     psi[P.padn + dst] = sb * inv;
 }
 
+// virtual_node's value computed by a warp, one box entry per warp: lane j
+// (1..18) tests and loads neighbour j, so the loads of all neighbours are in
+// flight at once; the values are then added in direction order, exactly as
+// virtual_value adds them (the same floats). Every lane of the warp calls it.
+__device__ __forceinline__ void virtual_node_warp(int t, float* __restrict__ psi, const DevState* __restrict__ st,
+                                                  const uint8_t* __restrict__ masks, const KParams& P)
+{
+    const int B = P.B;
+    if (t >= B * B * B) return;  // the same for the whole warp
+    const uint8_t* mask = masks + (size_t)st->cur * B * B * B;
+    if (!mask[t]) return;
+    const int lane = threadIdx.x & 31;
+    const int o[3] = {st->box0[0], st->box0[1], st->box0[2]};
+    const int d[3] = {t % B, (t / B) % B, t / (B * B)};
+    const int L[3] = {P.lx, P.ly, P.lz};
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        c[a] = o[a] + d[a];
+        if (!P.wall[a] && c[a] >= L[a]) c[a] -= L[a];
+    }
+    float va = 0.0f, vb = 0.0f;
+    bool ok = false;
+    if (lane >= 1 && lane <= 18) {
+        int q[3] = {c[0] + cxv(lane), c[1] + cyv(lane), c[2] + czv(lane)};
+        ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (q[a] < 0 || q[a] >= L[a]) {
+                if (P.wall[a]) ok = false;
+                else q[a] += (q[a] < 0) ? L[a] : -L[a];
+            }
+        }
+        ok = ok && !is_solid(q[0], q[1], q[2], o, mask, P);
+        if (ok) {
+            const long long pi = pad_index(q[0], q[1], q[2], P);
+            va = psi[pi];
+            vb = psi[P.padn + pi];
+        }
+    }
+    const unsigned fl = __ballot_sync(0xffffffffu, ok);
+    float sa = 0.0f, sb = 0.0f;
+#pragma unroll
+    for (int j = 1; j < 19; ++j) {
+        const float a = __shfl_sync(0xffffffffu, va, j), b = __shfl_sync(0xffffffffu, vb, j);
+        if (fl >> j & 1u) {
+            sa += a;
+            sb += b;
+        }
+    }
+    if (lane != 0) return;
+    const int cnt = __popc(fl);
+    float ra = 0.0f, rb = 0.0f;
+    if (cnt) {
+        const float inv = 1.0f / (float)cnt;
+        ra = fmaxf(sa * inv + P.drho, 0.0f);
+        rb = fmaxf(sb * inv - P.drho, 0.0f);
+    }
+    const long long q = pad_index(c[0], c[1], c[2], P);
+    psi[q] = ra;
+    psi[P.padn + q] = rb;
+}
+
+// Blocks of the virtual layer in k_shell_virtual: one box entry per warp.
+__host__ __device__ __forceinline__ int virtual_blocks(const KParams& P)
+{
+    return P.has_particle ? (P.B * P.B * P.B + kThreads / 32 - 1) / (kThreads / 32) : 0;
+}
+
 // Shell and virtual layer in one launch: the first nshell_blocks blocks run
-// the shell, the rest the particle box (no thread reads what another writes).
+// the shell, the rest the particle box (virtual_blocks of them; no thread
+// reads what another writes).
 static __global__ void __launch_bounds__(kThreads) k_shell_virtual(float* __restrict__ psi,
                                                                    const DevState* __restrict__ st,
                                                                    const uint8_t* __restrict__ masks, KParams P,
@@ -262,7 +332,7 @@ static __global__ void __launch_bounds__(kThreads) k_shell_virtual(float* __rest
     if ((int)blockIdx.x < nshell_blocks)
         shell_node(blockIdx.x * (long long)blockDim.x + threadIdx.x, psi, st, masks, P);
     else
-        virtual_node((blockIdx.x - nshell_blocks) * blockDim.x + threadIdx.x, psi, st, masks, P);
+        virtual_node_warp((blockIdx.x - nshell_blocks) * (kThreads / 32) + (threadIdx.x >> 5), psi, st, masks, P);
 }
 
 }  // namespace flbm
