@@ -686,8 +686,10 @@ __device__ __forceinline__ void adj_tile(int bx, int by, int bz, int tx, int ty,
     if (tid < kNodeParts - 8) parts[tile * kNodeParts + 8 + tid] = s_out[tid];
 }
 
-// Tiles away from the particle (all tiles when there is none).
-static __global__ void __launch_bounds__(kT, 2) ka_node_bulk(const float* __restrict__ tape, const float* __restrict__ psi,
+// Tiles away from the particle (all tiles when there is none). Three blocks
+// per SM: a few spills, and more resident warps to hide the neighbour
+// gathers (measured faster than two).
+static __global__ void __launch_bounds__(kT, 3) ka_node_bulk(const float* __restrict__ tape, const float* __restrict__ psi,
                                                           const lam_t* __restrict__ lam1, lam_t* __restrict__ lam0,
                                                           lg_t* __restrict__ lg, const DevState* __restrict__ s0,
                                                           const uint8_t* __restrict__ mk0,
