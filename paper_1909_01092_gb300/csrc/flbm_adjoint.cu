@@ -828,12 +828,43 @@ __device__ __forceinline__ void lpsi_gather_inner(int x, int y, int z, uint32_t 
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint of psi at the particle nodes (one thread per entry of the particle
-// box). A particle node with fluid neighbours (virtual layer) gets lambda
-// psi plus the Shan-Chen reaction's dependence on it, then
+// Adjoint of psi at the particle nodes, one warp per entry of the particle
+// box, lane i = 1..18 taking direction i. A particle node with fluid
+// neighbours (virtual layer) gets lambda psi (lpsi_gather's sum, its sources
+// p - c_i spread over the lanes, the reference the first nonzero source in
+// direction order) plus the Shan-Chen reaction's dependence on it, then
 // mu_l = lambda psi_l / cnt where the clip at 0 is inactive, written at the
-// node's place in lpsi; dJ/d delta_rho partial per block.
+// node's place in lpsi; dJ/d delta_rho partial per block of kLpsiEntries
+// entries. A node without fluid neighbours gets mu = 0.
 // ---------------------------------------------------------------------------
+constexpr int kLpsiEntries = kT / 32;  // box entries per block
+
+__host__ __device__ __forceinline__ int lpsi_blocks(const KParams& P)
+{
+    return (P.B * P.B * P.B + kLpsiEntries - 1) / kLpsiEntries;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__device__ __forceinline__ int warp_sum(int v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
 static __global__ void __launch_bounds__(kT) ka_lpsi(const lg_t* __restrict__ lg, const float* __restrict__ psi,
                                                      double* __restrict__ lpsi, const DevState* __restrict__ s0,
                                                      const uint8_t* __restrict__ mk0, const AdjState* __restrict__ adj,
@@ -842,10 +873,12 @@ static __global__ void __launch_bounds__(kT) ka_lpsi(const lg_t* __restrict__ lg
     __shared__ double s_red[(kT / 32) * 8];
     __shared__ double s_out[8];
     const int B = P.B;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * kLpsiEntries + (threadIdx.x >> 5);
     const uint8_t* m0 = cur_mask(s0, mk0, P);
     double dd = 0.0;
-    if (t < B * B * B && m0[t]) {
+    if (t < B * B * B && m0[t]) {  // the same for every lane of the warp
+        const size_t N = P.N;
         const int L[3] = {P.lx, P.ly, P.lz};
         const int dlt[3] = {t % B, (t / B) % B, t / (B * B)};
         int p[3];
@@ -853,44 +886,88 @@ static __global__ void __launch_bounds__(kT) ka_lpsi(const lg_t* __restrict__ lg
             p[a] = s0->box0[a] + dlt[a];
             if (!P.wall[a] && p[a] >= L[a]) p[a] -= L[a];
         }
-        const int x = p[0], y = p[1], z = p[2];
-        double lp[2];
-        lpsi_gather(p, lg, P, lp);
-        const long long pi = pad_index(x, y, z, P);
-        {
-            const int cnt = fluid_count(p, s0, m0, P);
-            double mu[2] = {0.0, 0.0};
-            if (cnt) {
+        const long long pi = pad_index(p[0], p[1], p[2], P);
+        const bool dir = lane >= 1 && lane <= 18;
+        const int c[3] = {cxv(lane), cyv(lane), czv(lane)};
+        // q = p - c_i: a source of the stencil transposed and, if fluid, a
+        // fluid neighbour reading psi(p) along +c_i.
+        int q[3];
+        const bool inq = dir && nbr(p[0], p[1], p[2], -c[0], -c[1], -c[2], P, q);
+        const bool fluid = inq && !solid_at(q[0], q[1], q[2], s0, m0, P);
+        const int cnt = __popc(__ballot_sync(0xffffffffu, fluid));
+        double mu[2] = {0.0, 0.0};
+        if (cnt) {
+            // lpsi_gather: sources whose lambda g is zero (particle nodes) add
+            // nothing; the others as float differences from the first of them
+            // (r), plus r sum w_i c_i over them in FP64.
+            Split v[6];
+            bool nz = false;
+            if (inq) {
+                const uint32_t sidx = lin(q[0], q[1], q[2], P);
+                for (int k = 0; k < 6; ++k) {
+                    v[k] = lg[k * N + sidx];
+                    nz = nz || v[k].hi != 0.0f || v[k].lo != 0.0f;
+                }
+            } else {
+                for (int k = 0; k < 6; ++k) v[k] = Split{0.0f, 0.0f};
+            }
+            const unsigned nzm = __ballot_sync(0xffffffffu, nz);
+            double lp[2] = {0.0, 0.0};
+            if (nzm) {
+                const int f = __ffs(nzm) - 1;
+                Split r[6];
+                for (int k = 0; k < 6; ++k) {
+                    r[k].hi = __shfl_sync(0xffffffffu, v[k].hi, f);
+                    r[k].lo = __shfl_sync(0xffffffffu, v[k].lo, f);
+                }
+                float la = 0.0f, lb = 0.0f;
+                int nc[3] = {0, 0, 0};
+                if (nz) {
+                    const int wt = lane <= 6 ? 2 : 1;  // w_i in units of 1/36
+                    const float w = wv(lane);
+                    for (int a = 0; a < 3; ++a) {
+                        if (!c[a]) continue;
+                        nc[a] = wt * c[a];
+                        lb += w * c[a] * sdiff(v[a], r[a]);
+                        la += w * c[a] * sdiff(v[3 + a], r[3 + a]);
+                    }
+                }
+                lp[0] = warp_sum(la);
+                lp[1] = warp_sum(lb);
+                for (int a = 0; a < 3; ++a) {
+                    const int n = warp_sum(nc[a]);
+                    if (n) {
+                        lp[1] += sval(r[a]) * (n * (1.0 / 36.0));
+                        lp[0] += sval(r[3 + a]) * (n * (1.0 / 36.0));
+                    }
+                }
+            }
+            // The Shan-Chen reaction on the particle through psi(p).
+            double ra = 0.0, rb = 0.0;
+            if (fluid) {
                 const float* lF = adj->lFf;
                 const float* lT = adj->lTf;
-                for (int i = 1; i < 19; ++i) {  // fluid x = p - c_i reads psi(p) along +c_i
-                    int q[3];
-                    if (!nbr(x, y, z, -cxv(i), -cyv(i), -czv(i), P, q)) continue;
-                    if (solid_at(q[0], q[1], q[2], s0, m0, P)) continue;
-                    const int cx = cxv(i), cy = cyv(i), cz = czv(i);
-                    float d[3];
-                    for (int a = 0; a < 3; ++a) {
-                        const int c = q[a];
-                        const int L = a == 0 ? P.lx : (a == 1 ? P.ly : P.lz);
-                        const float cc = a == 0 ? cx : (a == 1 ? cy : cz);
-                        d[a] = (float)rel_axis((double)c, s0->X[a], L, P.wall[a]) + 0.5f * cc;
-                    }
-                    const float kap = cx * (lF[0] + lT[1] * d[2] - lT[2] * d[1]) +
-                                      cy * (lF[1] + lT[2] * d[0] - lT[0] * d[2]) +
-                                      cz * (lF[2] + lT[0] * d[1] - lT[1] * d[0]);
-                    const long long qi = pad_index(q[0], q[1], q[2], P);
-                    lp[1] += double(kap * P.G * wv(i) * psi[qi]);           // d/d psiB(p) of rhoA(q) psiB(p)
-                    lp[0] += double(kap * P.G * wv(i) * psi[P.padn + qi]);  // d/d psiA(p) of rhoB(q) psiA(p)
-                }
-                const bool actA = psi[pi] > 0.0f, actB = psi[P.padn + pi] > 0.0f;
-                if (actA) { mu[0] = lp[0] / double(cnt); dd += lp[0]; }
-                if (actB) { mu[1] = lp[1] / double(cnt); dd -= lp[1]; }
+                float d[3];
+                for (int a = 0; a < 3; ++a) d[a] = (float)rel_axis((double)q[a], s0->X[a], L[a], P.wall[a]) + 0.5f * c[a];
+                const float kap = c[0] * (lF[0] + lT[1] * d[2] - lT[2] * d[1]) +
+                                  c[1] * (lF[1] + lT[2] * d[0] - lT[0] * d[2]) +
+                                  c[2] * (lF[2] + lT[0] * d[1] - lT[1] * d[0]);
+                const long long qi = pad_index(q[0], q[1], q[2], P);
+                rb = double(kap * P.G * wv(lane) * psi[qi]);           // d/d psiB(p) of rhoA(q) psiB(p)
+                ra = double(kap * P.G * wv(lane) * psi[P.padn + qi]);  // d/d psiA(p) of rhoB(q) psiA(p)
             }
+            lp[0] += warp_sum(ra);
+            lp[1] += warp_sum(rb);
+            const bool actA = psi[pi] > 0.0f, actB = psi[P.padn + pi] > 0.0f;
+            if (actA) { mu[0] = lp[0] / double(cnt); dd += lp[0]; }
+            if (actB) { mu[1] = lp[1] / double(cnt); dd -= lp[1]; }
+        }
+        if (lane == 0) {
             lpsi[pi] = mu[0];
             lpsi[P.padn + pi] = mu[1];
         }
     }
-    double v8[8] = {dd, 0, 0, 0, 0, 0, 0, 0};
+    double v8[8] = {lane == 0 ? dd : 0.0, 0, 0, 0, 0, 0, 0, 0};
     block_sum8<kT>(v8, s_red, s_out);
     if (threadIdx.x == 0) parts2[blockIdx.x] = s_out[0];
 }
@@ -1088,9 +1165,18 @@ struct AdjBuffers {
         p = static_cast<T*>(v);
         return true;
     }
+    // Orderings between the two streams of a reverse step's last stages.
+    cudaEvent_t ev_lpsi = nullptr, ev_shell = nullptr;
+    bool make_events()
+    {
+        return cudaEventCreateWithFlags(&ev_lpsi, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&ev_shell, cudaEventDisableTiming) == cudaSuccess;
+    }
     ~AdjBuffers()
     {
         for (void* v : owned) cudaFree(v);
+        if (ev_lpsi) cudaEventDestroy(ev_lpsi);
+        if (ev_shell) cudaEventDestroy(ev_shell);
     }
 };
 
@@ -1230,21 +1316,20 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     ka_node_bulk<<<h->grid, h->block, 0, st>>>(tn, psi_scr, L1, L0, b.lgf, s0, m0, b.adj, b.parts, k);
     if (int rc = acheck(h, "ka_node_bulk")) return rc;
     ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
-    // psi adjoint at particle nodes (side) and at wall ghosts (handle's
-    // stream): disjoint points of lpsi, joined before ka_final.
+    // The psi adjoint at particle nodes (side stream), then the a_l of the
+    // edge candidates, which read it and the wall ghosts' (side, after the
+    // handle's stream has those); on the handle's stream the wall ghosts, the
+    // a_l of the other fluid nodes (which read no psi adjoint) and, once the
+    // particle nodes' partials are in, the particle-adjoint reduction.
     ACK(h, cudaEventRecord(h->fork_ev, st));
     ACK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
-    ka_lpsi<<<h->box_blocks, kT, 0, h->side>>>(b.lgf, psi_scr, b.lpsi, s0, m0, b.adj, b.parts2, k);
+    ka_lpsi<<<lpsi_blocks(k), kT, 0, h->side>>>(b.lgf, psi_scr, b.lpsi, s0, m0, b.adj, b.parts2, k);
     if (int rc = acheck(h, "ka_lpsi")) return rc;
-    ACK(h, cudaEventRecord(h->join_ev, h->side));
+    ACK(h, cudaEventRecord(b.ev_lpsi, h->side));
     ka_lpsi_shell<<<nbs, kT, 0, st>>>(b.lgf, b.lpsi, s0, m0, k);
     if (int rc = acheck(h, "ka_lpsi_shell")) return rc;
-    ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
-    // The a_l of the edge candidates (side stream) and of the other fluid
-    // nodes, then the particle-adjoint reduction (handle's stream): disjoint
-    // nodes, and the reduction writes nothing the final passes read.
-    ACK(h, cudaEventRecord(h->fork_ev, st));
-    ACK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+    ACK(h, cudaEventRecord(b.ev_shell, st));
+    ACK(h, cudaStreamWaitEvent(h->side, b.ev_shell, 0));
     {
         const long long ne = adj_edge_entries(k);
         if (ne > 0) {
@@ -1255,7 +1340,8 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     ACK(h, cudaEventRecord(h->join_ev, h->side));
     ka_final<<<h->grid, h->block, 0, st>>>(L0, b.lgf, b.lpsi, s0, m0, k);
     if (int rc = acheck(h, "ka_final")) return rc;
-    ka_reduce<<<1, kT, 0, st>>>(b.adj, b.parts, h->ntiles, b.parts2, h->box_blocks);
+    ACK(h, cudaStreamWaitEvent(st, b.ev_lpsi, 0));
+    ka_reduce<<<1, kT, 0, st>>>(b.adj, b.parts, h->ntiles, b.parts2, lpsi_blocks(k));
     if (int rc = acheck(h, "ka_reduce")) return rc;
     ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
     return FLBM_OK;
@@ -1284,9 +1370,10 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
         !b.alloc(b.tape_st, (size_t)(K + 1)) || !b.alloc(b.tape_m, (size_t)(K + 1) * mbytes) ||
         !b.alloc(b.lam[0], 8 * N) || !b.alloc(b.lam[1], 8 * N) || !b.alloc(b.lgf, 6 * N) ||
         !b.alloc(b.lpsi, (size_t)(2 * k.padn)) || !b.alloc(b.uv, 2 * B3) ||
-        !b.alloc(b.parts, (size_t)h->ntiles * kNodeParts) || !b.alloc(b.parts2, (size_t)h->box_blocks) ||
+        !b.alloc(b.parts, (size_t)h->ntiles * kNodeParts) || !b.alloc(b.parts2, (size_t)lpsi_blocks(h->kp)) ||
         !b.alloc(b.cparts, (size_t)h->box_blocks * 9) || !b.alloc(b.adj, 1))
         return sim_fail(h, FLBM_E_NOMEM, "adjoint checkpoints and tape");
+    if (!b.make_events()) return sim_fail(h, FLBM_E_CUDA, "adjoint events");
     // The step sequences are replayed as CUDA graphs, which the legacy default
     // stream cannot capture: on that stream the run takes a private stream,
     // ordered after the handle's stream on entry and before it on exit.
