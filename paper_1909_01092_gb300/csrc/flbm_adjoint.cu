@@ -56,6 +56,7 @@ struct AdjState {
     double grad[3];                                    // dJ/dg, dJ/d delta_rho, dJ/dG
     double J;                                          // sum of Vavg_z over the forward steps
     float lFf[3], lTf[3], lledf[2], lPf[3], lLf[3];    // float copies for the node kernels
+    unsigned red_done;                                 // blocks of ka_reduce done (last-block ticket)
 };
 
 // Precision. The adjoint fields carry large smooth parts (the adjoints of
@@ -1099,34 +1100,57 @@ static __global__ void __launch_bounds__(kT) ka_final_edge(lam_t* __restrict__ l
 // Per-tile partials -> adjoint of step n's particle state and the gradient
 // sums. One block: each thread sums a fixed stride of tiles, then a fixed
 // reduction tree (deterministic).
+// Blocks of ka_reduce: each sums a fixed range of the tiles' partials (and of
+// the particle box's), so the FP64 additions spread over several SMs; the
+// last block to finish adds the blocks' sums in block order.
+constexpr int kRedBlocks = 16;
+constexpr int kRedSums = kNodeParts + 1;
+
+__host__ __device__ __forceinline__ int reduce_blocks(long long ntiles)
+{
+    const long long b = (ntiles + kT - 1) / kT;
+    return (int)(b < 1 ? 1 : (b > kRedBlocks ? kRedBlocks : b));
+}
+
 static __global__ void __launch_bounds__(kT) ka_reduce(AdjState* __restrict__ a, const double* __restrict__ parts,
-                                                       long long ntiles, const double* __restrict__ parts2, int nbox)
+                                                       long long ntiles, const double* __restrict__ parts2, int nbox,
+                                                       double* __restrict__ red)
 {
     __shared__ double s_red[(kT / 32) * 8];
     __shared__ double s_out[8];
     __shared__ double s_res[16];
-    double s[kNodeParts + 1];
-    for (int k = 0; k <= kNodeParts; ++k) s[k] = 0.0;
-    for (long long t = threadIdx.x; t < ntiles; t += blockDim.x)
+    const long long nb = gridDim.x;
+    const long long t0 = ntiles * blockIdx.x / nb, t1 = ntiles * (blockIdx.x + 1) / nb;
+    const long long u0 = (long long)nbox * blockIdx.x / nb, u1 = (long long)nbox * (blockIdx.x + 1) / nb;
+    double s[kRedSums];
+    for (int k = 0; k < kRedSums; ++k) s[k] = 0.0;
+    for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x)
         for (int k = 0; k < kNodeParts; ++k) s[k] += parts[t * kNodeParts + k];
-    for (int t = threadIdx.x; t < nbox; t += blockDim.x) s[kNodeParts] += parts2[t];
+    for (long long t = u0 + threadIdx.x; t < u1; t += blockDim.x) s[kNodeParts] += parts2[t];
     double v[8];
     for (int k = 0; k < 8; ++k) v[k] = s[k];
     block_sum8<kT>(v, s_red, s_out);
     if (threadIdx.x < 8) s_res[threadIdx.x] = s_out[threadIdx.x];
     __syncthreads();
-    for (int k = 0; k < 8; ++k) v[k] = (8 + k <= kNodeParts) ? s[8 + k] : 0.0;
+    for (int k = 0; k < 8; ++k) v[k] = (8 + k < kRedSums) ? s[8 + k] : 0.0;
     block_sum8<kT>(v, s_red, s_out);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kRedSums; ++k) red[blockIdx.x * kRedSums + k] = k < 8 ? s_res[k] : s_out[k - 8];
+    if (!last_block(&a->red_done, (unsigned)nb, threadIdx.x == 0)) return;
     if (threadIdx.x != 0) return;
+    double r[kRedSums];
+    for (int k = 0; k < kRedSums; ++k) r[k] = 0.0;
+    for (long long b = 0; b < nb; ++b)
+        for (int k = 0; k < kRedSums; ++k) r[k] += __ldcg(red + b * kRedSums + k);
     for (int k = 0; k < 3; ++k) {
-        a->lX[k] += s_res[k];
-        a->lV[k] += s_res[3 + k];
-        a->lOm[k] += (k < 2) ? s_res[6 + k] : s_out[0];
+        a->lX[k] += r[k];
+        a->lV[k] += r[3 + k];
+        a->lOm[k] += r[6 + k];
     }
-    a->grad[2] += s_out[1];
-    a->ld[0] = s_out[2];
-    a->ld[1] = s_out[3];
-    a->grad[1] += s_out[4];
+    a->grad[2] += r[9];
+    a->ld[0] = r[10];
+    a->ld[1] = r[11];
+    a->grad[1] += r[12];
 }
 
 }  // namespace flbm_adjoint
@@ -1152,6 +1176,7 @@ struct AdjBuffers {
     double* parts = nullptr;
     double* parts2 = nullptr;
     double* cparts = nullptr;
+    double* red = nullptr;      // per block of ka_reduce: its kRedSums sums
     AdjState* adj = nullptr;
     size_t bytes = 0;
 
@@ -1341,7 +1366,7 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     ka_final<<<h->grid, h->block, 0, st>>>(L0, b.lgf, b.lpsi, s0, m0, k);
     if (int rc = acheck(h, "ka_final")) return rc;
     ACK(h, cudaStreamWaitEvent(st, b.ev_lpsi, 0));
-    ka_reduce<<<1, kT, 0, st>>>(b.adj, b.parts, h->ntiles, b.parts2, lpsi_blocks(k));
+    ka_reduce<<<reduce_blocks(h->ntiles), kT, 0, st>>>(b.adj, b.parts, h->ntiles, b.parts2, lpsi_blocks(k), b.red);
     if (int rc = acheck(h, "ka_reduce")) return rc;
     ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
     return FLBM_OK;
@@ -1371,7 +1396,7 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
         !b.alloc(b.lam[0], 8 * N) || !b.alloc(b.lam[1], 8 * N) || !b.alloc(b.lgf, 6 * N) ||
         !b.alloc(b.lpsi, (size_t)(2 * k.padn)) || !b.alloc(b.uv, 2 * B3) ||
         !b.alloc(b.parts, (size_t)h->ntiles * kNodeParts) || !b.alloc(b.parts2, (size_t)lpsi_blocks(h->kp)) ||
-        !b.alloc(b.cparts, (size_t)h->box_blocks * 9) || !b.alloc(b.adj, 1))
+        !b.alloc(b.cparts, (size_t)h->box_blocks * 9) || !b.alloc(b.red, (size_t)kRedBlocks * kRedSums) || !b.alloc(b.adj, 1))
         return sim_fail(h, FLBM_E_NOMEM, "adjoint checkpoints and tape");
     if (!b.make_events()) return sim_fail(h, FLBM_E_CUDA, "adjoint events");
     // The step sequences are replayed as CUDA graphs, which the legacy default
