@@ -9,11 +9,12 @@
 // stages the descriptor of its current replica (kernel parameters and device
 // pointers) in shared memory and runs the same device bodies as the
 // single-simulation kernels, so each replica computes exactly what
-// flbm_create/flbm_step would. The step sequence (densities; density shell
-// with the virtual layer; collide-stream of bulk and near tiles, the near
-// launch ending with each replica's particle update; next-position masks;
-// cover/uncover ending with each replica's bookkeeping) is captured into a
-// CUDA graph of two steps when the stream allows capture.
+// flbm_create/flbm_step would. The step sequence (densities; density shell;
+// collide-stream of the bulk tiles; on a side stream meanwhile the virtual
+// layer, the near tiles, whose launch ends with each replica's particle
+// update, and the next-position masks; cover/uncover ending with each
+// replica's bookkeeping) is captured into a CUDA graph of two steps when the
+// stream allows capture.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -165,7 +166,8 @@ static __global__ void __launch_bounds__(256) kb_finish(const RepDesc* __restric
 // kernel variant (noise on/off x all relaxation times 1 or not).
 enum WorkKind {
     W_DENSITY = 0,
-    W_SHELL,           // shell and virtual layer
+    W_SHELL,           // shell
+    W_VIRT,            // virtual layer (blocks of kb_shell after the shell's)
     W_BULK,            // + variant (4 lists)
     W_NEAR = W_BULK + 4,  // + variant (4 lists)
     W_MARK = W_NEAR + 4,
@@ -185,10 +187,11 @@ struct flbm_ens {
     std::vector<RepDesc> rd;
     flbm_ens_config cfg{0, 4, 0};
     cudaStream_t stream = nullptr;
-    // Near-particle collide on a higher-priority side stream, concurrent with
-    // the bulk collide (disjoint writes), forked and joined by events.
+    // Virtual layers, near-particle collide and next-position masks on a
+    // higher-priority side stream, concurrent with the shells and the bulk
+    // collide (disjoint writes), forked (psi_ev, fork_ev) and joined by events.
     cudaStream_t side = nullptr;
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaEvent_t psi_ev = nullptr, fork_ev = nullptr, join_ev = nullptr;
     int nsm = 0;
     void* arena = nullptr;
     RepDesc* d_reps = nullptr;
@@ -238,7 +241,8 @@ long long blocks_of(const KParams& k, int w)
 {
     const bool part = k.has_particle != 0;
     if (w == W_DENSITY) return tile_count(k);
-    if (w == W_SHELL) return (shell_count(k) + 255) / 256 + (part ? box_block_count(k) : 0);
+    if (w == W_SHELL) return (shell_count(k) + 255) / 256;
+    if (w == W_VIRT) return part ? box_block_count(k) : 0;
     if (w >= W_BULK && w < W_BULK + 4) return variant(k) == w - W_BULK ? tile_count(k) : 0;
     if (w >= W_NEAR && w < W_NEAR + 4) return (part && variant(k) == w - W_NEAR) ? cand_count(k) : 0;
     if (w == W_MARK || w == W_COVER) return part ? box_block_count(k) : 0;
@@ -274,6 +278,7 @@ int apply_config(flbm_ens* e)
             return make_int4(r, (int)(b % k.gx), (int)(b / k.gx % k.gy), (int)(b / ((long long)k.gx * k.gy)));
         if (w >= W_NEAR && w < W_NEAR + 4)
             return make_int4(r, (int)(b % k.ncx), (int)(b / k.ncx % k.ncy), (int)(b / ((long long)k.ncx * k.ncy)));
+        if (w == W_VIRT) return make_int4(r, (int)(blocks_of(k, W_SHELL) + b), 0, 0);
         return make_int4(r, (int)b, 0, 0);
     };
     for (int w = 0; w < W_COUNT; ++w) {
@@ -416,8 +421,19 @@ int ens_step(flbm_ens* e)
 {
     const int par = e->cur;
     if (int rc = launch_list(e, W_DENSITY, kb_density, "kb_density", par)) return rc;
-    if (int rc = launch_list(e, W_SHELL, kb_shell, "kb_shell")) return rc;
+    // The particles' share of the step runs on the side stream: the virtual
+    // layers once the densities are in, the near tiles once the shells are
+    // in too, then the next-position masks. The shells and the bulk tiles,
+    // which read neither, run on the main stream meanwhile.
     const bool near = e->off[W_NEAR + 4] > e->off[W_NEAR];
+    if (near) {
+        ECK(e, cudaEventRecord(e->psi_ev, e->stream));
+        ECK(e, cudaStreamWaitEvent(e->side, e->psi_ev, 0));
+        if (int rc = launch_on(e, e->side, W_VIRT, kb_shell, "kb_shell")) return rc;
+    } else if (int rc = launch_list(e, W_VIRT, kb_shell, "kb_shell")) {
+        return rc;
+    }
+    if (int rc = launch_list(e, W_SHELL, kb_shell, "kb_shell")) return rc;
     if (near) {
         ECK(e, cudaEventRecord(e->fork_ev, e->stream));
         ECK(e, cudaStreamWaitEvent(e->side, e->fork_ev, 0));
@@ -425,6 +441,7 @@ int ens_step(flbm_ens* e)
         if (int rc = launch_on(e, e->side, W_NEAR + 1, kb_near<false, true>, "kb_near", par)) return rc;
         if (int rc = launch_on(e, e->side, W_NEAR + 2, kb_near<true, false>, "kb_near", par)) return rc;
         if (int rc = launch_on(e, e->side, W_NEAR + 3, kb_near<true, true>, "kb_near", par)) return rc;
+        if (int rc = launch_on(e, e->side, W_MARK, kb_mark_next, "kb_mark_next")) return rc;
         ECK(e, cudaEventRecord(e->join_ev, e->side));
     }
     if (int rc = launch_list(e, W_BULK + 0, kb_bulk<false, false>, "kb_bulk", par)) return rc;
@@ -432,7 +449,7 @@ int ens_step(flbm_ens* e)
     if (int rc = launch_list(e, W_BULK + 2, kb_bulk<true, false>, "kb_bulk", par)) return rc;
     if (int rc = launch_list(e, W_BULK + 3, kb_bulk<true, true>, "kb_bulk", par)) return rc;
     if (near) ECK(e, cudaStreamWaitEvent(e->stream, e->join_ev, 0));
-    if (int rc = launch_list(e, W_MARK, kb_mark_next, "kb_mark_next")) return rc;
+    else if (int rc = launch_list(e, W_MARK, kb_mark_next, "kb_mark_next")) return rc;
     if (int rc = launch_list(e, W_COVER, kb_cover, "kb_cover", par)) return rc;
     if (int rc = launch_list(e, W_FINISH, kb_finish, "kb_finish")) return rc;
     e->cur = 1 - e->cur;
@@ -518,6 +535,7 @@ int flbm_ensemble_create(const flbm_params* p, int32_t n, const flbm_ens_config*
     int dev = 0, lo = 0, hi = 0;
     if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
         cudaStreamCreateWithPriority(&e->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->psi_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&e->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&e->join_ev, cudaEventDisableTiming) != cudaSuccess) {
         flbm_ensemble_destroy(e);
@@ -658,6 +676,7 @@ void flbm_ensemble_destroy(flbm_ens_t* e)
         cudaStreamSynchronize(e->side);
         cudaStreamDestroy(e->side);
     }
+    if (e->psi_ev) cudaEventDestroy(e->psi_ev);
     if (e->fork_ev) cudaEventDestroy(e->fork_ev);
     if (e->join_ev) cudaEventDestroy(e->join_ev);
     cudaFree(e->arena);
