@@ -432,6 +432,9 @@ def run_ours(args):
     f_host = torch.empty(sim.shape, dtype=torch.float32, pin_memory=True).numpy()
     f_out = torch.empty(sim.shape, dtype=torch.float32, pin_memory=True).numpy()
     f_host[...] = sim.read_f()
+    # One untimed call of the same size first (record buffers, captured
+    # graphs, first use of the pinned pages), as the device leg warms up.
+    sim.run_host(f_host, args.steps, f_out=f_out, traj=True)
     barrier()
     t0 = time.perf_counter()
     sim.run_host(f_host, args.steps, f_out=f_out, traj=True)

@@ -190,8 +190,11 @@ int flbm_set_particle(flbm_t* h, const double X[3], const double V[3], const dou
 /* End-to-end call from host memory: copy host_f_in (2*19*N float32) to the
  * device, advance nsteps, write the particle record of every step to
  * traj[0..nsteps-1] (may be NULL), copy the final populations to host_f_out
- * (may be NULL). Synchronises before returning. Errors: FLBM_E_INVAL (NULL
- * handle or input, nsteps < 0), FLBM_E_NOMEM (host or device staging of the trajectory),
+ * (may be NULL). With flbm_use_graphs on, the steps replay captured graphs as
+ * flbm_step does, each step followed by a small kernel that stores its record
+ * on the device. Synchronises before returning. Errors: FLBM_E_INVAL (NULL
+ * handle or input, nsteps < 0, or more than 2^31 - 1 steps with a
+ * trajectory), FLBM_E_NOMEM (host or device staging of the trajectory),
  * FLBM_E_CUDA. */
 int flbm_run_host(flbm_t* h, const float* host_f_in, int64_t nsteps, float* host_f_out, flbm_particle* traj);
 

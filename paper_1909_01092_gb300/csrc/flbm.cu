@@ -305,33 +305,63 @@ int set_fused_geometry(flbm_sim* h, int K)
     return FLBM_OK;
 }
 
-// Captured graphs replay the kernels and parameters of their capture; drop them.
-int drop_graphs(flbm_sim* h)
+// Captured graphs replay the kernels and parameters of their capture; drop
+// them (with rec_only, only those that record the trajectory).
+int drop_graphs(flbm_sim* h, bool rec_only = false)
 {
     bool any = false;
-    for (int c = 0; c < 2; ++c) any = any || h->graph[c];
+    for (int c = 0; c < 2; ++c) any = any || h->graph_rec[c] || (!rec_only && h->graph[c]);
     if (!any) return FLBM_OK;
     CK(h, cudaStreamSynchronize(h->stream));
-    for (int c = 0; c < 2; ++c)
-        if (h->graph[c]) {
+    for (int c = 0; c < 2; ++c) {
+        if (h->graph_rec[c]) cudaGraphExecDestroy(h->graph_rec[c]);
+        h->graph_rec[c] = nullptr;
+        if (!rec_only && h->graph[c]) {
             cudaGraphExecDestroy(h->graph[c]);
             h->graph[c] = nullptr;
         }
+    }
     return FLBM_OK;
+}
+
+// The particle record of the step just finished into the next free slot of
+// traj (count of them kept on the device, so that captured steps can record).
+static __global__ void __launch_bounds__(64) k_record(const DevState* __restrict__ st, DevState* __restrict__ traj,
+                                                      int* __restrict__ count, int cap)
+{
+    const int slot = *count;
+    if (slot >= cap) return;  // the same for the whole block
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(st);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(traj + slot);
+    for (int w = threadIdx.x; w < (int)(sizeof(DevState) / 4); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();  // every thread has read the count
+    if (threadIdx.x == 0) *count = slot + 1;
+}
+static_assert(sizeof(DevState) % 4 == 0, "DevState is copied as 32-bit words");
+
+// One step and, with rec, its particle record (flbm_run_host).
+int launch_step_rec(flbm_sim* h, bool rec)
+{
+    if (int rc = launch_step(h)) return rc;
+    if (!rec) return FLBM_OK;
+    k_record<<<1, 64, 0, h->stream>>>(h->st, h->traj_dev, h->traj_count, (int)h->traj_cap);
+    return launch_check(h, "k_record");
 }
 
 // Steps per captured graph (even, so that a replay brings cur back). More
 // steps per graph spread the replay's own launch cost over more steps.
 constexpr int kGraphSteps = 8;
 
-// Capture kGraphSteps steps starting from cur = c into h->graph[c] (once).
-int ensure_graph(flbm_sim* h, int c)
+// Capture kGraphSteps steps starting from cur = c (with rec, each followed by
+// its particle record) into h->graph[c] or h->graph_rec[c] (once).
+int ensure_graph(flbm_sim* h, int c, bool rec = false)
 {
-    if (h->graph[c]) return FLBM_OK;
+    cudaGraphExec_t& ge = rec ? h->graph_rec[c] : h->graph[c];
+    if (ge) return FLBM_OK;
     const int64_t before = h->launches;
     CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     int rc = FLBM_OK;
-    for (int k = 0; k < kGraphSteps && !rc; ++k) rc = launch_step(h);
+    for (int k = 0; k < kGraphSteps && !rc; ++k) rc = launch_step_rec(h, rec);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (rc) {
@@ -339,15 +369,37 @@ int ensure_graph(flbm_sim* h, int c)
         return rc;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&h->graph[c], g, 0);
+    e = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        h->graph[c] = nullptr;
+        ge = nullptr;
         return cuda_fail(h, e, "cudaGraphInstantiate");
     }
     // Capturing only recorded the kernels: nothing ran, cur is back at c.
-    h->graph_launches[c] = h->launches - before;
+    (rec ? h->graph_rec_launches[c] : h->graph_launches[c]) = h->launches - before;
     h->launches = before;
+    return FLBM_OK;
+}
+
+// nsteps steps: replayed graphs of kGraphSteps steps while they fit (with
+// use_graphs), plain launches for the rest; with rec each step's particle
+// record follows it.
+int run_steps(flbm_sim* h, int64_t nsteps, bool rec)
+{
+    int64_t s = 0;
+    if (h->use_graphs) {
+        // A graph captures steps that start from valid densities.
+        if (use_fused(h) && nsteps >= kGraphSteps)
+            if (int rc = ensure_psi(h)) return rc;
+        for (; s + kGraphSteps <= nsteps; s += kGraphSteps) {
+            if (int rc = ensure_graph(h, h->cur, rec)) return rc;
+            CK(h, cudaGraphLaunch(rec ? h->graph_rec[h->cur] : h->graph[h->cur], h->stream));
+            // an even number of steps brings cur back
+            h->launches += rec ? h->graph_rec_launches[h->cur] : h->graph_launches[h->cur];
+        }
+    }
+    for (; s < nsteps; ++s)
+        if (int rc = launch_step_rec(h, rec)) return rc;
     return FLBM_OK;
 }
 
@@ -504,20 +556,7 @@ int flbm_step(flbm_t* h, int64_t nsteps)
 {
     if (!h || nsteps < 0) return fail(h, FLBM_E_INVAL, "invalid handle or step count");
     h->launches = 0;
-    int64_t s = 0;
-    if (h->use_graphs) {
-        // A graph captures steps that start from valid densities.
-        if (use_fused(h) && nsteps >= kGraphSteps)
-            if (int rc = ensure_psi(h)) return rc;
-        for (; s + kGraphSteps <= nsteps; s += kGraphSteps) {
-            if (int rc = ensure_graph(h, h->cur)) return rc;
-            CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
-            h->launches += h->graph_launches[h->cur];  // an even number of steps brings cur back
-        }
-    }
-    for (; s < nsteps; ++s)
-        if (int rc = launch_step(h)) return rc;
-    return FLBM_OK;
+    return run_steps(h, nsteps, false);
 }
 
 int flbm_use_tma(flbm_t* h, int enable)
@@ -761,25 +800,25 @@ int flbm_run_host(flbm_t* h, const float* host_f_in, int64_t nsteps, float* host
     if (!h || !host_f_in || nsteps < 0) return fail(h, FLBM_E_INVAL, "invalid argument");
     const KParams& k = h->kp;
     const size_t fbytes = sizeof(float) * 2 * 19 * k.N;
+    if (traj && nsteps > 0x7fffffff) return fail(h, FLBM_E_INVAL, "too many steps for a trajectory");
     if (traj && (size_t)nsteps > h->traj_cap) {
+        if (int rc = drop_graphs(h, true)) return rc;  // they hold the old record buffer
         if (h->traj_dev) cudaFree(h->traj_dev);
         h->traj_dev = nullptr;
         h->traj_cap = 0;
         CK(h, cudaMalloc(&h->traj_dev, sizeof(DevState) * (size_t)nsteps));
         h->traj_cap = (size_t)nsteps;
     }
+    if (traj && !h->traj_count) CK(h, cudaMalloc(&h->traj_count, sizeof(int)));
     CK(h, cudaMemcpyAsync(h->fbuf[h->cur], host_f_in, fbytes, cudaMemcpyHostToDevice, h->stream));
+    if (traj) CK(h, cudaMemsetAsync(h->traj_count, 0, sizeof(int), h->stream));
     h->launches = 0;
-    if (int rc = launch_psi(h)) return rc;
-    int64_t launches = h->launches;
-    for (int64_t s = 0; s < nsteps; ++s) {
-        h->launches = 0;
-        if (int rc = launch_step(h)) return rc;
-        launches += h->launches;
-        if (traj)
-            CK(h, cudaMemcpyAsync(h->traj_dev + s, h->st, sizeof(DevState), cudaMemcpyDeviceToDevice, h->stream));
-    }
-    h->launches = launches;
+    // New populations: the densities are stale (a two-pass step computes its
+    // own; the fused one needs them first).
+    h->psi_valid = false;
+    if (use_fused(h))
+        if (int rc = ensure_psi(h)) return rc;
+    if (int rc = run_steps(h, nsteps, traj != nullptr)) return rc;
     if (host_f_out)
         CK(h, cudaMemcpyAsync(host_f_out, h->fbuf[h->cur], fbytes, cudaMemcpyDeviceToHost, h->stream));
     if (traj && nsteps > 0) {
@@ -856,8 +895,11 @@ void flbm_destroy(flbm_t* h)
     cudaFree(h->obs_mode_out);
     cudaFree(h->scratch_rho);
     cudaFree(h->traj_dev);
+    cudaFree(h->traj_count);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     for (cudaGraphExec_t g : h->graph)
+        if (g) cudaGraphExecDestroy(g);
+    for (cudaGraphExec_t g : h->graph_rec)
         if (g) cudaGraphExecDestroy(g);
     if (h->side) {
         cudaStreamSynchronize(h->side);

@@ -48,14 +48,19 @@ struct flbm_sim {
     double* obs_mode_tiles = nullptr;  // per tile: kObsModes sums of k_obs_modes
     double* obs_mode_out = nullptr;
     float* scratch_rho = nullptr;
-    DevState* traj_dev = nullptr;
+    DevState* traj_dev = nullptr;  // per-step particle records of flbm_run_host
     size_t traj_cap = 0;
+    int* traj_count = nullptr;     // records written so far in this call (k_record)
     DevState* traj_host = nullptr;
     size_t traj_host_cap = 0;
     std::vector<cudaEvent_t> events;  // pool for flbm_step_timed
     bool use_graphs = false;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two steps starting from cur = 0 / 1
-    int64_t graph_launches[2] = {0, 0};            // kernels in each graph
+    // Captured steps starting from cur = 0 / 1; graph_rec also records each
+    // step's particle state into traj_dev (flbm_run_host with a trajectory).
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph_rec[2] = {nullptr, nullptr};
+    int64_t graph_launches[2] = {0, 0};      // kernels in each graph
+    int64_t graph_rec_launches[2] = {0, 0};
     dim3 grid, block;
     // Bulk collide with TMA-staged inputs (k_collide_bulk_tma): tensor maps of
     // the two population copies and of the padded densities; tma_ok when the

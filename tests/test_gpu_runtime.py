@@ -94,6 +94,35 @@ def test_graph_replay_equals_plain_launches(flbm, radius):
     _same_state(plain, g, p)
 
 
+def test_run_host_in_graphs_records_every_step(flbm):
+    """flbm_run_host with graph replay: each captured step is followed by a
+    kernel that writes its particle record into the next slot of the
+    trajectory buffer. The final populations and every step's record must
+    equal plain stepping, step by step, in a first call, in a second one
+    (the record count starts again) and in a longer third one (a larger
+    record buffer, so the recording graphs are captured again)."""
+    import torch
+
+    p = W.channel_small(kT=1e-5, radius=3.0)
+    ref = flbm.Sim(p)
+    g = flbm.Sim(p, stream=torch.cuda.Stream())
+    g.use_graphs(True)
+    f = ref.read_f()
+    keys = ("X", "V", "Omega", "F", "T", "delta", "step", "nfluid")
+    for n in (21, 13, 37):  # graphs of 8 steps and a plain rest
+        out = np.empty_like(f)
+        traj = g.run_host(f, n, f_out=out, traj=True)
+        torch.cuda.synchronize()
+        assert len(traj) == n
+        for k in range(n):
+            ref.step(1)
+            pr = ref.particle()
+            for key in keys:
+                assert np.array_equal(np.asarray(pr[key]), np.asarray(traj[k][key])), (n, k, key)
+        assert np.array_equal(ref.read_f(), out)
+        f = out
+
+
 def test_graphs_refused_on_the_legacy_stream(flbm):
     import torch
 
