@@ -121,6 +121,32 @@ static __global__ void __launch_bounds__(256, 3)
     FLBM_END_ITEMS
 }
 
+// Bulk collide with the replicas' descriptors as a kernel parameter (up to
+// kChunkReps of them per launch): blockIdx.y picks the replica and blockIdx.x
+// the tile. The descriptor's fields are then read from the constant bank at
+// an index the same for the whole block, as a single simulation reads its
+// kernel parameters, instead of from shared memory into registers: the
+// kernel fits four blocks per SM. Blocks past the replica's tile count return.
+constexpr int kChunkReps = 48;
+struct RepChunk {
+    RepDesc r[kChunkReps];
+};
+static_assert(sizeof(RepChunk) + 64 <= 32764, "kernel parameters are at most 32764 bytes");
+
+template <bool NOISE, bool TAU1>
+static __global__ void __launch_bounds__(256, 4) kb_bulk_rep(const __grid_constant__ RepChunk c, int par)
+{
+    const RepDesc& R = c.r[blockIdx.y];
+    const KParams& P = R.P;
+    const int plane = P.gx * P.gy;
+    const int t = blockIdx.x;
+    if (t >= plane * P.lz) return;
+    const int bz = t / plane, w = t - bz * plane;
+    const int by = w / P.gx, bx = w - by * P.gx;
+    const int tx = threadIdx.x & (P.tx - 1), ty = threadIdx.x >> (__ffs(P.tx) - 1);
+    bulk_tile<NOISE, TAU1>(bx, by, bz, tx, ty, R.f[par], R.f[1 - par], R.psi, R.st, P);
+}
+
 // Three blocks per SM: the register cap costs some spills, and the extra
 // resident warps hide more of the near tiles' latency (measured faster).
 template <bool NOISE, bool TAU1>
@@ -199,6 +225,15 @@ struct flbm_ens {
     Item* d_items = nullptr;
     size_t items_cap = 0;
     long long off[W_COUNT + 1] = {};  // work list k = d_items[off[k] .. off[k+1])
+    // Bulk collide launches of one block per tile (ctas_per_sm 0), per
+    // variant: replicas of similar tile counts grouped, kChunkReps at most
+    // per launch.
+    struct RepLaunch {
+        RepChunk c;
+        int n = 0;
+        int max_blocks = 0;
+    };
+    std::vector<RepLaunch> rep_launches[4];
     double* obs_tiles = nullptr;
     double* obs_out = nullptr;
     double* obs_mode_tiles = nullptr;
@@ -295,6 +330,29 @@ int apply_config(flbm_ens* e)
         }
     }
     e->off[W_COUNT] = (long long)items.size();
+    // Bulk launches with descriptor chunks: per variant, replicas by
+    // decreasing tile count; a chunk takes replicas while it has room and
+    // each has at least 3/4 of the first one's tiles (the blocks past a
+    // replica's own return at once).
+    for (int k = 0; k < 4; ++k) {
+        const int w = W_BULK + k;
+        auto& ch = e->rep_launches[k];
+        ch.clear();
+        std::vector<int> reps;
+        for (int r = 0; r < e->n; ++r)
+            if (blocks_of(e->kp[r], w) > 0) reps.push_back(r);
+        std::stable_sort(reps.begin(), reps.end(),
+                         [&](int a, int b) { return blocks_of(e->kp[a], w) > blocks_of(e->kp[b], w); });
+        for (int r : reps) {
+            const long long t = blocks_of(e->kp[r], w);
+            if (t > 0x7fffffffLL) return efail(e, FLBM_E_INVAL, "too many tiles in one replica");
+            if (ch.empty() || ch.back().n == kChunkReps || 4 * t < 3LL * ch.back().max_blocks) {
+                ch.emplace_back();
+                ch.back().max_blocks = (int)t;
+            }
+            ch.back().c.r[ch.back().n++] = e->rd[r];
+        }
+    }
     if (items.size() > (size_t)0x7fffffff) return efail(e, FLBM_E_INVAL, "too many work items");
     if (items.size() > e->items_cap) {
         cudaFree(e->d_items);
@@ -416,6 +474,19 @@ int launch_list(flbm_ens* e, int w, void (*kern)(const RepDesc*, const Item*, in
     return launch_on(e, e->stream, w, kern, what, args...);
 }
 
+// The bulk collide launches with descriptor chunks.
+int launch_bulk_reps(flbm_ens* e, int par)
+{
+    void (*kern[4])(const RepChunk, int) = {kb_bulk_rep<false, false>, kb_bulk_rep<false, true>,
+                                            kb_bulk_rep<true, false>, kb_bulk_rep<true, true>};
+    for (int k = 0; k < 4; ++k)
+        for (const auto& ch : e->rep_launches[k]) {
+            kern[k]<<<dim3((unsigned)ch.max_blocks, (unsigned)ch.n), 256, 0, e->stream>>>(ch.c, par);
+            if (int rc = elaunch(e, "kb_bulk_rep")) return rc;
+        }
+    return FLBM_OK;
+}
+
 // One step of every replica: reads f[cur], writes f[1 - cur].
 int ens_step(flbm_ens* e)
 {
@@ -444,10 +515,14 @@ int ens_step(flbm_ens* e)
         if (int rc = launch_on(e, e->side, W_MARK, kb_mark_next, "kb_mark_next")) return rc;
         ECK(e, cudaEventRecord(e->join_ev, e->side));
     }
-    if (int rc = launch_list(e, W_BULK + 0, kb_bulk<false, false>, "kb_bulk", par)) return rc;
-    if (int rc = launch_list(e, W_BULK + 1, kb_bulk<false, true>, "kb_bulk", par)) return rc;
-    if (int rc = launch_list(e, W_BULK + 2, kb_bulk<true, false>, "kb_bulk", par)) return rc;
-    if (int rc = launch_list(e, W_BULK + 3, kb_bulk<true, true>, "kb_bulk", par)) return rc;
+    if (e->cfg.ctas_per_sm == 0) {
+        if (int rc = launch_bulk_reps(e, par)) return rc;
+    } else {
+        if (int rc = launch_list(e, W_BULK + 0, kb_bulk<false, false>, "kb_bulk", par)) return rc;
+        if (int rc = launch_list(e, W_BULK + 1, kb_bulk<false, true>, "kb_bulk", par)) return rc;
+        if (int rc = launch_list(e, W_BULK + 2, kb_bulk<true, false>, "kb_bulk", par)) return rc;
+        if (int rc = launch_list(e, W_BULK + 3, kb_bulk<true, true>, "kb_bulk", par)) return rc;
+    }
     if (near) ECK(e, cudaStreamWaitEvent(e->stream, e->join_ev, 0));
     else if (int rc = launch_list(e, W_MARK, kb_mark_next, "kb_mark_next")) return rc;
     if (int rc = launch_list(e, W_COVER, kb_cover, "kb_cover", par)) return rc;
