@@ -979,27 +979,34 @@ static __global__ void __launch_bounds__(kT) ka_lpsi_shell(const lg_t* __restric
                                                            const DevState* __restrict__ s0,
                                                            const uint8_t* __restrict__ mk0, KParams P)
 {
+    // The shell points in the order shell_node takes them, decoded in 32 bits
+    // (each face holds fewer than 2^31 points).
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long pw = P.lx + 2;  // padded row length (the row stride P.px may be larger)
-    const long long nzf = 2LL * pw * P.py, nyf = 2LL * pw * P.lz, nxf = 2LL * P.ly * P.lz;
+    const int pw = P.lx + 2;  // padded row length (the row stride P.px may be larger)
+    const int zf = pw * P.py, yf = pw * P.lz, xf = P.ly * P.lz;
+    if (t >= 2LL * zf + 2LL * yf + 2LL * xf) return;
+    int u = (int)t;
     int p[3];
-    if (t < nzf) {
-        const long long r = t % (pw * P.py);
-        p[0] = (int)(r % pw) - 1;
-        p[1] = (int)(r / pw) - 1;
-        p[2] = (t < nzf / 2) ? -1 : P.lz;
-    } else if (t < nzf + nyf) {
-        const long long u = t - nzf, r = u % (pw * P.lz);
-        p[0] = (int)(r % pw) - 1;
-        p[2] = (int)(r / pw);
-        p[1] = (u < nyf / 2) ? -1 : P.ly;
-    } else if (t < nzf + nyf + nxf) {
-        const long long u = t - nzf - nyf, r = u % ((long long)P.ly * P.lz);
-        p[1] = (int)(r % P.ly);
-        p[2] = (int)(r / P.ly);
-        p[0] = (u < nxf / 2) ? -1 : P.lx;
+    if (u < 2 * zf) {
+        const int side = u >= zf;
+        const int r = u - side * zf;
+        p[1] = r / pw;
+        p[0] = r - p[1] * pw - 1;
+        p[1] -= 1;
+        p[2] = side ? P.lz : -1;
+    } else if ((u -= 2 * zf) < 2 * yf) {
+        const int side = u >= yf;
+        const int r = u - side * yf;
+        p[2] = r / pw;
+        p[0] = r - p[2] * pw - 1;
+        p[1] = side ? P.ly : -1;
     } else {
-        return;
+        u -= 2 * yf;
+        const int side = u >= xf;
+        const int r = u - side * xf;
+        p[2] = r / P.ly;
+        p[1] = r - p[2] * P.ly;
+        p[0] = side ? P.lx : -1;
     }
     const int L[3] = {P.lx, P.ly, P.lz};
     bool ghost = false;

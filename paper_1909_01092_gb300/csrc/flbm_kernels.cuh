@@ -156,30 +156,35 @@ __host__ __device__ __forceinline__ long long shell_count(const KParams& P)
 __host__ __device__ __forceinline__ void shell_node(long long t, float* __restrict__ psi, const DevState* __restrict__ st,
                                            const uint8_t* __restrict__ masks, const KParams& P)
 {
-    const long long pw = P.lx + 2;                  // padded row length
-    const long long nzf = 2LL * pw * P.py;          // z faces, full padded planes
-    const long long nyf = 2LL * pw * P.lz;          // y faces, interior z
-    const long long nxf = 2LL * P.ly * P.lz;        // x faces, interior y, z
+    // 32-bit decoding: a lattice has fewer than 2^32 / 38 nodes (population
+    // offsets are 32-bit), so each face holds fewer than 2^31 shell nodes.
+    const int pw = P.lx + 2;           // padded row length
+    const int zf = pw * P.py;          // one z face, a full padded plane
+    const int yf = pw * P.lz;          // one y face, interior z
+    const int xf = P.ly * P.lz;        // one x face, interior y, z
+    if (t < 0 || t >= 2LL * zf + 2LL * yf + 2LL * xf) return;
+    int u = (int)t;
     int p[3];
-    if (t < nzf) {
-        const long long r = t % (pw * P.py);
-        p[0] = (int)(r % pw) - 1;
-        p[1] = (int)(r / pw) - 1;
-        p[2] = (t < nzf / 2) ? -1 : P.lz;
-    } else if (t < nzf + nyf) {
-        const long long u = t - nzf;
-        const long long r = u % (pw * P.lz);
-        p[0] = (int)(r % pw) - 1;
-        p[2] = (int)(r / pw);
-        p[1] = (u < nyf / 2) ? -1 : P.ly;
-    } else if (t < nzf + nyf + nxf) {
-        const long long u = t - nzf - nyf;
-        const long long r = u % ((long long)P.ly * P.lz);
-        p[1] = (int)(r % P.ly);
-        p[2] = (int)(r / P.ly);
-        p[0] = (u < nxf / 2) ? -1 : P.lx;
+    if (u < 2 * zf) {
+        const int side = u >= zf;
+        const int r = u - side * zf;
+        p[1] = r / pw;
+        p[0] = r - p[1] * pw - 1;
+        p[1] -= 1;
+        p[2] = side ? P.lz : -1;
+    } else if ((u -= 2 * zf) < 2 * yf) {
+        const int side = u >= yf;
+        const int r = u - side * yf;
+        p[2] = r / pw;
+        p[0] = r - p[2] * pw - 1;
+        p[1] = side ? P.ly : -1;
     } else {
-        return;
+        u -= 2 * yf;
+        const int side = u >= xf;
+        const int r = u - side * xf;
+        p[2] = r / P.ly;
+        p[1] = r - p[2] * P.ly;
+        p[0] = side ? P.lx : -1;
     }
     const int L[3] = {P.lx, P.ly, P.lz};
     int q[3];
