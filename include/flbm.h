@@ -404,7 +404,9 @@ typedef struct flbm_ens_config {
                             1 interleaved (item k of every replica, then item k+1),
                             2 replica after replica, largest lattice first */
     int32_t ctas_per_sm; /* persistent blocks per SM of every batched launch (1..8);
-                            0: one block per work item */
+                            0: one block per work item, and the bulk collide in
+                            launches of up to 48 replicas of similar tile counts
+                            whose descriptors are a kernel parameter */
     int32_t tile_policy; /* 0: tile width min(32, next power of two >= lx), as flbm_create;
                             1: the largest of 32, 16, 8 that divides lx (else as 0) */
 } flbm_ens_config;

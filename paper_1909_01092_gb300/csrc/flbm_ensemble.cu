@@ -4,12 +4,14 @@
 // over noise realisations and channel geometries. An ensemble advances all
 // its replicas with one set of batched launches per step: every launch walks
 // a flat list of work items (replica and block of that replica, with the
-// block's tile coordinates decoded on the host), and its blocks
-// are persistent (a fixed number per SM, striding over the list). A block
+// block's tile coordinates decoded on the host), one block per item or a
+// fixed number of persistent blocks per SM striding over the list. A block
 // stages the descriptor of its current replica (kernel parameters and device
 // pointers) in shared memory and runs the same device bodies as the
 // single-simulation kernels, so each replica computes exactly what
-// flbm_create/flbm_step would. The step sequence (densities; density shell;
+// flbm_create/flbm_step would. With one block per item, the bulk collide
+// instead takes the descriptors of up to kChunkReps replicas as a kernel
+// parameter (kb_bulk_rep). The step sequence (densities; density shell;
 // collide-stream of the bulk tiles; on a side stream meanwhile the virtual
 // layer, the near tiles, whose launch ends with each replica's particle
 // update, and the next-position masks; cover/uncover ending with each
