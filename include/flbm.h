@@ -359,18 +359,24 @@ typedef struct flbm_adjoint_result {
     double dJ_ddelta_rho;    /* dJ / d delta_rho (wetting shift of the virtual layer, Section 2) */
     double dJ_dG;            /* dJ / d G (Shan-Chen coupling, Eq. (sc-force)) */
     int64_t steps;           /* T */
-    int32_t checkpoint_every;/* K actually used (min(K, T)) */
-    int32_t reserved;
-    double device_bytes;     /* device memory the call allocated (checkpoints, tape, adjoint fields) */
-    double ms_forward;       /* device time of the forward run with checkpoints */
-    double ms_reverse;       /* device time of the segment recomputes and the reverse sweep */
+    int32_t checkpoint_every;/* K actually used (min(K, T)): segment length of the reverse sweep */
+    int32_t whole_tape;      /* 1: the forward run kept the whole tape (no recompute); 0: checkpoints */
+    double device_bytes;     /* device memory the call allocated (checkpoints or tape store, tape, adjoint fields) */
+    double ms_forward;       /* device time of the forward run (with checkpoints or the tape) */
+    double ms_reverse;       /* device time of the reverse sweep (with the segment recomputes, if any) */
 } flbm_adjoint_result;
 
 /* Run T = nsteps steps from h's current state and return J and its gradient
- * with respect to (g, delta_rho, G) by the discrete adjoint of the step,
- * with the state checkpointed every checkpoint_every steps and each segment
- * recomputed (with a tape of the moments rho_l, j_l) before it is swept
- * backwards: memory (T/K) x populations + K x 8 floats per node. The
+ * with respect to (g, delta_rho, G) by the discrete adjoint of the step. The
+ * reverse sweep reads a tape of the moments rho_l, j_l of every step (8
+ * floats per node), the particle records and the masks, segment by segment
+ * of K = checkpoint_every steps. Where the tape of all T steps fits within
+ * the limit that flbm_adjoint_tape_limit sets (by default half of the free
+ * device memory), the forward run writes it and nothing is recomputed:
+ * memory (T + 1) x (8 floats per node + masks). Otherwise the state is
+ * checkpointed every K steps and each segment recomputed, with its tape,
+ * before it is swept backwards: memory (T/K) x populations + K x 8 floats
+ * per node. Both give the same J and gradient, bit for bit. The
  * adjoint holds the step's discrete sets fixed (particle nodes, links,
  * covered and uncovered nodes): J is differentiated along the forward
  * trajectory. On return h has advanced T steps, exactly as flbm_step(h, T)
@@ -384,6 +390,13 @@ typedef struct flbm_adjoint_result {
  * fluid_counterforce = 0: FLBM_E_UNSUPPORTED otherwise. Synchronises.
  * Errors: FLBM_E_INVAL, FLBM_E_UNSUPPORTED, FLBM_E_NOMEM, FLBM_E_CUDA. */
 int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_every, flbm_adjoint_result* out);
+
+/* Device bytes up to which flbm_adjoint_run keeps the tape of every step
+ * instead of recomputing segments from checkpoints: bytes < 0 (the default)
+ * half of the device memory free at the call, 0 never, > 0 that many bytes
+ * (a store that then cannot be allocated falls back to checkpoints).
+ * Errors: FLBM_E_INVAL (NULL handle). */
+int flbm_adjoint_tape_limit(flbm_t* h, int64_t bytes);
 
 /* ------------------------------------------------------------------------
  * Batched ensemble: many independent simulations (replicas) advanced

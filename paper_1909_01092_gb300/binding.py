@@ -25,6 +25,7 @@ EXPORTS = (
     "flbm_last_launch_count", "flbm_destroy", "flbm_error_string", "flbm_last_error",
     "flbm_step_timed", "flbm_kernel_name", "flbm_observables_noalloc",
     "flbm_checkpoint", "flbm_restore", "flbm_use_graphs", "flbm_use_tma", "flbm_set_tma_wait", "flbm_adjoint_run",
+    "flbm_adjoint_tape_limit",
     "flbm_set_density_mode", "flbm_get_density_mode",
     "flbm_ensemble_create", "flbm_ensemble_step", "flbm_ensemble_tune", "flbm_ensemble_config",
     "flbm_ensemble_particles", "flbm_ensemble_read_fields", "flbm_ensemble_observables", "flbm_ensemble_nodes",
@@ -36,7 +37,7 @@ NKERNELS = 4
 class AdjResult(ctypes.Structure):
     _fields_ = [("J", ctypes.c_double), ("dJ_dg", ctypes.c_double), ("dJ_ddelta_rho", ctypes.c_double),
                 ("dJ_dG", ctypes.c_double), ("steps", ctypes.c_int64), ("checkpoint_every", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("device_bytes", ctypes.c_double), ("ms_forward", ctypes.c_double),
+                ("whole_tape", ctypes.c_int32), ("device_bytes", ctypes.c_double), ("ms_forward", ctypes.c_double),
                 ("ms_reverse", ctypes.c_double)]
 
 
@@ -115,6 +116,7 @@ def load(build_if_missing: bool = True):
         lib.flbm_set_density_mode.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         lib.flbm_get_density_mode.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         lib.flbm_adjoint_run.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(AdjResult)]
+        lib.flbm_adjoint_tape_limit.argtypes = [vp, ctypes.c_int64]
         ens_p = ctypes.POINTER(EnsConfig)
         lib.flbm_ensemble_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, ens_p, vp,
                                              ctypes.POINTER(vp)]
@@ -242,14 +244,21 @@ class Sim:
     def step(self, n: int = 1) -> None:
         self._check(self.lib.flbm_step(self.h, int(n)), "flbm_step")
 
-    def adjoint(self, steps: int, checkpoint_every: int = 100) -> dict:
+    def adjoint(self, steps: int, checkpoint_every: int = 100, tape_limit: int | None = None) -> dict:
         """J = time-averaged settling velocity over the next `steps` steps and
         its gradient (dJ/dg, dJ/d delta_rho, dJ/dG) by the discrete adjoint;
-        the simulation advances `steps` steps."""
+        the simulation advances `steps` steps. `tape_limit` (bytes; None
+        keeps the handle's setting, default automatic) bounds the tape of
+        every step that spares the segment recomputes; 0 forces
+        checkpoint-recompute."""
+        if tape_limit is not None:
+            self._check(self.lib.flbm_adjoint_tape_limit(self.h, int(tape_limit)), "flbm_adjoint_tape_limit")
         r = AdjResult()
         self._check(self.lib.flbm_adjoint_run(self.h, int(steps), int(checkpoint_every), ctypes.byref(r)),
                     "flbm_adjoint_run")
-        return {k: getattr(r, k) for k, _ in AdjResult._fields_ if k != "reserved"}
+        d = {k: getattr(r, k) for k, _ in AdjResult._fields_}
+        d["whole_tape"] = bool(d["whole_tape"])
+        return d
 
     def use_graphs(self, enable: bool = True) -> None:
         """Replay flbm_step as captured eight-step CUDA graphs (needs a

@@ -1173,9 +1173,12 @@ struct AdjBuffers {
     DevState* ck_st = nullptr; // checkpoints: particle record
     uint8_t* ck_m = nullptr;   // checkpoints: both particle masks
     float* ck_psi = nullptr;   // checkpoints: density field of the state (the fused step carries it)
-    float* tape = nullptr;     // K+1 moment fields
+    float* tape = nullptr;     // K+1 moment fields (slots of one segment)
     DevState* tape_st = nullptr;
     uint8_t* tape_m = nullptr;
+    float* all_tape = nullptr;     // whole-tape store: T+1 moment fields
+    DevState* all_st = nullptr;
+    uint8_t* all_m = nullptr;
     lam_t* lam[2] = {nullptr, nullptr};
     lg_t* lgf = nullptr;
     double* lpsi = nullptr;
@@ -1196,6 +1199,22 @@ struct AdjBuffers {
         bytes += n * sizeof(T);
         p = static_cast<T*>(v);
         return true;
+    }
+    // The whole-tape store of T+1 slots, all or nothing.
+    bool alloc_store(size_t slots, size_t N, size_t mbytes)
+    {
+        const size_t keep = owned.size(), kept = bytes;
+        if (alloc(all_tape, slots * 8 * N) && alloc(all_st, slots) && alloc(all_m, slots * mbytes)) return true;
+        while (owned.size() > keep) {
+            cudaFree(owned.back());
+            owned.pop_back();
+        }
+        bytes = kept;
+        all_tape = nullptr;
+        all_st = nullptr;
+        all_m = nullptr;
+        cudaGetLastError();  // the failed allocation is not the run's error
+        return false;
     }
     // Orderings between the two streams of a reverse step's last stages.
     cudaEvent_t ev_lpsi = nullptr, ev_shell = nullptr;
@@ -1235,13 +1254,16 @@ constexpr int kAdjGraph = 8;
 
 struct AdjGraphs {
     cudaGraphExec_t fwd[2] = {nullptr, nullptr};
-    std::vector<cudaGraphExec_t> rec[2];
+    std::vector<cudaGraphExec_t> rec[2];  // recompute with tape, per chunk of a segment
+    std::vector<cudaGraphExec_t> fwt[2];  // forward with tape and J, per chunk of a segment
     cudaGraphExec_t rev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [lcur][cur], full segments
     ~AdjGraphs()
     {
         for (int c = 0; c < 2; ++c) {
             if (fwd[c]) cudaGraphExecDestroy(fwd[c]);
             for (cudaGraphExec_t g : rec[c])
+                if (g) cudaGraphExecDestroy(g);
+            for (cudaGraphExec_t g : fwt[c])
                 if (g) cudaGraphExecDestroy(g);
             for (int d = 0; d < 2; ++d)
                 if (rev[c][d]) cudaGraphExecDestroy(rev[c][d]);
@@ -1381,6 +1403,13 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
 
 }  // namespace
 
+extern "C" int flbm_adjoint_tape_limit(flbm_t* h, int64_t bytes)
+{
+    if (!h) return FLBM_E_INVAL;
+    h->adj_tape_limit = bytes;
+    return FLBM_OK;
+}
+
 extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_every, flbm_adjoint_result* out)
 {
     if (!h || !out || nsteps < 1 || checkpoint_every < 1) return sim_fail(h, FLBM_E_INVAL, "invalid argument");
@@ -1396,8 +1425,21 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
     const size_t N = k.N, B3 = (size_t)k.B * k.B * k.B, mbytes = 2 * B3;
     const size_t fN = 2 * 19 * N;
     AdjBuffers b;
-    if (!b.alloc(b.ck_f, (size_t)(nck + 1) * fN) || !b.alloc(b.ck_st, (size_t)(nck + 1)) ||
-        !b.alloc(b.ck_m, (size_t)(nck + 1) * mbytes) || !b.alloc(b.ck_psi, (size_t)(nck + 1) * 2 * k.padn) ||
+    // Whole tape (no recompute) where the tape of every step fits the limit.
+    bool whole = false;
+    if (h->adj_tape_limit != 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            fr = 0;
+            cudaGetLastError();
+        }
+        const double need = (double)(T + 1) * (8.0 * sizeof(float) * (double)N + sizeof(DevState) + (double)mbytes);
+        const double lim = h->adj_tape_limit > 0 ? (double)h->adj_tape_limit : 0.5 * (double)fr;
+        whole = need <= lim && b.alloc_store((size_t)(T + 1), N, mbytes);
+    }
+    if ((!whole && (!b.alloc(b.ck_f, (size_t)(nck + 1) * fN) || !b.alloc(b.ck_st, (size_t)(nck + 1)) ||
+                    !b.alloc(b.ck_m, (size_t)(nck + 1) * mbytes) ||
+                    !b.alloc(b.ck_psi, (size_t)(nck + 1) * 2 * k.padn))) ||
         !b.alloc(b.tape, (size_t)(K + 1) * 8 * N) ||
         !b.alloc(b.tape_st, (size_t)(K + 1)) || !b.alloc(b.tape_m, (size_t)(K + 1) * mbytes) ||
         !b.alloc(b.lam[0], 8 * N) || !b.alloc(b.lam[1], 8 * N) || !b.alloc(b.lgf, 6 * N) ||
@@ -1462,8 +1504,68 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
         ka_accJ<<<1, 1, 0, st>>>(h->st, b.adj);
         return acheck(h, "ka_accJ");
     };
+    // Tape slot kk of a segment (moments, particle record, masks of the
+    // current state), then, with step, a step.
+    auto tape_step = [&](int kk, bool step) -> int {
+        ka_tape<<<h->grid, h->block, 0, st>>>(h->fbuf[h->cur], b.tape + (size_t)kk * 8 * N, k);
+        if (int rc = acheck(h, "ka_tape")) return rc;
+        ACK(h, cudaMemcpyAsync(b.tape_st + kk, h->st, sizeof(DevState), cudaMemcpyDeviceToDevice, st));
+        ACK(h, cudaMemcpyAsync(b.tape_m + (size_t)kk * mbytes, h->masks, mbytes, cudaMemcpyDeviceToDevice, st));
+        return step ? sim_step(h) : FLBM_OK;
+    };
+    // Slots [0, n) of the segment's tape to (or from) the store's slots from step s0.
+    auto store_copy = [&](int64_t s0, int n, bool to_store) -> int {
+        float* t = b.all_tape + (size_t)s0 * 8 * N;
+        DevState* ts = b.all_st + s0;
+        uint8_t* tm = b.all_m + (size_t)s0 * mbytes;
+        const size_t nt = sizeof(float) * 8 * N * (size_t)n, ns = sizeof(DevState) * (size_t)n;
+        const size_t nm = mbytes * (size_t)n;
+        const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+        ACK(h, cudaMemcpyAsync(to_store ? (void*)t : (void*)b.tape, to_store ? (void*)b.tape : (void*)t, nt, d2d, st));
+        ACK(h, cudaMemcpyAsync(to_store ? (void*)ts : (void*)b.tape_st, to_store ? (void*)b.tape_st : (void*)ts, ns,
+                               d2d, st));
+        ACK(h, cudaMemcpyAsync(to_store ? (void*)tm : (void*)b.tape_m, to_store ? (void*)b.tape_m : (void*)tm, nm,
+                               d2d, st));
+        return FLBM_OK;
+    };
+    if (whole) {
+        // Forward run writing the tape of every step, a segment at a time
+        // (its slots staged in the segment's tape, whose graphs repeat), and
+        // the sum of Vavg_z.
+        for (int64_t c = 0; c < nck; ++c) {
+            const int64_t s0 = c * K;
+            const int Ls = (int)std::min<int64_t>(K, T - s0);
+            for (int kk = 0; kk < Ls;) {
+                if (graphs && kk % kAdjGraph == 0 && kk + kAdjGraph <= Ls) {
+                    std::vector<cudaGraphExec_t>& v = ag.fwt[h->cur];
+                    const size_t j = (size_t)(kk / kAdjGraph);
+                    if (v.size() <= j) v.resize(j + 1, nullptr);
+                    if (!v[j]) {
+                        const int k0 = kk;
+                        if (int rc = capture_graph(h, &v[j], [&]() -> int {
+                                for (int i = 0; i < kAdjGraph; ++i) {
+                                    if (int r = tape_step(k0 + i, false)) return r;
+                                    if (int r = fwd_step()) return r;
+                                }
+                                return FLBM_OK;
+                            }))
+                            return rc;
+                    }
+                    ACK(h, cudaGraphLaunch(v[j], st));
+                    kk += kAdjGraph;
+                } else {
+                    if (int rc = tape_step(kk, false)) return rc;
+                    if (int rc = fwd_step()) return rc;
+                    ++kk;
+                }
+            }
+            if (int rc = store_copy(s0, Ls, true)) return rc;
+        }
+        if (int rc = tape_step(0, false)) return rc;  // the final state
+        if (int rc = store_copy(T, 1, true)) return rc;
+    }
     // Forward run: checkpoints every K steps, the sum of Vavg_z.
-    for (int64_t s = 0; s < T;) {
+    for (int64_t s = 0; !whole && s < T;) {
         if (s % K == 0) {
             const int64_t c = s / K;
             if (int rc = save_state(h, b.ck_f + c * fN, b.ck_st + c, b.ck_m + c * mbytes, mbytes,
@@ -1489,9 +1591,10 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
             }
         }
     }
-    if (int rc = save_state(h, b.ck_f + nck * fN, b.ck_st + nck, b.ck_m + nck * mbytes, mbytes,
-                            b.ck_psi + nck * 2 * k.padn))
-        return rc;
+    if (!whole)
+        if (int rc = save_state(h, b.ck_f + nck * fN, b.ck_st + nck, b.ck_m + nck * mbytes, mbytes,
+                                b.ck_psi + nck * 2 * k.padn))
+            return rc;
     cudaEventRecord(ev[1], st);
     // Reverse sweep, segment by segment from the last.
     const double vol = 4.0 / 3.0 * M_PI * p.radius * p.radius * p.radius;
@@ -1501,18 +1604,14 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
     for (int64_t c = nck - 1; c >= 0; --c) {
         const int64_t s0 = c * K;
         const int Ls = (int)std::min<int64_t>(K, T - s0);
-        if (int rc = load_state(h, b.ck_f + c * fN, b.ck_st + c, b.ck_m + c * mbytes, mbytes,
-                                b.ck_psi + c * 2 * k.padn))
+        // The segment's tape: from the store, or recomputed from its checkpoint.
+        if (whole) {
+            if (int rc = store_copy(s0, Ls + 1, false)) return rc;
+        } else if (int rc = load_state(h, b.ck_f + c * fN, b.ck_st + c, b.ck_m + c * mbytes, mbytes,
+                                       b.ck_psi + c * 2 * k.padn)) {
             return rc;
-        // Tape slot kk (moments, particle record, masks of the state), then a step.
-        auto tape_step = [&](int kk, bool step) -> int {
-            ka_tape<<<h->grid, h->block, 0, st>>>(h->fbuf[h->cur], b.tape + (size_t)kk * 8 * N, k);
-            if (int rc = acheck(h, "ka_tape")) return rc;
-            ACK(h, cudaMemcpyAsync(b.tape_st + kk, h->st, sizeof(DevState), cudaMemcpyDeviceToDevice, st));
-            ACK(h, cudaMemcpyAsync(b.tape_m + (size_t)kk * mbytes, h->masks, mbytes, cudaMemcpyDeviceToDevice, st));
-            return step ? sim_step(h) : FLBM_OK;
-        };
-        for (int kk = 0; kk <= Ls;) {
+        }
+        for (int kk = 0; !whole && kk <= Ls;) {
             if (graphs && kk % kAdjGraph == 0 && kk + kAdjGraph <= Ls) {
                 std::vector<cudaGraphExec_t>& v = ag.rec[h->cur];
                 const size_t j = (size_t)(kk / kAdjGraph);
@@ -1552,9 +1651,10 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
         }
         if (Ls & 1) lcur = 1 - lcur;
     }
-    if (int rc = load_state(h, b.ck_f + nck * fN, b.ck_st + nck, b.ck_m + nck * mbytes, mbytes,
-                            b.ck_psi + nck * 2 * k.padn))
-        return rc;
+    if (!whole)
+        if (int rc = load_state(h, b.ck_f + nck * fN, b.ck_st + nck, b.ck_m + nck * mbytes, mbytes,
+                                b.ck_psi + nck * 2 * k.padn))
+            return rc;
     cudaEventRecord(ev[2], st);
     AdjState a;
     ACK(h, cudaMemcpyAsync(&a, b.adj, sizeof(a), cudaMemcpyDeviceToHost, st));
@@ -1568,6 +1668,7 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
     out->dJ_dG = a.grad[2];
     out->steps = T;
     out->checkpoint_every = K;
+    out->whole_tape = whole ? 1 : 0;
     out->device_bytes = (double)b.bytes;
     out->ms_forward = f0;
     out->ms_reverse = f1;

@@ -78,6 +78,7 @@ struct flbm_sim {
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     long long ntiles = 0;
     int64_t launches = 0;
+    int64_t adj_tape_limit = -1;  // flbm_adjoint_tape_limit: < 0 automatic, 0 never, > 0 bytes
     std::string err;
 };
 

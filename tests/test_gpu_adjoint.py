@@ -127,6 +127,30 @@ def test_checkpoint_interval_changes_nothing(flbm, small_case):
             assert r[key] == ref[key], (K, key)
 
 
+def test_whole_tape_equals_checkpoint_recompute(flbm, small_case):
+    """The small case fits the default tape limit, so its forward run keeps
+    the tape of every step and nothing is recomputed. With the limit at 0
+    (or below the store's size) the run checkpoints and recomputes each
+    segment instead. Both must give the same J and gradient, and leave the
+    same state, bit for bit, for full and ragged segments."""
+    p, T = small_case["p"], small_case["T"]
+    ref = small_case["res"]
+    assert ref["whole_tape"]
+    for K, limit in ((16, 0), (7, 0), (16, 1)):
+        a = _gpu_start(flbm, p, V0)
+        ra = a.adjoint(T, K, tape_limit=-1)
+        c = _gpu_start(flbm, p, V0)
+        rc = c.adjoint(T, K, tape_limit=limit)
+        assert ra["whole_tape"] and not rc["whole_tape"], (K, limit)
+        for key in ("J",) + KEYS:
+            assert ra[key] == rc[key] == ref[key], (K, limit, key)
+        assert np.array_equal(a.read_f(), c.read_f())
+        pa, pc = a.particle(), c.particle()
+        for k in ("X", "V", "Omega", "delta"):
+            assert np.array_equal(pa[k], pc[k])
+        assert pa["step"] == pc["step"] == T
+
+
 def test_leaves_the_state_of_plain_steps(flbm, small_case):
     p, T = small_case["p"], small_case["T"]
     plain = _gpu_start(flbm, p, V0)
