@@ -14,10 +14,14 @@
 // post-streaming populations is affine in c_i:
 //     lambda_f_li(x) = a_l(x) + c_i . b_l(x)
 // and the adjoint state is the field (a_A, a_B, b_A, b_B): 8 floats per node.
-// The forward run keeps a checkpoint every K steps; each segment is
-// recomputed from its checkpoint while a tape of the moments (rho_l, j_l: 8
-// floats per node), the particle record and the particle masks of every step
-// is written, and the segment is then swept backwards. Per reverse step:
+// The reverse sweep reads a tape of the moments (rho_l, j_l: 8 floats per
+// node), the particle record and the particle masks of every step, segment
+// by segment of K steps. Where the tape of all T steps fits the device (the
+// limit of flbm_adjoint_tape_limit), the forward run writes it to a store
+// and each segment's slots are copied back before its sweep. Otherwise the
+// forward run keeps a checkpoint every K steps, and each segment is
+// recomputed from its checkpoint, writing its tape, before it is swept
+// backwards. Per reverse step:
 //   ka_pre       adjoint of the mass ledger (delta_l = ledger_l / N_fluid)
 //   ka_cover     adjoint of cover/uncover at the new position
 //   ka_cover_mean  uncovered nodes' neighbour means -> a_l of those neighbours
