@@ -140,8 +140,13 @@ int launch_psi(flbm_sim* h, cudaEvent_t* ev = nullptr)
     const KParams& k = h->kp;
     float* psi = psi_cur(h);
     record(h, ev, 0);
-    k_density<<<h->grid, h->block, 0, h->stream>>>(h->fbuf[h->cur], psi, h->st, h->masks, k);
-    if (int rc = launch_check(h, "k_density")) return rc;
+    if (h->tape_out) {
+        k_density_tape<<<h->grid, h->block, 0, h->stream>>>(h->fbuf[h->cur], psi, h->st, h->masks, k, h->tape_out);
+        if (int rc = launch_check(h, "k_density_tape")) return rc;
+    } else {
+        k_density<<<h->grid, h->block, 0, h->stream>>>(h->fbuf[h->cur], psi, h->st, h->masks, k);
+        if (int rc = launch_check(h, "k_density")) return rc;
+    }
     record(h, ev, 1);
     const int nbs = (int)((shell_count(k) + kThreads - 1) / kThreads);
     const int nbv = virtual_blocks(k);
@@ -434,6 +439,14 @@ void fill_header(const flbm_sim* h, CkptHeader* hd)
 
 namespace flbm {
 int sim_step(flbm_sim* h, cudaEvent_t* ev) { return launch_step(h, ev); }
+int sim_step_tape(flbm_sim* h, float* tape)
+{
+    if (use_fused(h)) return fail(h, FLBM_E_UNSUPPORTED, "a taped step needs the two-pass density mode");
+    h->tape_out = tape;
+    const int rc = launch_step(h);
+    h->tape_out = nullptr;
+    return rc;
+}
 int sim_fail(flbm_sim* h, int code, const std::string& msg) { return fail(h, code, msg); }
 int sim_ensure_psi(flbm_sim* h) { return ensure_psi(h); }
 bool sim_fused(const flbm_sim* h) { return use_fused(h); }

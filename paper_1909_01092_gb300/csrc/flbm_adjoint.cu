@@ -1503,19 +1503,29 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
     // launches do not depend on host state).
     AdjGraphs ag;
     const bool graphs = st != nullptr && !sim_fused(h);
-    auto fwd_step = [&]() -> int {
-        if (int rc = sim_step(h)) return rc;
+    auto acc_J = [&]() -> int {
         ka_accJ<<<1, 1, 0, st>>>(h->st, b.adj);
         return acheck(h, "ka_accJ");
     };
+    auto fwd_step = [&]() -> int {
+        if (int rc = sim_step(h)) return rc;
+        return acc_J();
+    };
     // Tape slot kk of a segment (moments, particle record, masks of the
-    // current state), then, with step, a step.
+    // current state), then, with step, a step. A two-pass step's density
+    // pass writes the moments itself (sim_step_tape: one read of the
+    // populations); otherwise ka_tape does.
     auto tape_step = [&](int kk, bool step) -> int {
-        ka_tape<<<h->grid, h->block, 0, st>>>(h->fbuf[h->cur], b.tape + (size_t)kk * 8 * N, k);
-        if (int rc = acheck(h, "ka_tape")) return rc;
+        float* tp = b.tape + (size_t)kk * 8 * N;
+        const bool fused_tape = step && !sim_fused(h);
+        if (!fused_tape) {
+            ka_tape<<<h->grid, h->block, 0, st>>>(h->fbuf[h->cur], tp, k);
+            if (int rc = acheck(h, "ka_tape")) return rc;
+        }
         ACK(h, cudaMemcpyAsync(b.tape_st + kk, h->st, sizeof(DevState), cudaMemcpyDeviceToDevice, st));
         ACK(h, cudaMemcpyAsync(b.tape_m + (size_t)kk * mbytes, h->masks, mbytes, cudaMemcpyDeviceToDevice, st));
-        return step ? sim_step(h) : FLBM_OK;
+        if (!step) return FLBM_OK;
+        return fused_tape ? sim_step_tape(h, tp) : sim_step(h);
     };
     // Slots [0, n) of the segment's tape to (or from) the store's slots from step s0.
     auto store_copy = [&](int64_t s0, int n, bool to_store) -> int {
@@ -1548,8 +1558,8 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
                         const int k0 = kk;
                         if (int rc = capture_graph(h, &v[j], [&]() -> int {
                                 for (int i = 0; i < kAdjGraph; ++i) {
-                                    if (int r = tape_step(k0 + i, false)) return r;
-                                    if (int r = fwd_step()) return r;
+                                    if (int r = tape_step(k0 + i, true)) return r;
+                                    if (int r = acc_J()) return r;
                                 }
                                 return FLBM_OK;
                             }))
@@ -1558,8 +1568,8 @@ extern "C" int flbm_adjoint_run(flbm_t* h, int64_t nsteps, int32_t checkpoint_ev
                     ACK(h, cudaGraphLaunch(v[j], st));
                     kk += kAdjGraph;
                 } else {
-                    if (int rc = tape_step(kk, false)) return rc;
-                    if (int rc = fwd_step()) return rc;
+                    if (int rc = tape_step(kk, true)) return rc;
+                    if (int rc = acc_J()) return rc;
                     ++kk;
                 }
             }

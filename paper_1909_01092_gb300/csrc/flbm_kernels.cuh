@@ -70,6 +70,51 @@ __device__ __forceinline__ void density_node(int x, int y, int z, const float* _
     psi[P.padn + q] = rb;
 }
 
+// The density pass of a step whose state the adjoint records: it also
+// writes the moment tape (rho_l and j_l of every node as raw sums of its
+// populations, particle nodes included; fields rho_A, rho_B, j_A, j_B of N
+// floats each), so the populations are read once for both. The sums run in
+// direction order, as density_node's and the adjoint's own tape kernel's do.
+static __global__ void __launch_bounds__(kThreads) k_density_tape(const float* __restrict__ f,
+                                                                  float* __restrict__ psi,
+                                                                  const DevState* __restrict__ st,
+                                                                  const uint8_t* __restrict__ masks, KParams P,
+                                                                  float* __restrict__ tape)
+{
+    const int x = blockIdx.x * P.tx + threadIdx.x;
+    const int y = blockIdx.y * P.ty + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= P.lx || y >= P.ly) return;
+    const long long n = x + (long long)P.lx * (y + (long long)P.ly * z);
+    bool solid = false;
+    if (P.has_particle) {
+        const int o[3] = {st->box0[0], st->box0[1], st->box0[2]};
+        solid = is_solid(x, y, z, o, masks + (size_t)st->cur * P.B * P.B * P.B, P);
+    }
+    float rho[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        float fl[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) fl[i] = f[(long long)(19 * l + i) * P.N + n];
+        float r = 0.0f, j[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            r += fl[i];
+            j[0] += cxv(i) * fl[i];
+            j[1] += cyv(i) * fl[i];
+            j[2] += czv(i) * fl[i];
+        }
+        tape[(long long)l * P.N + n] = r;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) tape[(long long)(2 + 3 * l + a) * P.N + n] = j[a];
+        rho[l] = solid ? 0.0f : r;
+    }
+    const long long q = pad_index(x, y, z, P);
+    psi[q] = rho[0];
+    psi[P.padn + q] = rho[1];
+}
+
 static __global__ void __launch_bounds__(kThreads) k_density(const float* __restrict__ f, float* __restrict__ psi,
                                                              const DevState* __restrict__ st,
                                                              const uint8_t* __restrict__ masks, KParams P)

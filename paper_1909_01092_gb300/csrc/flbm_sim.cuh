@@ -79,6 +79,7 @@ struct flbm_sim {
     long long ntiles = 0;
     int64_t launches = 0;
     int64_t adj_tape_limit = -1;  // flbm_adjoint_tape_limit: < 0 automatic, 0 never, > 0 bytes
+    float* tape_out = nullptr;    // set by sim_step_tape: the step's density pass also writes this tape
     std::string err;
 };
 
@@ -90,6 +91,10 @@ inline float* psi_cur(flbm_sim* h) { return h->psibuf[h->cur]; }
 // Launch one time step on h's stream (h->cur flips). With ev, events
 // ev[0..5] are recorded between its kernel classes.
 int sim_step(flbm_sim* h, cudaEvent_t* ev = nullptr);
+
+// One two-pass step whose density pass also writes the adjoint's moment
+// tape of the current state (8 fields of N floats) to tape.
+int sim_step_tape(flbm_sim* h, float* tape);
 
 // Record an error message on h and return code.
 int sim_fail(flbm_sim* h, int code, const std::string& msg);
