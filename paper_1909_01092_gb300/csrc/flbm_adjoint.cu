@@ -22,10 +22,10 @@
 // forward run keeps a checkpoint every K steps, and each segment is
 // recomputed from its checkpoint, writing its tape, before it is swept
 // backwards. Per reverse step:
-//   ka_pre       adjoint of the mass ledger (delta_l = ledger_l / N_fluid)
-//   ka_cover     adjoint of cover/uncover at the new position
+//   ka_cover     adjoint of the mass ledger (delta_l = ledger_l / N_fluid) and of
+//                cover/uncover at the new position; its last block runs the
+//                leap-frog Newton-Euler update adjoint (FP64), dJ/dg
 //   ka_cover_mean  uncovered nodes' neighbour means -> a_l of those neighbours
-//   ka_update    leap-frog Newton-Euler update (FP64), dJ/dg
 //   ka_psi_tape, k_shell_virtual  density field of the step from the tape
 //   ka_node_bulk, ka_node_near  streaming (pull of the adjoint), moving
 //                links, Shan-Chen reaction, collision (flbm_adjoint_math.h)
@@ -59,8 +59,9 @@ struct AdjState {
     double lF[3], lT[3], lled[2];                      // adjoint of the step's force, torque, mass ledger
     double grad[3];                                    // dJ/dg, dJ/d delta_rho, dJ/dG
     double J;                                          // sum of Vavg_z over the forward steps
-    float lFf[3], lTf[3], lledf[2], lPf[3], lLf[3];    // float copies for the node kernels
+    float lFf[3], lTf[3];                              // float copies for the node kernels
     unsigned red_done;                                 // blocks of ka_reduce done (last-block ticket)
+    unsigned cover_done;                               // blocks of ka_cover done (last-block ticket)
 };
 
 // Precision. The adjoint fields carry large smooth parts (the adjoints of
@@ -211,22 +212,6 @@ static __global__ void __launch_bounds__(kT) ka_psi_tape(const float* __restrict
     psi[P.padn + q] = sol ? 0.0f : tape[P.N + n];
 }
 
-// ---------------------------------------------------------------------------
-// Mass ledger: delta_l(n+1) = ledger_l / N_fluid(n+1). Float copies of the
-// adjoints the box and node kernels read. One thread.
-// ---------------------------------------------------------------------------
-static __global__ void ka_pre(AdjState* __restrict__ a, const DevState* __restrict__ s1)
-{
-    for (int l = 0; l < 2; ++l) {
-        a->lled[l] = a->ld[l] / (double)s1->nfluid;
-        a->lledf[l] = (float)a->lled[l];
-    }
-    for (int k = 0; k < 3; ++k) {
-        a->lPf[k] = (float)a->lP[k];
-        a->lLf[k] = (float)a->lL[k];
-    }
-}
-
 // Modes 0..9 of sum_i e_k(c_i) f_i (the to_modes basis), any precision.
 template <class T>
 __device__ __forceinline__ void project10(const T f[19], T m[10])
@@ -262,6 +247,36 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 }
 
 // ---------------------------------------------------------------------------
+// Leap-frog update adjoint (FP64, one thread; c = the box blocks' partials
+// summed in block order): V' = V + (F + F_p z)/m_p, X' = X + V',
+// Omega' = Omega + T/I_p, plus the two halves of Vavg in J. On exit lX, lV,
+// lOm, lP, lL hold the adjoint of step n's input state without the link
+// terms ka_node adds; dJ/dg accumulates.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void update_adjoint(AdjState* __restrict__ a, const double c[9],
+                                               const DevState* __restrict__ s0, double inv2T, double dFp_dg)
+{
+    double lXp[3], lVp[3], lOmp[3];
+    for (int k = 0; k < 3; ++k) {
+        lXp[k] = a->lX[k] + c[k];
+        lOmp[k] = a->lOm[k] + c[6 + k];
+        lVp[k] = a->lV[k] + c[3 + k] + lXp[k] + (k == 2 ? inv2T : 0.0);
+    }
+    for (int k = 0; k < 3; ++k) {
+        a->lF[k] = lVp[k] / s0->mp;
+        a->lT[k] = lOmp[k] / s0->Ip;
+        a->lFf[k] = (float)a->lF[k];
+        a->lTf[k] = (float)a->lT[k];
+        a->lX[k] = lXp[k];
+        a->lV[k] = lVp[k] + (k == 2 ? inv2T : 0.0);
+        a->lOm[k] = lOmp[k];
+        a->lP[k] = a->lF[k];
+        a->lL[k] = a->lT[k];
+    }
+    a->grad[0] += lVp[2] * dFp_dg / s0->mp;
+}
+
+// ---------------------------------------------------------------------------
 // Cover/uncover adjoint (Section 2). s0/m0: state and masks of step n (old
 // position), s1/m1: of step n+1 (new position X', velocities V', Omega').
 // Covered node c (fluid at n, particle at n+1): its post-stream populations
@@ -272,16 +287,25 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 // (a_l, b_l) of c gives lambda_mean_l = a_l + b_l . u_b and lambda_u_b =
 // sum_l mean_l b_l, plus the particle's payment of the momentum and the
 // ledger. lambda_mean_l / cnt goes to uv[] for ka_cover_mean. Per-block
-// partials: lambda X', lambda V', lambda Omega'.
+// partials: lambda X', lambda V', lambda Omega'. The adjoint of the mass
+// ledger, delta_l(n+1) = ledger_l / N_fluid(n+1), is formed by every block.
+// The last block to finish (every other block has read the particle
+// adjoint by then) stores it for the node kernels and runs the leap-frog
+// update adjoint on the partials summed in block order.
 // ---------------------------------------------------------------------------
 static __global__ void __launch_bounds__(kT) ka_cover(lam_t* __restrict__ lam1, const float* __restrict__ tape1,
                                                       const DevState* __restrict__ s0, const uint8_t* __restrict__ mk0,
                                                       const DevState* __restrict__ s1, const uint8_t* __restrict__ mk1,
-                                                      const AdjState* __restrict__ adj, double* __restrict__ uv,
-                                                      double* __restrict__ parts, KParams P)
+                                                      AdjState* __restrict__ adj, double* __restrict__ uv,
+                                                      double* __restrict__ parts, KParams P, double inv2T,
+                                                      double dFp_dg)
 {
     __shared__ double s_red[(kT / 32) * 8];
     __shared__ double s_out[8];
+    __shared__ double s_lled[2];
+    __shared__ double s_c[9];
+    if (threadIdx.x < 2) s_lled[threadIdx.x] = adj->ld[threadIdx.x] / (double)s1->nfluid;
+    __syncthreads();
     const int B = P.B, B3 = B * B * B;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const uint8_t* m0 = cur_mask(s0, mk0, P);
@@ -308,7 +332,7 @@ static __global__ void __launch_bounds__(kT) ka_cover(lam_t* __restrict__ lam1, 
                 cross3(adj->lL, r, lb);
                 for (int a = 0; a < 3; ++a) lb[a] += adj->lP[a];
                 for (int l = 0; l < 2; ++l) {
-                    lam1[(size_t)l * N + n] = ssplit(adj->lled[l]);
+                    lam1[(size_t)l * N + n] = ssplit(s_lled[l]);
                     for (int a = 0; a < 3; ++a) lam1[(size_t)(2 + 3 * l + a) * N + n] = ssplit(lb[a]);
                 }
                 for (int a = 0; a < 3; ++a) j[a] = (double)tape1[(2 + a) * N + n] + (double)tape1[(5 + a) * N + n];
@@ -349,7 +373,7 @@ static __global__ void __launch_bounds__(kT) ka_cover(lam_t* __restrict__ lam1, 
                     const double al = sval(lam1[(size_t)l * N + n]);
                     double bl[3];
                     for (int a = 0; a < 3; ++a) bl[a] = sval(lam1[(size_t)(2 + 3 * l + a) * N + n]);
-                    const double lmean = al + bl[0] * ub[0] + bl[1] * ub[1] + bl[2] * ub[2] - lqub - adj->lled[l];
+                    const double lmean = al + bl[0] * ub[0] + bl[1] * ub[1] + bl[2] * ub[2] - lqub - s_lled[l];
                     if (cnt) uv[(size_t)l * B3 + t] = lmean / cnt;
                     for (int a = 0; a < 3; ++a) lub[a] += rl[l] * bl[a];
                 }
@@ -376,6 +400,17 @@ static __global__ void __launch_bounds__(kT) ka_cover(lam_t* __restrict__ lam1, 
     double v1[8] = {acc[8], 0, 0, 0, 0, 0, 0, 0};
     block_sum8<kT>(v1, s_red, s_out);
     if (threadIdx.x == 0) parts[blockIdx.x * 9 + 8] = s_out[0];
+    if (!last_block(&adj->cover_done, gridDim.x, threadIdx.x < 8)) return;  // threads 0..7 wrote parts
+    if (threadIdx.x < 9) {
+        double sum = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) sum += __ldcg(parts + b * 9 + threadIdx.x);
+        s_c[threadIdx.x] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    adj->lled[0] = s_lled[0];
+    adj->lled[1] = s_lled[1];
+    update_adjoint(adj, s_c, s0, inv2T, dFp_dg);
 }
 
 // Neighbours of uncovered nodes that fed the neighbour mean: fluid at n and
@@ -422,43 +457,6 @@ static __global__ void __launch_bounds__(kT) ka_cover_mean(lam_t* __restrict__ l
     }
 }
 
-// ---------------------------------------------------------------------------
-// Leap-frog update adjoint (FP64, one warp: lane k < 9 sums partial k over
-// the box blocks in order, lane 0 updates): V' = V + (F + F_p z)/m_p,
-// X' = X + V', Omega' = Omega + T/I_p, plus the two halves of Vavg in J.
-// On exit lX, lV, lOm, lP, lL hold the adjoint of step n's input state
-// without the link terms ka_node adds; dJ/dg accumulates.
-// ---------------------------------------------------------------------------
-static __global__ void ka_update(AdjState* __restrict__ a, const double* __restrict__ parts, int nblocks,
-                                 const DevState* __restrict__ s0, double inv2T, double dFp_dg)
-{
-    __shared__ double c[9];
-    if (threadIdx.x < 9) {
-        double sum = 0.0;
-        for (int b = 0; b < nblocks; ++b) sum += parts[b * 9 + threadIdx.x];
-        c[threadIdx.x] = sum;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    double lXp[3], lVp[3], lOmp[3];
-    for (int k = 0; k < 3; ++k) {
-        lXp[k] = a->lX[k] + c[k];
-        lOmp[k] = a->lOm[k] + c[6 + k];
-        lVp[k] = a->lV[k] + c[3 + k] + lXp[k] + (k == 2 ? inv2T : 0.0);
-    }
-    for (int k = 0; k < 3; ++k) {
-        a->lF[k] = lVp[k] / s0->mp;
-        a->lT[k] = lOmp[k] / s0->Ip;
-        a->lFf[k] = (float)a->lF[k];
-        a->lTf[k] = (float)a->lT[k];
-        a->lX[k] = lXp[k];
-        a->lV[k] = lVp[k] + (k == 2 ? inv2T : 0.0);
-        a->lOm[k] = lOmp[k];
-        a->lP[k] = a->lF[k];
-        a->lL[k] = a->lT[k];
-    }
-    a->grad[0] += lVp[2] * dFp_dg / s0->mp;
-}
 
 // ---------------------------------------------------------------------------
 // Per fluid node of step n: adjoint of streaming (pulled from the
@@ -1353,15 +1351,11 @@ int reverse_step(flbm_sim* h, AdjBuffers& b, int kk, lam_t* L1, lam_t* L0, doubl
     k_shell_virtual<<<nbs + nbv, kThreads, 0, h->side>>>(psi_scr, s0, m0, k, (int)nbs);
     if (int rc = acheck(h, "k_shell_virtual")) return rc;
     ACK(h, cudaEventRecord(h->join_ev, h->side));
-    ka_pre<<<1, 1, 0, st>>>(b.adj, s1);
-    if (int rc = acheck(h, "ka_pre")) return rc;
-    ka_cover<<<h->box_blocks, kT, 0, st>>>(L1, t1, s0, m0, s1, m1, b.adj, b.uv, b.cparts, k);
+    ka_cover<<<h->box_blocks, kT, 0, st>>>(L1, t1, s0, m0, s1, m1, b.adj, b.uv, b.cparts, k, inv2T, dFp_dg);
     if (int rc = acheck(h, "ka_cover")) return rc;
     const int G3 = (k.B + 2) * (k.B + 2) * (k.B + 2);
     ka_cover_mean<<<(G3 + kT - 1) / kT, kT, 0, st>>>(L1, s0, m0, s1, m1, b.uv, k);
     if (int rc = acheck(h, "ka_cover_mean")) return rc;
-    ka_update<<<1, 32, 0, st>>>(b.adj, b.cparts, h->box_blocks, s0, inv2T, dFp_dg);
-    if (int rc = acheck(h, "ka_update")) return rc;
     ACK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
     // Near tiles on the handle's side stream, concurrently with the bulk tiles
     // (disjoint nodes and partials), joined before the psi adjoint.
