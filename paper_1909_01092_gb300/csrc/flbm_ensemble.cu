@@ -332,27 +332,20 @@ int apply_config(flbm_ens* e)
         }
     }
     e->off[W_COUNT] = (long long)items.size();
-    // Bulk launches with descriptor chunks: per variant, replicas by
-    // decreasing tile count; a chunk takes replicas while it has room and
-    // each has at least 3/4 of the first one's tiles (the blocks past a
-    // replica's own return at once).
+    // Bulk launches with descriptor chunks, per variant (group_by_blocks;
+    // the blocks past a replica's own tiles return at once).
     for (int k = 0; k < 4; ++k) {
-        const int w = W_BULK + k;
+        std::vector<long long> tiles(e->n);
+        for (int r = 0; r < e->n; ++r) {
+            tiles[r] = blocks_of(e->kp[r], W_BULK + k);
+            if (tiles[r] > 0x7fffffffLL) return efail(e, FLBM_E_INVAL, "too many tiles in one replica");
+        }
         auto& ch = e->rep_launches[k];
         ch.clear();
-        std::vector<int> reps;
-        for (int r = 0; r < e->n; ++r)
-            if (blocks_of(e->kp[r], w) > 0) reps.push_back(r);
-        std::stable_sort(reps.begin(), reps.end(),
-                         [&](int a, int b) { return blocks_of(e->kp[a], w) > blocks_of(e->kp[b], w); });
-        for (int r : reps) {
-            const long long t = blocks_of(e->kp[r], w);
-            if (t > 0x7fffffffLL) return efail(e, FLBM_E_INVAL, "too many tiles in one replica");
-            if (ch.empty() || ch.back().n == kChunkReps || 4 * t < 3LL * ch.back().max_blocks) {
-                ch.emplace_back();
-                ch.back().max_blocks = (int)t;
-            }
-            ch.back().c.r[ch.back().n++] = e->rd[r];
+        for (const auto& g : group_by_blocks(tiles, kChunkReps)) {
+            ch.emplace_back();
+            ch.back().max_blocks = (int)tiles[g[0]];
+            for (int r : g) ch.back().c.r[ch.back().n++] = e->rd[r];
         }
     }
     if (items.size() > (size_t)0x7fffffff) return efail(e, FLBM_E_INVAL, "too many work items");

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "flbm.h"
 #include "flbm_kernels.cuh"
@@ -125,6 +126,27 @@ inline void make_kparams(const flbm_params& p, int tile_policy, KParams& k)
 inline long long tile_count(const KParams& k) { return (long long)k.gx * k.gy * k.lz; }
 inline long long cand_count(const KParams& k) { return (long long)k.ncx * k.ncy * k.ncz; }
 inline int box_block_count(const KParams& k) { return (k.B * k.B * k.B + 255) / 256; }
+
+// Groups of replicas for launches whose grid is (largest block count of the
+// group, members): blocks[r] > 0 is replica r's block count (0: not in any
+// launch). Replicas by decreasing block count (stable); a group takes
+// replicas while it has fewer than cap and each has at least 3/4 of its
+// first member's blocks, so that at most a quarter of a launch's blocks
+// find no work.
+inline std::vector<std::vector<int>> group_by_blocks(const std::vector<long long>& blocks, int cap)
+{
+    std::vector<int> order;
+    for (int r = 0; r < (int)blocks.size(); ++r)
+        if (blocks[r] > 0) order.push_back(r);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return blocks[a] > blocks[b]; });
+    std::vector<std::vector<int>> groups;
+    for (int r : order) {
+        if (groups.empty() || (int)groups.back().size() == cap || 4 * blocks[r] < 3 * blocks[groups.back()[0]])
+            groups.emplace_back();
+        groups.back().push_back(r);
+    }
+    return groups;
+}
 
 // Particle record at creation (Section 3, Eq. (fp)): sphere of radius R at
 // pos0, at rest, mass 4/3 pi R^3 rho_p, moment of inertia 2/5 m_p R^2.

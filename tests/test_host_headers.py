@@ -29,6 +29,10 @@ brute-force scan of the lattice:
   population of every node equals the target taken from the definition
   (x + c_i with wrap, or the node itself in the opposite direction across a
   wall);
+* tests/host_groups.cu (group_by_blocks): the ensemble's descriptor-chunk
+  bulk launches take every replica exactly once, at most the cap per
+  launch, with a grid that covers every member's tiles and at most a quarter
+  of its blocks idle, and start a new launch only when they must;
 * tests/host_restore.cu (check_restored_state): a particle record read from
   a checkpoint passes when it is one the library wrote, and is refused when
   its mask index, centre, velocities, box origin, fluid count, step or mass
@@ -94,3 +98,8 @@ def test_push_targets_follow_streaming_and_bounce_back(tmp_path):
     words = out.split()
     configs, targets, failed = (int(words[words.index(w) + 1]) for w in ("configurations", "targets", "failed"))
     assert failed == 0 and configs > 250 and targets > 10 ** 6, out
+
+
+def test_ensemble_launch_groups(tmp_path):
+    out = _build_and_run(tmp_path, "host_groups", 2000)
+    assert "cases 2000 failed 0" in out, out
